@@ -1,0 +1,329 @@
+"""Throughput of streamed RAVE-like decoding on GB300 (real-time 48 kHz streams).
+
+One step = one 2048-sample buffer (one latent frame) for every stream of the
+batch, through the whole reconfigured decoder: cached convolutions, polyphase
+transposed convolutions, aligned residual adds, heads and inverse PQMF.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   (the FP64 oracle on the host cores)
+
+Prints one JSON line.  ``value`` = output samples per second / 48000 over all
+ranks (each rank runs an independent replica: streams are independent).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SR = 48000
+METRIC = "real-time 48kHz streams per GB300 (BF16 vs FP32 cached conv); p99 buffer latency"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+WORKLOADS = {
+    # name: (dtype, streams, buffer latent frames)
+    "decoder-fp32-b256": ("f32", 256, 1),
+    "decoder-fp32-b1": ("f32", 1, 1),
+}
+DEFAULT_WORKLOAD = "decoder-fp32-b256"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK, sm_max_mhz=2070.0), "fallback"
+
+
+def node_flops(node, frames_out_per_step):
+    """Algorithmic FLOPs (2 per MAC) of one node for one stream-step."""
+    op = node["op"]
+    if op == "conv":
+        return 2 * node["c_out"] * node["c_in"] * node["k"] * frames_out_per_step
+    if op == "convt":
+        return 2 * node["c_in"] * node["c_out"] * node["k"] * frames_out_per_step // node["stride"]
+    return 0
+
+
+def build_decoder(dtype, streams, seed=1):
+    from paper_2204_07064_gb300 import api
+    from paper_2204_07064_gb300 import workloads as W
+
+    nodes = W.rave_decoder()
+    params = W.init_params(nodes, seed)
+    _, g, _ = api.pqmf_design(16, 64, 5.0)
+    params[W.pqmf_node_index(nodes)] = (api.inverse_pqmf_weights(g), None)
+    model = api.Model(nodes, params, dtype=dtype, max_streams=streams, max_steps_per_call=1)
+    return nodes, params, model
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [l.split(",") for l in out.strip().splitlines() if l.strip()]
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(steps, seed=1, stream_seed=11):
+    """FP64 oracle streaming of the same decoder, one stream, `steps` buffers.
+    Runs in a subprocess with one BLAS thread; returns audio seconds / wall."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from oracle import model as M, pqmf
+from paper_2204_07064_gb300 import workloads as W
+nodes = W.rave_decoder(); p = W.init_params(nodes, {seed})
+_, g, _, _ = pqmf.design(16, 64)
+p[W.pqmf_node_index(nodes)] = (pqmf.synthesis_weights(g), None)
+z = W.signal(5, {steps}, 128)
+s = M.Stream(nodes, p, seed={stream_seed})
+s.process(z[:1])
+t = time.perf_counter()
+for i in range({steps}):
+    s.process(z[i:i + 1])
+wall = time.perf_counter() - t
+print(json.dumps({{"wall": wall, "audio_s": {steps} * 2048 / {SR}}}))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["audio_s"] / d["wall"], d
+
+
+def run_reference(args):
+    """The oracle as the reference arm: FP64 NumPy streaming on host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    dtype, streams, frames = WORKLOADS[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    vals = []
+    walls = []
+    for _ in range(args.steps):
+        v, d = oracle_sample(2)
+        vals.append(v)
+        walls.append(d["wall"] / 2)
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "streams",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * statistics.mean(walls), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "streams": streams, "buffer_samples": 2048 * frames,
+                   "note": "oracle timed on 1 stream x 2 buffers per step (bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": "streams", "cores": 1, "kind": "oracle",
+                         "sample": "1 stream x 2 buffers of 2048 samples per step, FP64 NumPy, 1 BLAS thread"},
+        "e2e": {"value": value, "unit": "streams", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flush-l2", action="store_true", help="write 256 MB between steps")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2204_07064_gb300 import workloads as W
+
+    dtype, streams, frames = WORKLOADS[args.workload]
+    nodes, params, model = build_decoder(dtype, streams)
+    seeds = W.stream_seeds(1000 + rank, streams)
+    ss = [model.stream(seed=s) for s in seeds]
+    rng = np.random.default_rng(rank)
+    steps_total = args.warmup + args.steps
+    z = torch.tensor(rng.standard_normal((steps_total, streams, frames, 128)), dtype=torch.float32,
+                     device=dev)
+    y = torch.empty((streams, 2048 * frames, 1), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if args.flush_l2 else None
+    st = torch.cuda.current_stream()
+
+    for i in range(args.warmup):
+        model.process_batch(ss, z[i], y)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, per-step events, per-node library events
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    model.timing(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        if flush is not None:
+            flush.zero_()
+        starts[k].record(st)
+        model.process_batch(ss, z[args.warmup + k], y)
+        ends[k].record(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    node_ms, node_launches = model.timing_read()
+    model.timing(False)
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    samples = streams * 2048 * frames * args.steps * world
+    value = samples / (total_ms / 1000.0) / SR
+
+    # end to end through the C ABI with pinned host buffers (copies in the timed region)
+    zh = torch.empty((streams, frames, 128), dtype=torch.float32).pin_memory()
+    zh.copy_(z[0].cpu())
+    yh = torch.empty((streams, 2048 * frames, 1), dtype=torch.float32).pin_memory()
+    e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        e_starts[k].record(st)
+        model.process_batch(ss, zh, yh)
+        e_ends[k].record(st)
+        e_ends[k].synchronize()
+    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends))
+    e2e_value = streams * 2048 * frames * args.steps * world / (e2e_ms / 1000.0) / SR
+
+    # roofline of the dominant kernel class (the contractions)
+    info_u = [model.node_info(i)["frames_per_step"] for i in range(len(nodes))]
+    conv_nodes = [i for i, n in enumerate(nodes) if n["op"] in ("conv", "convt")]
+    flops = sum(node_flops(nodes[i], info_u[i]) for i in conv_nodes) * streams * frames
+    conv_ms = sum(node_ms[i] for i in conv_nodes)
+    conv_launches = sum(node_launches[i] for i in conv_nodes)
+    pk, pk_kind = peaks()
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops * args.steps / (conv_ms / 1000.0) / 1e12 if conv_ms > 0 else 0.0
+    if dtype == "f32":
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "cached conv / polyphase convT contractions (FFMA)",
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {pk.get('sm_max_mhz', 2070.0):.0f} MHz"}
+    else:
+        peak = pk.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "tcgen05 implicit-GEMM contractions", "peak_source": f"bf16 burst, {pk_kind}"}
+    roof["share_of_step"] = conv_ms / total_ms if total_ms else None
+
+    step_sorted = sorted(step_ms)
+    p50 = float(np.percentile(step_ms, 50))
+    p99 = float(np.percentile(step_ms, 99))
+    launches_per_step = (sum(node_launches) / args.steps) + 1  # + the step-counter advance
+    line = {
+        "metric": METRIC, "value": value, "unit": "streams", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": args.workload, "model": "RAVE-like decoder, random init",
+                   "streams_per_gpu": streams, "buffer_samples": 2048 * frames, "sample_rate": SR,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps" if flush is not None else
+                   "working set per step > L2 (arena + weights)",
+                   "samples_per_s": samples / (total_ms / 1000.0)},
+        "latency_ms": {"p50": p50, "p99": p99, "max": step_sorted[-1],
+                       "buffer_ms": 2048 * frames / SR * 1000.0,
+                       "meets_deadline": p99 < 2048 * frames / SR * 1000.0},
+        "e2e": {"value": e2e_value, "unit": "streams",
+                "h2d_bytes_per_step": int(zh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)},
+        "roofline": roof,
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, d = oracle_sample(64)
+        line["cpu_baseline"] = {"value": v, "unit": "streams", "cores": 1, "kind": "oracle",
+                                "sample": f"1 stream x 64 buffers of 2048 samples, FP64 NumPy, "
+                                          f"1 BLAS thread ({d['wall']:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * cachedconv.h -- C ABI of the GB300 (sm_103a) streamed-convolution library.
+ *
+ * Buffer-by-buffer inference of a non-causal 1-D convolutional audio model
+ * after post-training causal reconfiguration (Caillon & Esling, "Streamable
+ * neural audio synthesis with non-causal convolutions", DAFx-22):
+ *   - cached padding: every convolution keeps the last N input frames of the
+ *     previous buffer and uses them instead of zero left padding (section 2.2,
+ *     Fig. 1);
+ *   - right padding is moved to the left after training, which delays the
+ *     layer's output (section 3);
+ *   - strided convolutions receive an extra input delay D_a (Eq. 2,
+ *     section 3.1); transposed convolutions only delay their output;
+ *   - parallel branches are re-aligned by extra delays A_i (Eq. 3, section 3.2).
+ * The calls follow the paper's statement of the problem: a model is built from
+ * its layer list and weights, each audio stream owns a cache state, each DSP
+ * call processes one buffer (section 1, section 5.1), and the total latency
+ * is queried so that it can be compensated (section 4.2, section 4.3).
+ *
+ * Conventions for every entry point:
+ *   - Signals are float32, channels-last ("interleaved"): element (t, c) of a
+ *     buffer with C channels is at index t*C + c.
+ *   - Pointers to signal buffers may be device or host memory (detected per
+ *     call).  Host buffers are staged through device memory inside the call;
+ *     the call is asynchronous on `cuda_stream` in both cases, so the caller
+ *     synchronises that stream before reading a host output buffer.
+ *   - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - The caller owns every buffer it passes.  The library copies weights in;
+ *     a model owns its packed weights, its state arena and its streams' slots.
+ *   - Errors are returned as negative cc_status values, never by aborting; a
+ *     thread-local message is available from cc_last_error().
+ *   - A stream must not be processed concurrently with itself; different
+ *     streams may be processed concurrently on different CUDA streams only if
+ *     they are not in the same batch call.
+ */
+#ifndef CACHEDCONV_H
+#define CACHEDCONV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t cc_status;
+#define CC_OK 0
+#define CC_ERR_INVALID_ARG (-1) /* null pointer, bad enum, out-of-range size */
+#define CC_ERR_BAD_GRAPH (-2)   /* layer list not a valid streamable DAG       */
+#define CC_ERR_BAD_LENGTH (-3)  /* buffer length not a multiple of a model step */
+#define CC_ERR_NO_MEMORY (-4)   /* arena full (admission) or allocation failed */
+#define CC_ERR_CUDA (-5)        /* a CUDA runtime call failed                   */
+#define CC_ERR_TIMEOUT (-6)     /* a bounded device-side wait gave up           */
+#define CC_ERR_STATE (-7)       /* object used in the wrong state               */
+
+typedef enum {
+  CC_OP_INPUT = 0, /* the model input (exactly one, node 0)                          */
+  CC_OP_CONV = 1,  /* Conv1d, Eq. 1 with stride, dilation, trained pads L/R          */
+  CC_OP_CONVT = 2, /* ConvTranspose1d, stride S, kernel K (K % S == 0), left crop p  */
+  CC_OP_ADD = 3,   /* sum of two branches (residual), aligned by Eq. 3               */
+  CC_OP_HEADS = 4  /* tanh(in0)*sigmoid(in1) + sigmoid(in2)*u, branches aligned by Eq. 3,
+                      u = SplitMix64 noise in [-1,1) keyed on the aligned frame index */
+} cc_op;
+
+typedef enum { CC_ACT_NONE = 0, CC_ACT_LEAKY = 1 /* LeakyReLU, slope 0.2, on the node input */ } cc_act;
+
+typedef enum {
+  CC_F32 = 0,  /* FP32 storage, FP32 FFMA contractions                                   */
+  CC_BF16 = 1, /* BF16 operands on tensor cores (tcgen05), FP32 accumulation            */
+  CC_F16 = 2   /* FP16 operands on tensor cores (tcgen05), FP32 accumulation            */
+} cc_dtype;
+
+/* One layer of the trained (non-causal) model, in topological order. */
+typedef struct {
+  int32_t op;        /* cc_op                                                      */
+  int32_t n_inputs;  /* 0 (input), 1 (conv/convt), 2 (add), 3 (heads)              */
+  int32_t inputs[3]; /* producer node indices, each < this node's index           */
+  int32_t c_in, c_out;
+  int32_t kernel, stride, dilation;
+  int32_t pad_left, pad_right; /* trained zero padding, in input frames (conv)    */
+  int32_t crop;                /* trained left crop p of the full ConvT output;
+                                  the trained right crop is K - S - p             */
+  int32_t act_in;              /* cc_act applied to the node's input              */
+  int32_t has_bias;
+} cc_node_desc;
+
+typedef struct {
+  int32_t compute;            /* cc_dtype                                             */
+  int32_t max_streams;        /* number of per-stream state slots in the arena; 0 builds a
+                                 plan only (analysis queries, no device memory, no
+                                 weights needed; streams cannot be created)           */
+  int32_t max_steps_per_call; /* model steps one launch chain covers (longer buffers are
+                                 split); sizes the per-slot scratch rows              */
+  int32_t noise;              /* 1: heads add sigmoid(in2)*u; 0: u = 0 (section 4.2)  */
+} cc_model_config;
+
+typedef struct cc_model cc_model;
+typedef struct cc_stream cc_stream;
+
+/* Build a model: validate the DAG, run the causal-reconfiguration analysis
+ * (section 3: right pad -> left pad, Eq. 2 stride alignment, cumulated lag,
+ * Eq. 3 branch alignment), size every cache, allocate the arena
+ * (max_streams slots) and upload packed weights.
+ * weights[i] / biases[i]: host float32 arrays for node i (NULL where the node
+ * has none): conv [c_out][c_in][kernel], convt [c_in][c_out][kernel],
+ * bias [c_out].  They are copied; the caller may free them on return.
+ * Errors: INVALID_ARG, BAD_GRAPH (with the offending node in cc_last_error),
+ * NO_MEMORY, CUDA. */
+cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes,
+                          const float* const* weights, const float* const* biases,
+                          const cc_model_config* config, cc_model** out);
+cc_status cc_model_destroy(cc_model* model);
+
+/* Total latency of the reconfigured model, in output frames: the cumulated
+ * delay of the last node (section 3.1, section 4.3). */
+cc_status cc_model_total_delay(const cc_model* model, int64_t* out_frames);
+
+/* Channels and frames per model step.  A step is the smallest input length
+ * that gives every layer a whole number of frames (e.g. 1 latent frame for a
+ * x2048 decoder, 2048 samples for a /2048 encoder). */
+cc_status cc_model_io(const cc_model* model, int32_t* in_channels, int32_t* out_channels,
+                      int32_t* in_per_step, int32_t* out_per_step);
+
+/* Per-node analysis results: cumulated delay D (own frames), Eq. 2 extra delay
+ * D_a (strided convs), Eq. 3 alignment A_i of each input (merges), frames of
+ * this node's output kept between calls (the cached padding of its consumers),
+ * and the node's frames per model step.  Any output pointer may be NULL. */
+cc_status cc_model_node_info(const cc_model* model, int32_t node, int64_t* delay,
+                             int32_t* extra_delay, int32_t* align3, int32_t* kept_frames,
+                             int32_t* frames_per_step);
+
+/* Bytes of persistent cache state per stream (the cached padding), and bytes
+ * of one arena slot (state plus per-call rows). */
+cc_status cc_model_state_bytes(const cc_model* model, size_t* state_bytes, size_t* slot_bytes);
+
+/* Create a stream: take a free arena slot (NO_MEMORY when none is left: admission
+ * by cache memory), zero its caches.  `seed` keys the heads' noise. */
+cc_status cc_stream_create(cc_model* model, uint64_t seed, void* cuda_stream, cc_stream** out);
+cc_status cc_stream_destroy(cc_stream* stream);
+
+/* Zero the stream's caches and its step counter (enqueued on cuda_stream). */
+cc_status cc_stream_reset(cc_stream* stream, void* cuda_stream);
+
+/* Process one buffer: n_in input frames ([n_in][in_channels]) -> n_out output
+ * frames ([n_out][out_channels]).  n_in must be a multiple of in_per_step and
+ * n_out == n_in / in_per_step * out_per_step (else BAD_LENGTH).  The output of
+ * a call is the reconfigured model's output for these frames: it equals the
+ * offline model's output delayed by cc_model_total_delay frames. */
+cc_status cc_stream_process(cc_stream* stream, const float* in, int64_t n_in, float* out,
+                            int64_t n_out, void* cuda_stream);
+
+/* Process one buffer for each of `count` distinct streams of one model in a
+ * single launch chain (streams batched into the contraction's N dimension).
+ * in:  count buffers of n_in frames, stream i at in + i*in_stride (floats);
+ * out: count buffers of n_out frames, stream i at out + i*out_stride.
+ * Same length rules as cc_stream_process.  A stream may appear only once. */
+cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, int32_t count,
+                           const float* in, int64_t in_stride, int64_t n_in, float* out,
+                           int64_t out_stride, int64_t n_out, void* cuda_stream);
+
+/* Checkpoint / resume: the whole stream state (its arena slot, holding every
+ * cache, plus its step counter) as an opaque host blob of exactly
+ * cc_stream_state_size() bytes.  Both calls synchronise cuda_stream.  A blob
+ * restores into any stream of the same model. */
+cc_status cc_stream_state_size(const cc_stream* stream, size_t* bytes);
+cc_status cc_stream_get_state(cc_stream* stream, void* host_blob, size_t bytes, void* cuda_stream);
+cc_status cc_stream_set_state(cc_stream* stream, const void* host_blob, size_t bytes,
+                              void* cuda_stream);
+
+/* Per-node device timing (CUDA events recorded around every launch on the
+ * launching stream).  enable=1 starts accumulating; cc_model_timing_read
+ * synchronises and returns, per node, the summed milliseconds and launch count
+ * since the last enable. */
+cc_status cc_model_timing(cc_model* model, int32_t enable);
+cc_status cc_model_timing_read(cc_model* model, double* ms_per_node, int64_t* launches_per_node,
+                               int32_t n_nodes);
+
+/* Host utility: a cosine-modulated pseudo-QMF bank (bands x taps) with a
+ * Kaiser(beta) prototype whose cutoff minimises the prototype autocorrelation
+ * at lags 2*bands*l (Lin & Vaidyanathan 1998).  analysis / synthesis:
+ * [bands][taps] float64 (may be NULL); cutoff in rad/sample (may be NULL).
+ * The paper uses such a bank inside RAVE (section 2.3) but does not specify it. */
+cc_status cc_pqmf_design(int32_t bands, int32_t taps, double beta, double* analysis,
+                         double* synthesis, double* cutoff);
+
+const char* cc_status_str(cc_status status);
+const char* cc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CACHEDCONV_H */

@@ -1,0 +1,294 @@
+"""Thin Python binding of ``include/cachedconv.h`` (argument marshalling only).
+
+Every step of the streamed model runs in the CUDA library; this module only
+converts node dictionaries and weights to the C structures and passes
+pointers.  Device buffers are torch CUDA tensors (float32, contiguous); host
+buffers are numpy float32 arrays or CPU tensors (staged by the library).
+If the compiled library is missing, every entry point raises: there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OPS = {"input": 0, "conv": 1, "convt": 2, "add": 3, "heads": 4}
+ACTS = {None: 0, "leaky": 1}
+DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
+STATUS = {0: "ok", -1: "invalid argument", -2: "bad graph", -3: "bad length",
+          -4: "no memory", -5: "cuda error", -6: "timeout", -7: "bad state"}
+
+
+class CCError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class NodeDesc(C.Structure):
+    _fields_ = [("op", C.c_int32), ("n_inputs", C.c_int32), ("inputs", C.c_int32 * 3),
+                ("c_in", C.c_int32), ("c_out", C.c_int32), ("kernel", C.c_int32),
+                ("stride", C.c_int32), ("dilation", C.c_int32), ("pad_left", C.c_int32),
+                ("pad_right", C.c_int32), ("crop", C.c_int32), ("act_in", C.c_int32),
+                ("has_bias", C.c_int32)]
+
+
+class ModelConfig(C.Structure):
+    _fields_ = [("compute", C.c_int32), ("max_streams", C.c_int32),
+                ("max_steps_per_call", C.c_int32), ("noise", C.c_int32)]
+
+
+_LIB = None
+_P = C.c_void_p
+_I32, _I64, _U64, _SZ, _DBL = C.c_int32, C.c_int64, C.c_uint64, C.c_size_t, C.c_double
+
+_SIGNATURES = {
+    "cc_model_create": [C.POINTER(NodeDesc), _I32, C.POINTER(_P), C.POINTER(_P),
+                        C.POINTER(ModelConfig), C.POINTER(_P)],
+    "cc_model_destroy": [_P],
+    "cc_model_total_delay": [_P, C.POINTER(_I64)],
+    "cc_model_io": [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)],
+    "cc_model_node_info": [_P, _I32, C.POINTER(_I64), C.POINTER(_I32), C.POINTER(_I32),
+                           C.POINTER(_I32), C.POINTER(_I32)],
+    "cc_model_state_bytes": [_P, C.POINTER(_SZ), C.POINTER(_SZ)],
+    "cc_stream_create": [_P, _U64, _P, C.POINTER(_P)],
+    "cc_stream_destroy": [_P],
+    "cc_stream_reset": [_P, _P],
+    "cc_stream_process": [_P, _P, _I64, _P, _I64, _P],
+    "cc_process_batch": [_P, C.POINTER(_P), _I32, _P, _I64, _I64, _P, _I64, _I64, _P],
+    "cc_stream_state_size": [_P, C.POINTER(_SZ)],
+    "cc_stream_get_state": [_P, _P, _SZ, _P],
+    "cc_stream_set_state": [_P, _P, _SZ, _P],
+    "cc_model_timing": [_P, _I32],
+    "cc_model_timing_read": [_P, C.POINTER(_DBL), C.POINTER(_I64), _I32],
+    "cc_pqmf_design": [_I32, _I32, _DBL, C.POINTER(_DBL), C.POINTER(_DBL), C.POINTER(_DBL)],
+    "cc_status_str": [_I32],
+    "cc_last_error": [],
+}
+
+EXPORTED = tuple(_SIGNATURES)
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load the compiled library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built ({path}); run __graft_entry__.build()")
+        L = C.CDLL(path)
+        for name, args in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_char_p if name in ("cc_status_str", "cc_last_error") else C.c_int32
+        _LIB = L
+    return _LIB
+
+
+def _check(status):
+    if status != 0:
+        raise CCError(status, lib().cc_last_error().decode())
+
+
+def _ptr(x):
+    """Data pointer of a torch tensor or numpy array (float32, contiguous)."""
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.float32 and x.flags.c_contiguous
+        return x.ctypes.data
+    assert x.dtype.__str__().endswith("float32") and x.is_contiguous()
+    return x.data_ptr()
+
+
+def _cuda_stream(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _desc(node):
+    d = NodeDesc()
+    d.op = OPS[node["op"]]
+    ins = list(node["inputs"])
+    d.n_inputs = len(ins)
+    for i, v in enumerate(ins):
+        d.inputs[i] = v
+    d.c_in, d.c_out = node["c_in"], node["c_out"]
+    d.kernel, d.stride, d.dilation = node["k"], node["stride"], node["dilation"]
+    d.pad_left, d.pad_right, d.crop = node["pad_left"], node["pad_right"], node["crop"]
+    d.act_in = ACTS[node["act_in"]]
+    d.has_bias = int(bool(node["bias"]))
+    return d
+
+
+class Model:
+    """A reconfigured model on the GPU: packed weights + stream-state arena."""
+
+    def __init__(self, nodes, params, dtype="f32", max_streams=1, max_steps_per_call=1, noise=True):
+        L = lib()
+        n = len(nodes)
+        descs = (NodeDesc * n)(*[_desc(nd) for nd in nodes])
+        self._keep = []
+        wp = (_P * n)()
+        bp = (_P * n)()
+        for i, nd in enumerate(nodes):
+            if i in params:
+                w, b = params[i]
+                w32 = np.ascontiguousarray(w, dtype=np.float32)
+                self._keep.append(w32)
+                wp[i] = w32.ctypes.data
+                if b is not None:
+                    b32 = np.ascontiguousarray(b, dtype=np.float32)
+                    self._keep.append(b32)
+                    bp[i] = b32.ctypes.data
+        cfg = ModelConfig(DTYPES[dtype], max_streams, max_steps_per_call, int(bool(noise)))
+        h = _P()
+        _check(L.cc_model_create(descs, n, wp, bp, C.byref(cfg), C.byref(h)))
+        self._keep = None
+        self.handle = h
+        self.nodes = nodes
+        self.dtype = dtype
+        self.max_streams = max_streams
+        self.max_steps_per_call = max_steps_per_call
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().cc_model_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def total_delay(self):
+        v = _I64()
+        _check(lib().cc_model_total_delay(self.handle, C.byref(v)))
+        return v.value
+
+    @property
+    def io(self):
+        a, b, c, d = _I32(), _I32(), _I32(), _I32()
+        _check(lib().cc_model_io(self.handle, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+        return dict(in_channels=a.value, out_channels=b.value, in_per_step=c.value,
+                    out_per_step=d.value)
+
+    def node_info(self, i):
+        d, da, k, u = _I64(), _I32(), _I32(), _I32()
+        al = (_I32 * 3)()
+        _check(lib().cc_model_node_info(self.handle, i, C.byref(d), C.byref(da), al, C.byref(k), C.byref(u)))
+        return dict(delay=d.value, extra_delay=da.value, align=list(al), kept=k.value,
+                    frames_per_step=u.value)
+
+    @property
+    def state_bytes(self):
+        a, b = _SZ(), _SZ()
+        _check(lib().cc_model_state_bytes(self.handle, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def stream(self, seed=0, cuda_stream=None):
+        return Stream(self, seed, cuda_stream)
+
+    def process_batch(self, streams, x, y, cuda_stream=None):
+        """x: [count][n_in][C_in], y: [count][n_out][C_out] float32 (device or host)."""
+        count = len(streams)
+        arr = (_P * count)(*[s.handle for s in streams])
+        n_in = x.shape[1]
+        n_out = y.shape[1]
+        in_stride = int(np.prod(x.shape[1:]))
+        out_stride = int(np.prod(y.shape[1:]))
+        _check(lib().cc_process_batch(self.handle, arr, count, _ptr(x), in_stride, n_in, _ptr(y),
+                                      out_stride, n_out, _cuda_stream(cuda_stream)))
+
+    def timing(self, enable):
+        _check(lib().cc_model_timing(self.handle, int(enable)))
+
+    def timing_read(self):
+        n = len(self.nodes)
+        ms = (_DBL * n)()
+        cnt = (_I64 * n)()
+        _check(lib().cc_model_timing_read(self.handle, ms, cnt, n))
+        return list(ms), list(cnt)
+
+
+class Stream:
+    """Per-stream cache state (one arena slot)."""
+
+    def __init__(self, model, seed=0, cuda_stream=None):
+        self.model = model
+        h = _P()
+        _check(lib().cc_stream_create(model.handle, seed & (2 ** 64 - 1),
+                                      _cuda_stream(cuda_stream) if _has_cuda() else None, C.byref(h)))
+        self.handle = h
+        self.seed = seed
+
+    def process(self, x, y, cuda_stream=None):
+        """x: [n_in][C_in], y: [n_out][C_out] float32 (device or host buffers)."""
+        _check(lib().cc_stream_process(self.handle, _ptr(x), x.shape[0], _ptr(y), y.shape[0],
+                                       _cuda_stream(cuda_stream)))
+
+    def reset(self, cuda_stream=None):
+        _check(lib().cc_stream_reset(self.handle, _cuda_stream(cuda_stream)))
+
+    def get_state(self, cuda_stream=None):
+        n = _SZ()
+        _check(lib().cc_stream_state_size(self.handle, C.byref(n)))
+        blob = np.empty(n.value, dtype=np.uint8)
+        _check(lib().cc_stream_get_state(self.handle, blob.ctypes.data, n.value, _cuda_stream(cuda_stream)))
+        return blob
+
+    def set_state(self, blob, cuda_stream=None):
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(lib().cc_stream_set_state(self.handle, blob.ctypes.data, blob.size, _cuda_stream(cuda_stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().cc_stream_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _has_cuda():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def pqmf_design(bands=16, taps=64, beta=5.0):
+    """Host PQMF design (analysis h, synthesis g as [bands][taps] float64, cutoff)."""
+    h = np.zeros((bands, taps))
+    g = np.zeros((bands, taps))
+    wc = _DBL()
+    _check(lib().cc_pqmf_design(bands, taps, beta, h.ctypes.data_as(C.POINTER(_DBL)),
+                                g.ctypes.data_as(C.POINTER(_DBL)), C.byref(wc)))
+    return h, g, wc.value
+
+
+def inverse_pqmf_weights(g):
+    """ConvT(bands -> 1) kernel [bands][1][taps] = bands * g_b."""
+    return (g.shape[0] * g)[:, None, :].copy()
+
+
+def pqmf_analysis_weights(g):
+    """Conv(1 -> bands) kernel [bands][1][taps] = g_b (correlating with g_b
+    filters by its time reverse, the analysis filter h_b)."""
+    return g[:, None, :].copy()

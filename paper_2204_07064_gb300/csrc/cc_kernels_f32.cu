@@ -1,0 +1,382 @@
+// FP32 kernels of the streamed model: cached convolutions (Eq. 1 over a ring
+// window, section 2.2), polyphase transposed convolutions, the aligned merges
+// (Eq. 3) and the RAVE-like heads.  The FP32 path is FFMA only: no TF32.
+#include <cstdint>
+
+#include "cc_internal.h"
+
+namespace cc {
+namespace {
+
+__device__ __forceinline__ int64_t ring_row(int64_t t, int32_t rows) {
+  int64_t r = t % rows;
+  return r < 0 ? r + rows : r;
+}
+
+__device__ __forceinline__ int32_t wrap_row(int32_t r, int32_t rows) {
+  return r >= rows ? r - rows : r;
+}
+
+__device__ __forceinline__ float activate(float x, int32_t act) {
+  return (act && x < 0.f) ? kLeakySlope * x : x;
+}
+
+template <typename T>
+__device__ __forceinline__ T* ring_ptr(const Batch& b, int32_t s, const Ring& r) {
+  return reinterpret_cast<T*>(b.arena + (int64_t)b.slots[s] * b.slot_bytes + r.off);
+}
+
+__device__ __forceinline__ int64_t steps_of(const Batch& b, int32_t s) {
+  return b.counters[b.slots[s]];
+}
+
+// Epilogue of a conv / convT GEMM element: bias, fused residual (Eq. 3 aligned
+// skip), store into the output ring or the caller's buffer.
+__device__ __forceinline__ void store_conv(const ConvArgs& a, int32_t m, int32_t n, float v) {
+  const int32_t s = n / a.ncols;
+  const int32_t j = n - s * a.ncols;
+  int32_t ch, lt;
+  if (a.phases == 1) {
+    ch = m;
+    lt = j;
+  } else {
+    const int32_t ph = m / a.cout;
+    ch = m - ph * a.cout;
+    lt = j * a.phases + ph;
+  }
+  if (a.bias) v += a.bias[ch];
+  const int64_t t = steps_of(a.batch, s) * a.out.u + lt;
+  if (a.has_skip) {
+    const float* sk = ring_ptr<const float>(a.batch, s, a.skip);
+    v += sk[ring_row(t - a.skip_A, a.skip.rows) * a.skip.chans + ch];
+  }
+  if (a.ext_out) {
+    a.ext_out[(int64_t)s * a.ext_stride + (int64_t)lt * a.cout + ch] = v;
+  } else {
+    ring_ptr<float>(a.batch, s, a.out)[ring_row(t, a.out.rows) * a.out.chans + ch] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Skinny GEMM (few columns per launch: single-stream steps).  One warp per
+// output row m, eight columns per block column; the reduction over (tap,
+// channel) is split across lanes and finished with warp shuffles.
+// ---------------------------------------------------------------------------
+constexpr int kGemvCols = 8;
+constexpr int kGemvWarps = 8;
+
+template <bool kVec>
+__global__ void __launch_bounds__(kGemvWarps * 32) k_conv_gemv_f32(const ConvArgs a) {
+  const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t m = blockIdx.y * kGemvWarps + warp;
+  const int32_t n0 = blockIdx.x * kGemvCols;
+  const int32_t N = a.batch.count * a.ncols;
+  if (m >= a.M) return;
+
+  const float* col[kGemvCols];
+  int32_t r0[kGemvCols];
+  bool ok[kGemvCols];
+#pragma unroll
+  for (int c = 0; c < kGemvCols; ++c) {
+    const int32_t n = n0 + c;
+    ok[c] = n < N;
+    col[c] = nullptr;
+    r0[c] = 0;
+    if (ok[c]) {
+      const int32_t s = n / a.ncols, j = n - s * a.ncols;
+      const int64_t t = steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist;
+      r0[c] = (int32_t)ring_row(t, a.in.rows);
+      col[c] = ring_ptr<const float>(a.batch, s, a.in);
+    }
+  }
+  float acc[kGemvCols];
+#pragma unroll
+  for (int c = 0; c < kGemvCols; ++c) acc[c] = 0.f;
+  const float* Arow = a.A + (int64_t)m * a.Kt;
+
+  if (kVec) {
+    for (int32_t tap = 0; tap < a.taps; ++tap) {
+      int32_t rowoff[kGemvCols];
+#pragma unroll
+      for (int c = 0; c < kGemvCols; ++c)
+        rowoff[c] = wrap_row(r0[c] + tap * a.dil, a.in.rows) * a.cin;
+      const float* At = Arow + tap * a.cin;
+      for (int32_t ch = lane * 4; ch < a.cin; ch += 128) {
+        const float4 w = *reinterpret_cast<const float4*>(At + ch);
+#pragma unroll
+        for (int c = 0; c < kGemvCols; ++c) {
+          if (ok[c]) {
+            const float4 x = *reinterpret_cast<const float4*>(col[c] + rowoff[c] + ch);
+            acc[c] = fmaf(w.x, activate(x.x, a.act), acc[c]);
+            acc[c] = fmaf(w.y, activate(x.y, a.act), acc[c]);
+            acc[c] = fmaf(w.z, activate(x.z, a.act), acc[c]);
+            acc[c] = fmaf(w.w, activate(x.w, a.act), acc[c]);
+          }
+        }
+      }
+    }
+  } else {
+    for (int32_t k = lane; k < a.Kt; k += 32) {
+      const int32_t tap = k / a.cin, ch = k - tap * a.cin;
+      const float w = Arow[k];
+#pragma unroll
+      for (int c = 0; c < kGemvCols; ++c) {
+        if (ok[c]) {
+          const int32_t row = wrap_row(r0[c] + tap * a.dil, a.in.rows);
+          acc[c] = fmaf(w, activate(col[c][row * a.cin + ch], a.act), acc[c]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kGemvCols; ++c) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+  }
+  float v = acc[0];
+#pragma unroll
+  for (int c = 1; c < kGemvCols; ++c)
+    if (lane == c) v = acc[c];
+  if (lane < kGemvCols && n0 + lane < N) store_conv(a, m, n0 + lane, v);
+}
+
+// ---------------------------------------------------------------------------
+// Tiled GEMM (many columns: batched streams).  64x64 tile, 16-deep K slices
+// staged through shared memory (double-buffered via registers), 4x4 outputs
+// per thread.  Requires cin % 16 == 0 so that a K slice lies inside one tap.
+// ---------------------------------------------------------------------------
+constexpr int kTM = 64, kTN = 64, kTK = 16;
+
+__global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
+  __shared__ __align__(16) float As[2][kTK][kTM + 4];
+  __shared__ __align__(16) float Bs[2][kTK][kTN + 4];
+  const int32_t tid = threadIdx.x;
+  const int32_t tx = tid & 15, ty = tid >> 4;
+  const int32_t m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  const int32_t N = a.batch.count * a.ncols;
+
+  // loader coordinates: one float4 of A (row lm) and one of B (column ln)
+  const int32_t lm = tid >> 2, lk = (tid & 3) * 4;
+  const int32_t ln = tid >> 2;
+  const bool a_ok = (m0 + lm) < a.M;
+  const float* Arow = a.A + (int64_t)(a_ok ? m0 + lm : 0) * a.Kt;
+  const bool b_ok = (n0 + ln) < N;
+  const float* bcol = nullptr;
+  int32_t br0 = 0;
+  if (b_ok) {
+    const int32_t n = n0 + ln;
+    const int32_t s = n / a.ncols, j = n - s * a.ncols;
+    const int64_t t = steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist;
+    br0 = (int32_t)ring_row(t, a.in.rows);
+    bcol = ring_ptr<const float>(a.batch, s, a.in);
+  }
+
+  auto load = [&](int32_t kt, float4& ra, float4& rb) {
+    ra = a_ok ? *reinterpret_cast<const float4*>(Arow + kt + lk) : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (b_ok) {
+      const int32_t tap = kt / a.cin, ch = kt - tap * a.cin + lk;
+      const int32_t row = wrap_row(br0 + tap * a.dil, a.in.rows);
+      const float4 x = *reinterpret_cast<const float4*>(bcol + (int64_t)row * a.cin + ch);
+      rb = make_float4(activate(x.x, a.act), activate(x.y, a.act), activate(x.z, a.act),
+                       activate(x.w, a.act));
+    } else {
+      rb = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto stash = [&](int buf, const float4& ra, const float4& rb) {
+    As[buf][lk + 0][lm] = ra.x;
+    As[buf][lk + 1][lm] = ra.y;
+    As[buf][lk + 2][lm] = ra.z;
+    As[buf][lk + 3][lm] = ra.w;
+    Bs[buf][lk + 0][ln] = rb.x;
+    Bs[buf][lk + 1][ln] = rb.y;
+    Bs[buf][lk + 2][ln] = rb.z;
+    Bs[buf][lk + 3][ln] = rb.w;
+  };
+
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+  float4 ra, rb;
+  load(0, ra, rb);
+  stash(0, ra, rb);
+  __syncthreads();
+  int buf = 0;
+  for (int32_t kt = 0; kt < a.Kt; kt += kTK) {
+    const bool more = kt + kTK < a.Kt;
+    if (more) load(kt + kTK, ra, rb);
+#pragma unroll
+    for (int k = 0; k < kTK; ++k) {
+      const float4 av = *reinterpret_cast<const float4*>(&As[buf][k][tx * 4]);
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][k][ty * 4]);
+      const float am[4] = {av.x, av.y, av.z, av.w};
+      const float bn[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(am[i], bn[j], acc[i][j]);
+    }
+    if (more) {
+      stash(buf ^ 1, ra, rb);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int32_t n = n0 + ty * 4 + j;
+    if (n >= N) continue;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int32_t m = m0 + tx * 4 + i;
+      if (m < a.M) store_conv(a, m, n, acc[i][j]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Element-wise kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+  // SplitMix64 output function (Steele, Lea & Flood 2014)
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ float noise_uniform(uint64_t seed, int64_t frame, int32_t band,
+                                               int32_t bands) {
+  const uint64_t counter = (uint64_t)(frame * bands + band);
+  const uint64_t z = splitmix_mix(seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull);
+  return (float)(z >> 40) * 0x1p-23f - 1.0f;
+}
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+__global__ void k_heads(const HeadsArgs a) {
+  const int64_t total = (int64_t)a.batch.count * a.ncols * a.bands;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t b = (int32_t)(i % a.bands);
+    const int64_t nj = i / a.bands;
+    const int32_t j = (int32_t)(nj % a.ncols);
+    const int32_t s = (int32_t)(nj / a.ncols);
+    const int64_t t = steps_of(a.batch, s) * a.out.u + j;
+    float v[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float* p = ring_ptr<const float>(a.batch, s, a.in[q]);
+      v[q] = p[ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + b];
+    }
+    float y = tanhf(v[0]) * sigmoidf_(v[1]);
+    if (a.noise) {
+      const uint64_t seed = a.batch.seeds[a.batch.slots[s]];
+      y += sigmoidf_(v[2]) * noise_uniform(seed, t - a.delay, b, a.bands);
+    }
+    if (a.ext_out)
+      a.ext_out[(int64_t)s * a.ext_stride + (int64_t)j * a.bands + b] = y;
+    else
+      ring_ptr<float>(a.batch, s, a.out)[ring_row(t, a.out.rows) * a.out.chans + b] = y;
+  }
+}
+
+__global__ void k_add(const AddArgs a) {
+  const int32_t C = a.out.chans;
+  const int64_t total = (int64_t)a.batch.count * a.ncols * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = (int32_t)(i % C);
+    const int64_t nj = i / C;
+    const int32_t j = (int32_t)(nj % a.ncols);
+    const int32_t s = (int32_t)(nj / a.ncols);
+    const int64_t t = steps_of(a.batch, s) * a.out.u + j;
+    float y = 0.f;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float* p = ring_ptr<const float>(a.batch, s, a.in[q]);
+      y += p[ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + c];
+    }
+    if (a.ext_out)
+      a.ext_out[(int64_t)s * a.ext_stride + (int64_t)j * C + c] = y;
+    else
+      ring_ptr<float>(a.batch, s, a.out)[ring_row(t, a.out.rows) * C + c] = y;
+  }
+}
+
+__global__ void k_input(const InputArgs a) {
+  const int32_t C = a.out.chans;
+  const int64_t total = (int64_t)a.batch.count * a.ncols * C;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = (int32_t)(i % C);
+    const int64_t nj = i / C;
+    const int32_t j = (int32_t)(nj % a.ncols);
+    const int32_t s = (int32_t)(nj / a.ncols);
+    const int64_t t = steps_of(a.batch, s) * a.out.u + j;
+    ring_ptr<float>(a.batch, s, a.out)[ring_row(t, a.out.rows) * C + c] =
+        a.src[(int64_t)s * a.src_stride + (int64_t)j * C + c];
+  }
+}
+
+__global__ void k_advance(const Batch b, int64_t steps) {
+  const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < b.count) const_cast<int64_t*>(b.counters)[b.slots[s]] += steps;
+}
+
+int elementwise_grid(int64_t total) {
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  return (int)(blocks < 1 ? 1 : blocks);
+}
+
+}  // namespace
+
+cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
+  const int64_t N = (int64_t)a.batch.count * a.ncols;
+  if (N <= 0) return cudaSuccess;
+  const int64_t tiles = ((a.M + kTM - 1) / kTM) * ((N + kTN - 1) / kTN);
+  if (a.cin % kTK == 0 && tiles >= 152) {
+    dim3 grid((unsigned)((N + kTN - 1) / kTN), (unsigned)((a.M + kTM - 1) / kTM));
+    k_conv_tile_f32<<<grid, 256, 0, st>>>(a);
+  } else {
+    dim3 grid((unsigned)((N + kGemvCols - 1) / kGemvCols),
+              (unsigned)((a.M + kGemvWarps - 1) / kGemvWarps));
+    if (a.cin % 4 == 0 && a.cin >= 64)
+      k_conv_gemv_f32<true><<<grid, kGemvWarps * 32, 0, st>>>(a);
+    else
+      k_conv_gemv_f32<false><<<grid, kGemvWarps * 32, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_heads(const HeadsArgs& a, cudaStream_t st) {
+  const int64_t total = (int64_t)a.batch.count * a.ncols * a.bands;
+  if (total <= 0) return cudaSuccess;
+  k_heads<<<elementwise_grid(total), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add(const AddArgs& a, cudaStream_t st) {
+  const int64_t total = (int64_t)a.batch.count * a.ncols * a.out.chans;
+  if (total <= 0) return cudaSuccess;
+  k_add<<<elementwise_grid(total), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_input(const InputArgs& a, cudaStream_t st) {
+  const int64_t total = (int64_t)a.batch.count * a.ncols * a.out.chans;
+  if (total <= 0) return cudaSuccess;
+  k_input<<<elementwise_grid(total), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const Batch& b, int64_t steps, cudaStream_t st) {
+  if (b.count <= 0) return cudaSuccess;
+  k_advance<<<(b.count + 255) / 256, 256, 0, st>>>(b, steps);
+  return cudaGetLastError();
+}
+
+}  // namespace cc

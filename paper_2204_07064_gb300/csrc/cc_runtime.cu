@@ -1,0 +1,762 @@
+// Host runtime behind include/cachedconv.h: graph validation, the
+// post-training causal reconfiguration analysis (section 3: right pad moved
+// left; Eq. 2 stride alignment; cumulated lag; Eq. 3 branch alignment), the
+// per-stream ring-buffer arena (cached padding, section 2.2), weight packing
+// and the launch chain of one buffer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/cachedconv.h"
+#include "cc_internal.h"
+#include "cc_runtime.h"
+
+namespace cc {
+
+thread_local std::string g_last_error;
+
+cc_status fail(cc_status code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CC_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(CC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));           \
+  } while (0)
+
+static int64_t gcd64(int64_t a, int64_t b) { return b == 0 ? (a < 0 ? -a : a) : gcd64(b, a % b); }
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// Planning
+// ---------------------------------------------------------------------------
+static cc_status validate_and_analyze(Model& m) {
+  const int n = (int)m.nodes.size();
+  if (n < 2) return fail(CC_ERR_BAD_GRAPH, "a model needs an input node and at least one layer");
+  for (int i = 0; i < n; ++i) {
+    NodePlan& p = m.nodes[i];
+    const cc_node_desc& d = p.d;
+    if ((d.op == CC_OP_INPUT) != (i == 0))
+      return fail(CC_ERR_BAD_GRAPH, "node %d: exactly node 0 must be the input", i);
+    const int want = d.op == CC_OP_INPUT ? 0 : d.op == CC_OP_ADD ? 2 : d.op == CC_OP_HEADS ? 3 : 1;
+    if (d.op < CC_OP_INPUT || d.op > CC_OP_HEADS)
+      return fail(CC_ERR_BAD_GRAPH, "node %d: unknown op %d", i, d.op);
+    if (d.n_inputs != want)
+      return fail(CC_ERR_BAD_GRAPH, "node %d: op %d takes %d inputs, got %d", i, d.op, want, d.n_inputs);
+    for (int q = 0; q < want; ++q)
+      if (d.inputs[q] < 0 || d.inputs[q] >= i)
+        return fail(CC_ERR_BAD_GRAPH, "node %d: input %d must be an earlier node", i, d.inputs[q]);
+    if (d.act_in != CC_ACT_NONE && d.act_in != CC_ACT_LEAKY)
+      return fail(CC_ERR_BAD_GRAPH, "node %d: unknown activation %d", i, d.act_in);
+    if (d.c_out <= 0 || d.c_in <= 0) return fail(CC_ERR_BAD_GRAPH, "node %d: channels must be > 0", i);
+    if (d.op == CC_OP_INPUT) {
+      if (d.c_in != d.c_out) return fail(CC_ERR_BAD_GRAPH, "input node: c_in != c_out");
+      p.rnum = 1;
+      p.rden = 1;
+      p.D = 0;
+      continue;
+    }
+    const NodePlan& src = m.nodes[d.inputs[0]];
+    for (int q = 0; q < want; ++q) {
+      const NodePlan& s = m.nodes[d.inputs[q]];
+      if (s.d.c_out != d.c_in)
+        return fail(CC_ERR_BAD_GRAPH, "node %d: c_in %d != producer %d's c_out %d", i, d.c_in,
+                    d.inputs[q], s.d.c_out);
+      if (s.rnum * src.rden != src.rnum * s.rden)
+        return fail(CC_ERR_BAD_GRAPH, "node %d: merged branches run at different rates", i);
+    }
+    if (d.op == CC_OP_CONV) {
+      if (d.kernel < 1 || d.stride < 1 || d.dilation < 1 || d.pad_left < 0 || d.pad_right < 0)
+        return fail(CC_ERR_BAD_GRAPH, "node %d: bad conv geometry", i);
+      const int S = d.stride, R = d.pad_right;
+      const int64_t Dc = src.D;
+      // Eq. 2, read as the minimal extra delay in [0, S)
+      p.Da = (int32_t)((S - (R + Dc) % S) % S);
+      const int64_t total = Dc + R + p.Da;
+      p.D = total / S;
+      p.hist_need = d.pad_left + d.pad_right + p.Da;
+      // streamable: the last output of a buffer may not need future input
+      if ((int64_t)(d.kernel - 1) * d.dilation > p.hist_need + S - 1)
+        return fail(CC_ERR_BAD_GRAPH,
+                    "node %d: kernel span %d exceeds its left padding %d + stride - 1 "
+                    "(the layer looks ahead; it cannot stream)",
+                    i, (d.kernel - 1) * d.dilation, p.hist_need);
+      const int64_t g = gcd64(src.rnum, src.rden * S);
+      p.rnum = src.rnum / g;
+      p.rden = src.rden * S / g;
+    } else if (d.op == CC_OP_CONVT) {
+      if (d.kernel < 1 || d.stride < 1 || d.kernel % d.stride != 0)
+        return fail(CC_ERR_BAD_GRAPH, "node %d: convt kernel must be a multiple of its stride", i);
+      if (d.crop < 0 || d.crop > d.kernel - d.stride)
+        return fail(CC_ERR_BAD_GRAPH, "node %d: convt crop must lie in [0, K - S]", i);
+      p.D = src.D * d.stride + d.crop;
+      p.hist_need = d.kernel / d.stride - 1;
+      const int64_t g = gcd64(src.rnum * d.stride, src.rden);
+      p.rnum = src.rnum * d.stride / g;
+      p.rden = src.rden / g;
+    } else {
+      if (d.c_in != d.c_out) return fail(CC_ERR_BAD_GRAPH, "node %d: merge keeps channels", i);
+      if (d.act_in != CC_ACT_NONE) return fail(CC_ERR_BAD_GRAPH, "node %d: merges take no activation", i);
+      int64_t dmax = 0;
+      for (int q = 0; q < want; ++q) dmax = std::max(dmax, m.nodes[d.inputs[q]].D);
+      for (int q = 0; q < want; ++q) p.A[q] = (int32_t)(dmax - m.nodes[d.inputs[q]].D);  // Eq. 3
+      p.D = dmax;
+      p.rnum = src.rnum;
+      p.rden = src.rden;
+    }
+  }
+  // steps: lcm of rate denominators
+  int64_t ips = 1;
+  for (auto& p : m.nodes) ips = ips / gcd64(ips, p.rden) * p.rden;
+  if (ips > (1 << 24)) return fail(CC_ERR_BAD_GRAPH, "model step of %lld input frames is too long", (long long)ips);
+  m.in_per_step = (int32_t)ips;
+  for (auto& p : m.nodes) p.u = (int32_t)(ips * p.rnum / p.rden);
+  // history each producer keeps = max over its consumers' needs
+  for (int i = 0; i < n; ++i) {
+    const cc_node_desc& d = m.nodes[i].d;
+    for (int q = 0; q < d.n_inputs; ++q) {
+      NodePlan& src = m.nodes[d.inputs[q]];
+      src.consumers.push_back(i);
+      const int need = (d.op == CC_OP_ADD || d.op == CC_OP_HEADS) ? m.nodes[i].A[q] : m.nodes[i].hist_need;
+      src.keep = std::max(src.keep, need);
+    }
+  }
+  return CC_OK;
+}
+
+// Residual adds are folded into the epilogue of the layer that finishes their
+// last branch when that layer has no other consumer and is not delayed.
+static void plan_fusion(Model& m) {
+  const int n = (int)m.nodes.size();
+  for (int i = 0; i < n; ++i) {
+    NodePlan& add = m.nodes[i];
+    if (add.d.op != CC_OP_ADD) continue;
+    for (int k = 1; k >= 0; --k) {
+      const int pk = add.d.inputs[k], other = add.d.inputs[1 - k];
+      NodePlan& prod = m.nodes[pk];
+      if ((prod.d.op == CC_OP_CONV || prod.d.op == CC_OP_CONVT) && prod.consumers.size() == 1 &&
+          add.A[k] == 0 && other < pk && prod.fused_add < 0) {
+        prod.fused_add = i;
+        prod.fused_skip = other;
+        prod.fused_skip_A = add.A[1 - k];
+        add.fused = true;
+        break;
+      }
+    }
+  }
+}
+
+static cc_status plan_arena(Model& m) {
+  size_t off = 0, state = 0;
+  const int n = (int)m.nodes.size();
+  for (int i = 0; i < n; ++i) {
+    NodePlan& p = m.nodes[i];
+    const bool needs_ring = !p.consumers.empty() && p.fused_add < 0;
+    if (!needs_ring) continue;
+    p.has_ring = true;
+    p.ring.rows = p.keep + p.u * m.max_steps;
+    p.ring.chans = p.d.c_out;
+    p.ring.u = p.u;
+    p.ring.dtype = 0;
+    p.ring.off = (int64_t)off;
+    off = align_up(off + (size_t)p.ring.rows * p.ring.chans * sizeof(float), 256);
+    state += (size_t)p.keep * p.d.c_out * sizeof(float);
+  }
+  m.slot_bytes = std::max<size_t>(align_up(off, 256), 256);
+  m.state_bytes = state;
+  return CC_OK;
+}
+
+static cc_status pack_and_upload(Model& m, const float* const* weights, const float* const* biases) {
+  for (int i = 0; i < (int)m.nodes.size(); ++i) {
+    NodePlan& p = m.nodes[i];
+    const cc_node_desc& d = p.d;
+    if (d.op != CC_OP_CONV && d.op != CC_OP_CONVT) continue;
+    if (!weights || !weights[i]) return fail(CC_ERR_INVALID_ARG, "node %d: missing weights", i);
+    if (d.has_bias && (!biases || !biases[i])) return fail(CC_ERR_INVALID_ARG, "node %d: missing bias", i);
+    std::vector<float> A;
+    const float* w = weights[i];
+    if (d.op == CC_OP_CONV) {
+      // trained [c_out][c_in][K] -> [c_out][K][c_in]: a K-slice is one tap
+      p.taps = d.kernel;
+      p.phases = 1;
+      p.M = d.c_out;
+      p.Kt = d.kernel * d.c_in;
+      A.resize((size_t)p.M * p.Kt);
+      for (int o = 0; o < d.c_out; ++o)
+        for (int c = 0; c < d.c_in; ++c)
+          for (int k = 0; k < d.kernel; ++k)
+            A[(size_t)o * p.Kt + (size_t)k * d.c_in + c] = w[((size_t)o * d.c_in + c) * d.kernel + k];
+    } else {
+      // trained [c_in][c_out][K] -> polyphase rows (phase, n), columns (tap k', c):
+      // y[qS + phase] = sum_j w[c][n][phase + jS] x[q - j], tap k' = T - 1 - j
+      const int S = d.stride, T = d.kernel / S;
+      p.taps = T;
+      p.phases = S;
+      p.M = S * d.c_out;
+      p.Kt = T * d.c_in;
+      A.resize((size_t)p.M * p.Kt);
+      for (int ph = 0; ph < S; ++ph)
+        for (int o = 0; o < d.c_out; ++o)
+          for (int kp = 0; kp < T; ++kp)
+            for (int c = 0; c < d.c_in; ++c) {
+              const int k = ph + (T - 1 - kp) * S;
+              A[(size_t)(ph * d.c_out + o) * p.Kt + (size_t)kp * d.c_in + c] =
+                  w[((size_t)c * d.c_out + o) * d.kernel + k];
+            }
+    }
+    CC_CUDA(cudaMalloc(&p.dA, A.size() * sizeof(float)));
+    CC_CUDA(cudaMemcpy(p.dA, A.data(), A.size() * sizeof(float), cudaMemcpyHostToDevice));
+    m.weight_bytes += A.size() * sizeof(float);
+    if (d.has_bias) {
+      CC_CUDA(cudaMalloc(&p.dbias, d.c_out * sizeof(float)));
+      CC_CUDA(cudaMemcpy(p.dbias, biases[i], d.c_out * sizeof(float), cudaMemcpyHostToDevice));
+    }
+  }
+  return CC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One launch chain: `steps` model steps for every stream of `batch`.
+// ---------------------------------------------------------------------------
+cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_stride, float* out,
+                           int64_t out_stride, int32_t steps, cudaStream_t st) {
+  const int n = (int)nodes.size();
+  const int last = n - 1;
+  auto begin = [&](int i) -> cc_status {
+    if (timing_on) {
+      TimingRec r;
+      r.node = i;
+      CC_CUDA(take_event(&r.start));
+      CC_CUDA(take_event(&r.stop));
+      CC_CUDA(cudaEventRecord(r.start, st));
+      timing_recs.push_back(r);
+    }
+    return CC_OK;
+  };
+  auto end = [&]() -> cc_status {
+    if (timing_on) CC_CUDA(cudaEventRecord(timing_recs.back().stop, st));
+    return CC_OK;
+  };
+  for (int i = 0; i < n; ++i) {
+    NodePlan& p = nodes[i];
+    const cc_node_desc& d = p.d;
+    if (d.op == CC_OP_INPUT) {
+      InputArgs a{};
+      a.src = in;
+      a.src_stride = in_stride;
+      a.ncols = p.u * steps;
+      a.out = p.ring;
+      a.batch = batch;
+      cc_status s = begin(i);
+      if (s) return s;
+      CC_CUDA(launch_input(a, st));
+      if ((s = end())) return s;
+      continue;
+    }
+    if (d.op == CC_OP_ADD && p.fused) continue;
+    // the node whose output this launch writes (a fused add writes for its conv)
+    const int wi = (d.op == CC_OP_CONV || d.op == CC_OP_CONVT) && p.fused_add >= 0 ? p.fused_add : i;
+    const NodePlan& w = nodes[wi];
+    float* ext = wi == last ? out : nullptr;
+    if (!ext && !w.has_ring) continue;  // dead branch
+    cc_status s = begin(i);
+    if (s) return s;
+    if (d.op == CC_OP_CONV || d.op == CC_OP_CONVT) {
+      const NodePlan& src = nodes[d.inputs[0]];
+      ConvArgs a{};
+      a.A = p.dA;
+      a.bias = p.dbias;
+      a.M = p.M;
+      a.Kt = p.Kt;
+      a.taps = p.taps;
+      a.cin = d.c_in;
+      a.act = d.act_in;
+      a.cout = d.c_out;
+      a.phases = p.phases;
+      if (d.op == CC_OP_CONV) {
+        a.dil = d.dilation;
+        a.stride = d.stride;
+        a.hist = p.hist_need;
+        a.ncols = p.u * steps;
+      } else {
+        a.dil = 1;
+        a.stride = 1;
+        a.hist = p.hist_need;
+        a.ncols = src.u * steps;
+      }
+      a.in = src.ring;
+      a.out = w.ring;
+      a.out.u = w.u;
+      a.ext_out = ext;
+      a.ext_stride = out_stride;
+      if (p.fused_add >= 0) {
+        a.has_skip = 1;
+        a.skip = nodes[p.fused_skip].ring;
+        a.skip_A = p.fused_skip_A;
+      }
+      a.batch = batch;
+      CC_CUDA(launch_conv_f32(a, st));
+    } else if (d.op == CC_OP_ADD) {
+      AddArgs a{};
+      for (int q = 0; q < 2; ++q) {
+        a.in[q] = nodes[d.inputs[q]].ring;
+        a.A[q] = p.A[q];
+      }
+      a.ncols = p.u * steps;
+      a.out = p.ring;
+      a.out.u = p.u;
+      a.out.chans = d.c_out;
+      a.ext_out = ext;
+      a.ext_stride = out_stride;
+      a.batch = batch;
+      CC_CUDA(launch_add(a, st));
+    } else {
+      HeadsArgs a{};
+      for (int q = 0; q < 3; ++q) {
+        a.in[q] = nodes[d.inputs[q]].ring;
+        a.A[q] = p.A[q];
+      }
+      a.delay = p.D;
+      a.bands = d.c_out;
+      a.ncols = p.u * steps;
+      a.noise = noise;
+      a.out = p.ring;
+      a.out.u = p.u;
+      a.ext_out = ext;
+      a.ext_stride = out_stride;
+      a.batch = batch;
+      CC_CUDA(launch_heads(a, st));
+    }
+    if ((s = end())) return s;
+  }
+  CC_CUDA(launch_advance(batch, steps, st));
+  return CC_OK;
+}
+
+cudaError_t Model::take_event(cudaEvent_t* ev) {
+  if (event_pool_used < event_pool.size()) {
+    *ev = event_pool[event_pool_used++];
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaEventCreate(ev);
+  if (e != cudaSuccess) return e;
+  event_pool.push_back(*ev);
+  ++event_pool_used;
+  return cudaSuccess;
+}
+
+Batch Model::batch_for(const int32_t* d_slots, int32_t count) const {
+  Batch b;
+  b.arena = arena;
+  b.slot_bytes = (int64_t)slot_bytes;
+  b.slots = d_slots;
+  b.counters = counters;
+  b.seeds = seeds;
+  b.count = count;
+  return b;
+}
+
+// Splits a buffer into chains of at most max_steps steps; stages host I/O.
+cc_status Model::process(const int32_t* d_slots, int32_t count, const float* in, int64_t in_stride,
+                         int64_t n_in, float* out, int64_t out_stride, int64_t n_out,
+                         cudaStream_t st) {
+  const int32_t cin = nodes.front().d.c_in, cout = nodes.back().d.c_out;
+  const int32_t ops = nodes.back().u;
+  if (n_in < 0 || n_in % in_per_step != 0)
+    return fail(CC_ERR_BAD_LENGTH, "n_in %lld is not a multiple of the model step (%d input frames)",
+                (long long)n_in, in_per_step);
+  const int64_t total_steps = n_in / in_per_step;
+  if (n_out != total_steps * ops)
+    return fail(CC_ERR_BAD_LENGTH, "n_out %lld != %lld steps x %d output frames", (long long)n_out,
+                (long long)total_steps, ops);
+  if (total_steps == 0) return CC_OK;
+  if (!in || !out) return fail(CC_ERR_INVALID_ARG, "null buffer");
+  const bool host_in = !is_device_ptr(in), host_out = !is_device_ptr(out);
+  const Batch b = batch_for(d_slots, count);
+  for (int64_t done = 0; done < total_steps; done += max_steps) {
+    const int32_t steps = (int32_t)std::min<int64_t>(max_steps, total_steps - done);
+    const float* cin_ptr = in + done * in_per_step * cin;
+    float* cout_ptr = out + done * ops * cout;
+    int64_t is = in_stride, os = out_stride;
+    if (host_in || host_out) {
+      cc_status s = ensure_staging(count);
+      if (s) return s;
+    }
+    if (host_in) {
+      const size_t width = (size_t)steps * in_per_step * cin * sizeof(float);
+      CC_CUDA(cudaMemcpy2DAsync(stage_in, width, cin_ptr, (size_t)in_stride * sizeof(float), width,
+                                count, cudaMemcpyHostToDevice, st));
+      cin_ptr = stage_in;
+      is = (int64_t)steps * in_per_step * cin;
+    }
+    float* dst = host_out ? stage_out : cout_ptr;
+    if (host_out) os = (int64_t)steps * ops * cout;
+    cc_status s = run_chain(b, cin_ptr, is, dst, os, steps, st);
+    if (s) return s;
+    if (host_out) {
+      const size_t width = (size_t)steps * ops * cout * sizeof(float);
+      CC_CUDA(cudaMemcpy2DAsync(cout_ptr, (size_t)out_stride * sizeof(float), stage_out, width, width,
+                                count, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  return CC_OK;
+}
+
+cc_status Model::ensure_staging(int32_t count) {
+  const int32_t cin = nodes.front().d.c_in, cout = nodes.back().d.c_out;
+  const size_t need_in = (size_t)count * max_steps * in_per_step * cin * sizeof(float);
+  const size_t need_out = (size_t)count * max_steps * nodes.back().u * cout * sizeof(float);
+  if (need_in > stage_in_bytes) {
+    if (stage_in) cudaFree(stage_in);
+    stage_in = nullptr;
+    CC_CUDA(cudaMalloc(&stage_in, need_in));
+    stage_in_bytes = need_in;
+  }
+  if (need_out > stage_out_bytes) {
+    if (stage_out) cudaFree(stage_out);
+    stage_out = nullptr;
+    CC_CUDA(cudaMalloc(&stage_out, need_out));
+    stage_out_bytes = need_out;
+  }
+  return CC_OK;
+}
+
+Model::~Model() {
+  for (auto& p : nodes) {
+    if (p.dA) cudaFree(p.dA);
+    if (p.dbias) cudaFree(p.dbias);
+  }
+  if (arena) cudaFree(arena);
+  if (counters) cudaFree(counters);
+  if (seeds) cudaFree(seeds);
+  if (batch_slots) cudaFree(batch_slots);
+  if (batch_slots_host) cudaFreeHost(batch_slots_host);
+  if (batch_upload_done) cudaEventDestroy(batch_upload_done);
+  if (stage_in) cudaFree(stage_in);
+  if (stage_out) cudaFree(stage_out);
+  for (auto e : event_pool) cudaEventDestroy(e);
+}
+
+}  // namespace cc
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using cc::fail;
+
+struct cc_stream {
+  cc::Model* model;
+  int32_t slot;
+  uint64_t seed;
+  int32_t* d_slot;
+};
+
+extern "C" {
+
+const char* cc_last_error(void) { return cc::g_last_error.c_str(); }
+
+const char* cc_status_str(cc_status s) {
+  switch (s) {
+    case CC_OK: return "ok";
+    case CC_ERR_INVALID_ARG: return "invalid argument";
+    case CC_ERR_BAD_GRAPH: return "bad graph";
+    case CC_ERR_BAD_LENGTH: return "bad length";
+    case CC_ERR_NO_MEMORY: return "no memory";
+    case CC_ERR_CUDA: return "cuda error";
+    case CC_ERR_TIMEOUT: return "timeout";
+    case CC_ERR_STATE: return "bad state";
+    default: return "unknown status";
+  }
+}
+
+cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const float* const* weights,
+                          const float* const* biases, const cc_model_config* config, cc_model** out) {
+  if (!nodes || !config || !out || n_nodes <= 0) return fail(CC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (config->compute != CC_F32) return fail(CC_ERR_INVALID_ARG, "compute dtype %d not built", config->compute);
+  if (config->max_streams < 0 || config->max_steps_per_call <= 0)
+    return fail(CC_ERR_INVALID_ARG, "max_streams must be >= 0 and max_steps_per_call > 0");
+  auto* m = new cc::Model();
+  m->dtype = config->compute;
+  m->max_streams = config->max_streams;
+  m->max_steps = config->max_steps_per_call;
+  m->noise = config->noise ? 1 : 0;
+  m->nodes.resize(n_nodes);
+  for (int i = 0; i < n_nodes; ++i) m->nodes[i].d = nodes[i];
+  cc_status s = cc::validate_and_analyze(*m);
+  if (!s) {
+    cc::plan_fusion(*m);
+    s = cc::plan_arena(*m);
+  }
+  if (!s && m->max_streams == 0) {  // plan only: analysis queries, no device memory
+    *out = reinterpret_cast<cc_model*>(m);
+    return CC_OK;
+  }
+  if (!s) s = cc::pack_and_upload(*m, weights, biases);
+  if (!s) {
+    const size_t arena_bytes = m->slot_bytes * (size_t)m->max_streams;
+    cudaError_t e = cudaMalloc(&m->arena, arena_bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      m->arena = nullptr;
+      s = fail(CC_ERR_NO_MEMORY, "arena of %zu bytes: %s", arena_bytes, cudaGetErrorString(e));
+    }
+  }
+  if (!s && (cudaMalloc(&m->counters, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
+             cudaMalloc(&m->seeds, sizeof(uint64_t) * m->max_streams) != cudaSuccess ||
+             cudaMalloc(&m->batch_slots, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
+             cudaMallocHost(&m->batch_slots_host, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
+             cudaEventCreateWithFlags(&m->batch_upload_done, cudaEventDisableTiming) != cudaSuccess))
+    s = fail(CC_ERR_NO_MEMORY, "model bookkeeping allocation failed");
+  if (!s && (cudaMemset(m->counters, 0, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
+             cudaMemset(m->seeds, 0, sizeof(uint64_t) * m->max_streams) != cudaSuccess))
+    s = fail(CC_ERR_CUDA, "memset failed");
+  if (s) {
+    delete m;
+    return s;
+  }
+  for (int i = m->max_streams - 1; i >= 0; --i) m->free_slots.push_back(i);
+  *out = reinterpret_cast<cc_model*>(m);
+  return CC_OK;
+}
+
+cc_status cc_model_destroy(cc_model* model) {
+  if (!model) return fail(CC_ERR_INVALID_ARG, "null model");
+  auto* m = reinterpret_cast<cc::Model*>(model);
+  if (m->max_streams > 0) cudaDeviceSynchronize();
+  delete m;
+  return CC_OK;
+}
+
+cc_status cc_model_total_delay(const cc_model* model, int64_t* out_frames) {
+  if (!model || !out_frames) return fail(CC_ERR_INVALID_ARG, "null argument");
+  *out_frames = reinterpret_cast<const cc::Model*>(model)->nodes.back().D;
+  return CC_OK;
+}
+
+cc_status cc_model_io(const cc_model* model, int32_t* in_ch, int32_t* out_ch, int32_t* in_per_step,
+                      int32_t* out_per_step) {
+  if (!model) return fail(CC_ERR_INVALID_ARG, "null model");
+  auto* m = reinterpret_cast<const cc::Model*>(model);
+  if (in_ch) *in_ch = m->nodes.front().d.c_in;
+  if (out_ch) *out_ch = m->nodes.back().d.c_out;
+  if (in_per_step) *in_per_step = m->in_per_step;
+  if (out_per_step) *out_per_step = m->nodes.back().u;
+  return CC_OK;
+}
+
+cc_status cc_model_node_info(const cc_model* model, int32_t node, int64_t* delay, int32_t* extra_delay,
+                             int32_t* align3, int32_t* kept, int32_t* fps) {
+  if (!model) return fail(CC_ERR_INVALID_ARG, "null model");
+  auto* m = reinterpret_cast<const cc::Model*>(model);
+  if (node < 0 || node >= (int)m->nodes.size()) return fail(CC_ERR_INVALID_ARG, "node %d out of range", node);
+  const auto& p = m->nodes[node];
+  if (delay) *delay = p.D;
+  if (extra_delay) *extra_delay = p.Da;
+  if (align3)
+    for (int q = 0; q < 3; ++q) align3[q] = p.A[q];
+  if (kept) *kept = p.keep;
+  if (fps) *fps = p.u;
+  return CC_OK;
+}
+
+cc_status cc_model_state_bytes(const cc_model* model, size_t* state_bytes, size_t* slot_bytes) {
+  if (!model) return fail(CC_ERR_INVALID_ARG, "null model");
+  auto* m = reinterpret_cast<const cc::Model*>(model);
+  if (state_bytes) *state_bytes = m->state_bytes;
+  if (slot_bytes) *slot_bytes = m->slot_bytes;
+  return CC_OK;
+}
+
+static cc_status zero_slot(cc::Model* m, int32_t slot, uint64_t seed, cudaStream_t st) {
+  CC_CUDA(cudaMemsetAsync(m->arena + (size_t)slot * m->slot_bytes, 0, m->slot_bytes, st));
+  CC_CUDA(cudaMemsetAsync(m->counters + slot, 0, sizeof(int64_t), st));
+  const uint64_t host_seed = seed;
+  CC_CUDA(cudaMemcpyAsync(m->seeds + slot, &host_seed, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  CC_CUDA(cudaStreamSynchronize(st));  // host_seed leaves scope on return
+  return CC_OK;
+}
+
+cc_status cc_stream_create(cc_model* model, uint64_t seed, void* cuda_stream, cc_stream** out) {
+  if (!model || !out) return fail(CC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  auto* m = reinterpret_cast<cc::Model*>(model);
+  int32_t slot;
+  {
+    std::lock_guard<std::mutex> g(m->mu);
+    if (m->free_slots.empty())
+      return fail(CC_ERR_NO_MEMORY, "arena full: all %d stream slots (%zu bytes each) are in use",
+                  m->max_streams, m->slot_bytes);
+    slot = m->free_slots.back();
+    m->free_slots.pop_back();
+  }
+  auto* s = new cc_stream{m, slot, seed, nullptr};
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  cc_status r = CC_OK;
+  if (cudaMalloc(&s->d_slot, sizeof(int32_t)) != cudaSuccess) {
+    r = fail(CC_ERR_NO_MEMORY, "stream handle allocation failed");
+  } else if (cudaMemcpy(s->d_slot, &slot, sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+    r = fail(CC_ERR_CUDA, "stream handle upload failed");
+  } else {
+    r = zero_slot(m, slot, seed, st);
+  }
+  if (r) {
+    if (s->d_slot) cudaFree(s->d_slot);
+    std::lock_guard<std::mutex> g(m->mu);
+    m->free_slots.push_back(slot);
+    delete s;
+    return r;
+  }
+  *out = s;
+  return CC_OK;
+}
+
+cc_status cc_stream_destroy(cc_stream* s) {
+  if (!s) return fail(CC_ERR_INVALID_ARG, "null stream");
+  cudaDeviceSynchronize();
+  cudaFree(s->d_slot);
+  {
+    std::lock_guard<std::mutex> g(s->model->mu);
+    s->model->free_slots.push_back(s->slot);
+    s->model->batch_slots_valid = false;
+  }
+  delete s;
+  return CC_OK;
+}
+
+cc_status cc_stream_reset(cc_stream* s, void* cuda_stream) {
+  if (!s) return fail(CC_ERR_INVALID_ARG, "null stream");
+  return zero_slot(s->model, s->slot, s->seed, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+cc_status cc_stream_process(cc_stream* s, const float* in, int64_t n_in, float* out, int64_t n_out,
+                            void* cuda_stream) {
+  if (!s) return fail(CC_ERR_INVALID_ARG, "null stream");
+  cc::Model* m = s->model;
+  const int32_t cin = m->nodes.front().d.c_in, cout = m->nodes.back().d.c_out;
+  return m->process(s->d_slot, 1, in, n_in * cin, n_in, out, n_out * cout, n_out,
+                    reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, int32_t count, const float* in,
+                           int64_t in_stride, int64_t n_in, float* out, int64_t out_stride, int64_t n_out,
+                           void* cuda_stream) {
+  if (!model || !streams || count <= 0) return fail(CC_ERR_INVALID_ARG, "null argument or empty batch");
+  auto* m = reinterpret_cast<cc::Model*>(model);
+  if (count > m->max_streams) return fail(CC_ERR_INVALID_ARG, "batch larger than max_streams");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  std::vector<int32_t> slots(count);
+  for (int i = 0; i < count; ++i) {
+    if (!streams[i] || streams[i]->model != m) return fail(CC_ERR_INVALID_ARG, "stream %d not of this model", i);
+    slots[i] = streams[i]->slot;
+  }
+  {
+    std::vector<int32_t> sorted = slots;
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return fail(CC_ERR_INVALID_ARG, "a stream appears twice in one batch");
+  }
+  if (!m->batch_slots_valid || m->batch_slots_cache != slots) {
+    // the pinned staging buffer may still feed the previous upload
+    CC_CUDA(cudaEventSynchronize(m->batch_upload_done));
+    std::memcpy(m->batch_slots_host, slots.data(), sizeof(int32_t) * count);
+    CC_CUDA(cudaMemcpyAsync(m->batch_slots, m->batch_slots_host, sizeof(int32_t) * count,
+                            cudaMemcpyHostToDevice, st));
+    CC_CUDA(cudaEventRecord(m->batch_upload_done, st));
+    m->batch_slots_cache = slots;
+    m->batch_slots_valid = true;
+  }
+  return m->process(m->batch_slots, count, in, in_stride, n_in, out, out_stride, n_out, st);
+}
+
+cc_status cc_stream_state_size(const cc_stream* s, size_t* bytes) {
+  if (!s || !bytes) return fail(CC_ERR_INVALID_ARG, "null argument");
+  *bytes = s->model->slot_bytes + 2 * sizeof(uint64_t);
+  return CC_OK;
+}
+
+cc_status cc_stream_get_state(cc_stream* s, void* blob, size_t bytes, void* cuda_stream) {
+  if (!s || !blob) return fail(CC_ERR_INVALID_ARG, "null argument");
+  cc::Model* m = s->model;
+  if (bytes != m->slot_bytes + 2 * sizeof(uint64_t)) return fail(CC_ERR_INVALID_ARG, "state blob size mismatch");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  auto* b = static_cast<char*>(blob);
+  CC_CUDA(cudaMemcpyAsync(b, m->counters + s->slot, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CC_CUDA(cudaMemcpyAsync(b + 8, m->seeds + s->slot, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+  CC_CUDA(cudaMemcpyAsync(b + 16, m->arena + (size_t)s->slot * m->slot_bytes, m->slot_bytes,
+                          cudaMemcpyDeviceToHost, st));
+  CC_CUDA(cudaStreamSynchronize(st));
+  return CC_OK;
+}
+
+cc_status cc_stream_set_state(cc_stream* s, const void* blob, size_t bytes, void* cuda_stream) {
+  if (!s || !blob) return fail(CC_ERR_INVALID_ARG, "null argument");
+  cc::Model* m = s->model;
+  if (bytes != m->slot_bytes + 2 * sizeof(uint64_t)) return fail(CC_ERR_INVALID_ARG, "state blob size mismatch");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  auto* b = static_cast<const char*>(blob);
+  CC_CUDA(cudaMemcpyAsync(m->counters + s->slot, b, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  CC_CUDA(cudaMemcpyAsync(m->seeds + s->slot, b + 8, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  CC_CUDA(cudaMemcpyAsync(m->arena + (size_t)s->slot * m->slot_bytes, b + 16, m->slot_bytes,
+                          cudaMemcpyHostToDevice, st));
+  CC_CUDA(cudaStreamSynchronize(st));
+  std::memcpy(&s->seed, b + 8, sizeof(uint64_t));
+  return CC_OK;
+}
+
+cc_status cc_model_timing(cc_model* model, int32_t enable) {
+  if (!model) return fail(CC_ERR_INVALID_ARG, "null model");
+  auto* m = reinterpret_cast<cc::Model*>(model);
+  CC_CUDA(cudaDeviceSynchronize());
+  m->timing_on = enable != 0;
+  m->timing_recs.clear();
+  m->event_pool_used = 0;
+  return CC_OK;
+}
+
+cc_status cc_model_timing_read(cc_model* model, double* ms, int64_t* launches, int32_t n_nodes) {
+  if (!model) return fail(CC_ERR_INVALID_ARG, "null model");
+  auto* m = reinterpret_cast<cc::Model*>(model);
+  if (n_nodes != (int)m->nodes.size()) return fail(CC_ERR_INVALID_ARG, "n_nodes mismatch");
+  for (int i = 0; i < n_nodes; ++i) {
+    if (ms) ms[i] = 0.0;
+    if (launches) launches[i] = 0;
+  }
+  for (auto& r : m->timing_recs) {
+    CC_CUDA(cudaEventSynchronize(r.stop));
+    float t = 0.f;
+    CC_CUDA(cudaEventElapsedTime(&t, r.start, r.stop));
+    if (ms) ms[r.node] += t;
+    if (launches) launches[r.node] += 1;
+  }
+  return CC_OK;
+}
+
+}  // extern "C"

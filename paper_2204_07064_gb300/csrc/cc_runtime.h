@@ -1,0 +1,80 @@
+// Host-side model and plan structures of the runtime (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/cachedconv.h"
+#include "cc_internal.h"
+
+namespace cc {
+
+cc_status fail(cc_status code, const char* fmt, ...);
+
+// Analysis and storage plan of one node of the reconfigured model.
+struct NodePlan {
+  cc_node_desc d{};
+  int64_t rnum = 1, rden = 1;  // frames per input frame
+  int32_t u = 0;               // frames per model step
+  int64_t D = 0;               // cumulated delay (own frames), section 3.1
+  int32_t Da = 0;              // Eq. 2 extra delay (strided conv)
+  int32_t A[3] = {0, 0, 0};    // Eq. 3 alignment per input (merges)
+  int32_t hist_need = 0;       // cached frames this layer reads before its window
+  int32_t keep = 0;            // frames of this node's output kept for consumers
+  std::vector<int> consumers;
+  bool has_ring = false;
+  Ring ring{};
+  // residual add folded into this conv's epilogue
+  int32_t fused_add = -1, fused_skip = -1, fused_skip_A = 0;
+  bool fused = false;  // (add) computed by its producer's epilogue
+  // packed GEMM view
+  int32_t M = 0, Kt = 0, taps = 0, phases = 1;
+  float* dA = nullptr;
+  float* dbias = nullptr;
+};
+
+struct TimingRec {
+  int node;
+  cudaEvent_t start, stop;
+};
+
+struct Model {
+  int32_t dtype = CC_F32;
+  int32_t max_streams = 0, max_steps = 1, noise = 1;
+  int32_t in_per_step = 1;
+  std::vector<NodePlan> nodes;
+  size_t slot_bytes = 0, state_bytes = 0, weight_bytes = 0;
+  char* arena = nullptr;
+  int64_t* counters = nullptr;
+  uint64_t* seeds = nullptr;
+  std::mutex mu;
+  std::vector<int32_t> free_slots;
+  // batch slot list (device) and its host mirror
+  int32_t* batch_slots = nullptr;
+  int32_t* batch_slots_host = nullptr;
+  cudaEvent_t batch_upload_done = nullptr;
+  std::vector<int32_t> batch_slots_cache;
+  bool batch_slots_valid = false;
+  // host I/O staging
+  float* stage_in = nullptr;
+  float* stage_out = nullptr;
+  size_t stage_in_bytes = 0, stage_out_bytes = 0;
+  // per-node timing
+  bool timing_on = false;
+  std::vector<TimingRec> timing_recs;
+  std::vector<cudaEvent_t> event_pool;
+  size_t event_pool_used = 0;
+
+  ~Model();
+  Batch batch_for(const int32_t* d_slots, int32_t count) const;
+  cc_status process(const int32_t* d_slots, int32_t count, const float* in, int64_t in_stride,
+                    int64_t n_in, float* out, int64_t out_stride, int64_t n_out, cudaStream_t st);
+  cc_status run_chain(const Batch& b, const float* in, int64_t in_stride, float* out,
+                      int64_t out_stride, int32_t steps, cudaStream_t st);
+  cc_status ensure_staging(int32_t count);
+  cudaError_t take_event(cudaEvent_t* ev);
+};
+
+}  // namespace cc

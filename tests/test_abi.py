@@ -1,0 +1,100 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads,
+exports every entry point that include/cachedconv.h declares, and its
+planning pass reproduces the oracle's section 3 analysis (Eq. 2 / Eq. 3
+delays, kept frames) without touching device memory."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import model as M
+from oracle import pqmf
+from paper_2204_07064_gb300 import api
+from paper_2204_07064_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "cachedconv.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(cclib):
+    names = _declared()
+    assert "cc_model_create" in names and "cc_stream_process" in names
+    for name in names:
+        assert hasattr(cclib, name), name
+    assert set(api.EXPORTED) <= set(names)
+
+
+def _plan(nodes):
+    return api.Model(nodes, {}, max_streams=0)
+
+
+@pytest.mark.parametrize("builder", [W.tiny_stack, W.rave_decoder, W.rave_encoder])
+def test_plan_matches_oracle_analysis(cclib, builder):
+    nodes = builder()
+    info = M.analyze(nodes)
+    keep = M.cache_frames(nodes, info)
+    m = _plan(nodes)
+    assert m.total_delay == info["delay"]
+    io = m.io
+    assert io["in_per_step"] == info["in_per_step"]
+    for i, nd in enumerate(nodes):
+        ni = m.node_info(i)
+        assert ni["delay"] == info["D"][i], (i, nd["name"])
+        assert ni["extra_delay"] == info["Da"][i]
+        assert ni["align"][:len(info["A"][i])] == info["A"][i]
+        assert ni["kept"] == keep[i]
+        assert ni["frames_per_step"] == info["rate"][i] * info["in_per_step"]
+    state, slot = m.state_bytes
+    assert state == 4 * M.cache_elements(nodes, info)
+    m.close()
+
+
+def test_decoder_plan_numbers(cclib):
+    m = _plan(W.rave_decoder())
+    assert m.total_delay == 12424
+    assert m.io == dict(in_channels=128, out_channels=1, in_per_step=1, out_per_step=2048)
+    assert m.state_bytes[0] == 27648 * 4
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda n: n.__setitem__(1, dict(n[1], inputs=[5])), "earlier node"),
+    (lambda n: n.__setitem__(1, dict(n[1], c_in=7)), "c_in"),
+    (lambda n: n.__setitem__(1, dict(n[1], pad_left=0, pad_right=0)), "looks ahead"),
+    (lambda n: n.__setitem__(0, dict(n[0], op="conv", inputs=[])), "input"),
+])
+def test_bad_graphs_are_rejected(cclib, mutate, msg):
+    nodes = W.tiny_stack()
+    mutate(nodes)
+    with pytest.raises(api.CCError) as e:
+        _plan(nodes)
+    assert e.value.status == -2 and msg in str(e.value)
+
+
+def test_bad_convt_rejected(cclib):
+    nodes = [W.input_node(4), W._node("convt", [0], 4, 4, k=6, stride=4, crop=1)]
+    with pytest.raises(api.CCError) as e:
+        _plan(nodes)
+    assert "multiple of its stride" in str(e.value)
+
+
+def test_merge_rate_mismatch_rejected(cclib):
+    nodes = [W.input_node(2), W._node("conv", [0], 2, 2, k=3, stride=2, pad_left=1, pad_right=1),
+             W._node("add", [0, 1], 2, 2, bias=False)]
+    with pytest.raises(api.CCError) as e:
+        _plan(nodes)
+    assert "rates" in str(e.value)
+
+
+def test_host_pqmf_design_matches_oracle(cclib):
+    for bands, taps, beta in [(16, 64, 5.0), (16, 128, 8.0), (4, 64, 9.0)]:
+        h, g, wc = api.pqmf_design(bands, taps, beta)
+        h2, g2, _, wc2 = pqmf.design(bands, taps, beta)
+        np.testing.assert_allclose(h, h2, atol=1e-13)
+        np.testing.assert_allclose(g, g2, atol=1e-13)
+        assert abs(wc - wc2) < 1e-12

@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+FP32 bar: max |out - oracle| <= 1e-5 x RMS(oracle) on every compared sample.
+Compared against the oracle's causal-offline model (which the oracle's own
+streaming equals exactly, section 4.2) and against the original non-causal
+model delayed by the computed latency on the interior."""
+import numpy as np
+import pytest
+
+from oracle import metrics
+from oracle import model as M
+from oracle import pqmf
+from paper_2204_07064_gb300 import api
+from paper_2204_07064_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-5
+
+
+def _assert_fp32(out, ref, what=""):
+    out = np.asarray(out, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert out.shape == ref.shape, (out.shape, ref.shape)
+    err = metrics.max_abs(ref, out)
+    bound = FP32_TOL * metrics.rms(ref)
+    assert err <= bound, f"{what}: max-abs {err:.3e} > {bound:.3e} (rms {metrics.rms(ref):.3e})"
+
+
+def _decoder(seed=1):
+    dec = W.rave_decoder()
+    p = W.init_params(dec, seed)
+    _, g, _, _ = pqmf.design(16, 64)
+    p[W.pqmf_node_index(dec)] = (pqmf.synthesis_weights(g), None)
+    return dec, p
+
+
+def _encoder(seed=4):
+    enc = W.rave_encoder()
+    p = W.init_params(enc, seed)
+    _, g, _, _ = pqmf.design(16, 64)
+    p[W.pqmf_node_index(enc)] = (pqmf.analysis_weights(g), None)
+    return enc, p
+
+
+def _run_stream(model, stream, x, partition, torch, dev):
+    outs, pos = [], 0
+    io = model.io
+    for n in partition:
+        xb = torch.tensor(x[pos:pos + n], dtype=torch.float32, device=dev).contiguous()
+        yb = torch.empty((n // io["in_per_step"] * io["out_per_step"], io["out_channels"]),
+                         dtype=torch.float32, device=dev)
+        stream.process(xb, yb)
+        outs.append(yb.cpu().numpy())
+        pos += n
+    torch.cuda.synchronize()
+    return np.concatenate(outs, axis=0)
+
+
+def test_tiny_config_32_buffers_of_512(cclib, cuda):
+    import torch
+
+    nodes = W.tiny_stack()
+    p = W.init_params(nodes, 0)
+    x = W.signal(0, 16384, 16)
+    model = api.Model(nodes, p, max_streams=2, max_steps_per_call=512)
+    assert model.total_delay == 7
+    s = model.stream(seed=0)
+    y = _run_stream(model, s, x, [512] * 32, torch, cuda)
+    yc = M.run_causal(nodes, p, x)
+    _assert_fp32(y, yc, "tiny streamed vs causal offline")
+    yo = M.run_original(nodes, p, x)
+    d, w = 7, M.warmup_frames(nodes)
+    _assert_fp32(y[d + w:], yo[w:len(yo) - d], "tiny streamed vs original delayed")
+
+
+@pytest.mark.parametrize("partition,max_steps", [([1, 1, 1, 5, 64, 3, 437, 512, 1024, 2048], 512),
+                                                 ([4096], 4096), ([3] * 40, 2)])
+def test_tiny_ragged_buffers(cclib, cuda, partition, max_steps):
+    import torch
+
+    nodes = W.tiny_stack()
+    p = W.init_params(nodes, 2)
+    total = sum(partition)
+    x = W.signal(3, total, 16)
+    model = api.Model(nodes, p, max_streams=1, max_steps_per_call=max_steps)
+    y = _run_stream(model, model.stream(), x, partition, torch, cuda)
+    _assert_fp32(y, M.run_causal(nodes, p, x), f"tiny partition {partition[:4]}...")
+
+
+def test_decoder_fp32_single_stream_full_length(cclib, cuda):
+    """The decoder workload at full length: 235 latent frames (10 s at 48 kHz),
+    one 2048-sample buffer per call, every output sample compared."""
+    import torch
+
+    dec, p = _decoder()
+    frames = 235
+    z = W.signal(1, frames, 128)
+    model = api.Model(dec, p, max_streams=1, max_steps_per_call=1)
+    assert model.total_delay == 12424
+    s = model.stream(seed=11)
+    y = _run_stream(model, s, z, [1] * frames, torch, cuda)
+    yc = M.run_causal(dec, p, z, seed=11)
+    _assert_fp32(y, yc, "decoder streamed vs causal offline")
+    yo = M.run_original(dec, p, z, seed=11)
+    d, w = 12424, M.warmup_frames(dec)
+    _assert_fp32(y[d + w:], yo[w:len(yo) - d], "decoder vs original delayed")
+
+
+def test_decoder_buffer_size_invariance(cclib, cuda):
+    """Section 4.2: the streamed output does not depend on the buffer sizes."""
+    import torch
+
+    dec, p = _decoder(3)
+    z = W.signal(7, 12, 128)
+    yc = M.run_causal(dec, p, z, seed=5)
+    for part, ms in (([2, 1, 3, 4, 2], 2), ([12], 4), ([5, 7], 3)):
+        model = api.Model(dec, p, max_streams=1, max_steps_per_call=ms)
+        y = _run_stream(model, model.stream(seed=5), z, part, torch, cuda)
+        _assert_fp32(y, yc, f"decoder partition {part}")
+        model.close()
+
+
+def test_decoder_batched_streams_match_oracle_and_alone(cclib, cuda):
+    import torch
+
+    dec, p = _decoder(4)
+    count, steps = 6, 5
+    seeds = W.stream_seeds(21, count)
+    zs = [W.signal(100 + i, steps, 128) for i in range(count)]
+    model = api.Model(dec, p, max_streams=count + 1, max_steps_per_call=1)
+    streams = [model.stream(seed=s) for s in seeds]
+    outs = np.zeros((count, steps * 2048, 1))
+    for t in range(steps):
+        x = torch.tensor(np.stack([z[t:t + 1] for z in zs]), dtype=torch.float32, device=cuda)
+        y = torch.empty((count, 2048, 1), dtype=torch.float32, device=cuda)
+        model.process_batch(streams, x, y)
+        outs[:, t * 2048:(t + 1) * 2048] = y.cpu().numpy()
+    alone = model.stream(seed=seeds[2])
+    ya = _run_stream(model, alone, zs[2], [1] * steps, torch, cuda)
+    for i in range(count):
+        _assert_fp32(outs[i], M.run_causal(dec, p, zs[i], seed=seeds[i]), f"batched stream {i}")
+    _assert_fp32(ya, outs[2], "alone vs in the batch")
+
+
+def test_encoder_strided_and_pqmf_analysis(cclib, cuda):
+    import torch
+
+    enc, p = _encoder()
+    x = W.signal(4, 2048 * 9, 1, std=0.1)
+    model = api.Model(enc, p, max_streams=1, max_steps_per_call=2)
+    assert model.total_delay == 3
+    y = _run_stream(model, model.stream(), x, [2048, 4096, 2048 * 3, 2048 * 3], torch, cuda)
+    yc = M.run_causal(enc, p, x)
+    _assert_fp32(y, yc, "encoder streamed vs causal offline")
+
+
+def test_checkpoint_resume_and_reset(cclib, cuda):
+    import torch
+
+    dec, p = _decoder(5)
+    z = W.signal(9, 8, 128)
+    model = api.Model(dec, p, max_streams=3, max_steps_per_call=2)
+    a = model.stream(seed=3)
+    first = _run_stream(model, a, z[:4], [2, 2], torch, cuda)
+    blob = a.get_state()
+    rest_a = _run_stream(model, a, z[4:], [1, 3], torch, cuda)
+    b = model.stream(seed=999)
+    b.set_state(blob)
+    rest_b = _run_stream(model, b, z[4:], [2, 2], torch, cuda)
+    _assert_fp32(rest_b, rest_a, "restored stream")
+    a.reset()
+    again = _run_stream(model, a, z[:4], [4], torch, cuda)
+    _assert_fp32(again, first, "after reset")
+
+
+def test_host_buffers_match_device_buffers(cclib, cuda):
+    import torch
+
+    nodes = W.tiny_stack()
+    p = W.init_params(nodes, 6)
+    x = W.signal(6, 2048, 16).astype(np.float32)
+    model = api.Model(nodes, p, max_streams=2, max_steps_per_call=1024)
+    s1, s2 = model.stream(), model.stream()
+    yh = np.zeros((2048, 16), np.float32)
+    s1.process(x, yh)
+    torch.cuda.synchronize()
+    yd = _run_stream(model, s2, x, [2048], torch, cuda)
+    np.testing.assert_array_equal(yh, yd)
+
+
+def test_errors(cclib, cuda):
+    import torch
+
+    nodes = W.rave_encoder()
+    p = W.init_params(nodes, 0)
+    _, g, _, _ = pqmf.design(16, 64)
+    p[1] = (pqmf.analysis_weights(g), None)
+    model = api.Model(nodes, p, max_streams=1, max_steps_per_call=1)
+    s = model.stream()
+    with pytest.raises(api.CCError) as e:  # not a whole model step
+        s.process(torch.zeros((1000, 1), device=cuda), torch.zeros((0, 128), device=cuda))
+    assert e.value.status == -3
+    with pytest.raises(api.CCError) as e:  # wrong output length
+        s.process(torch.zeros((2048, 1), device=cuda), torch.zeros((2, 128), device=cuda))
+    assert e.value.status == -3
+    with pytest.raises(api.CCError) as e:  # arena full: admission by cache memory
+        model.stream()
+    assert e.value.status == -4
+    s.close()
+    model.stream().close()  # the slot came back
+    # empty buffers are a no-op
+    s2 = model.stream()
+    s2.process(torch.zeros((0, 1), device=cuda), torch.zeros((0, 128), device=cuda))

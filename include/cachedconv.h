@@ -109,6 +109,8 @@ typedef struct cc_stream cc_stream;
 cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes,
                           const float* const* weights, const float* const* biases,
                           const cc_model_config* config, cc_model** out);
+/* Frees the model, its arena and every stream still created on it (their
+ * handles become invalid). */
 cc_status cc_model_destroy(cc_model* model);
 
 /* Total latency of the reconfigured model, in output frames: the cumulated

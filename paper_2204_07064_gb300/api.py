@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -154,6 +155,7 @@ class Model:
         h = _P()
         _check(L.cc_model_create(descs, n, wp, bp, C.byref(cfg), C.byref(h)))
         self._keep = None
+        self._streams = weakref.WeakSet()
         self.handle = h
         self.nodes = nodes
         self.dtype = dtype
@@ -162,6 +164,8 @@ class Model:
 
     def close(self):
         if getattr(self, "handle", None):
+            for s in list(self._streams):  # the library frees them with the model
+                s.handle = None
             _check(lib().cc_model_destroy(self.handle))
             self.handle = None
 
@@ -232,6 +236,7 @@ class Stream:
                                       _cuda_stream(cuda_stream) if _has_cuda() else None, C.byref(h)))
         self.handle = h
         self.seed = seed
+        model._streams.add(self)
 
     def process(self, x, y, cuda_stream=None):
         """x: [n_in][C_in], y: [n_out][C_out] float32 (device or host buffers)."""
@@ -253,9 +258,9 @@ class Stream:
         _check(lib().cc_stream_set_state(self.handle, blob.ctypes.data, blob.size, _cuda_stream(cuda_stream)))
 
     def close(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and getattr(self.model, "handle", None):
             _check(lib().cc_stream_destroy(self.handle))
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:

@@ -551,6 +551,11 @@ cc_status cc_model_destroy(cc_model* model) {
   if (!model) return fail(CC_ERR_INVALID_ARG, "null model");
   auto* m = reinterpret_cast<cc::Model*>(model);
   if (m->max_streams > 0) cudaDeviceSynchronize();
+  for (cc_stream* s : m->live_streams) {  // streams die with their model
+    if (s->d_slot) cudaFree(s->d_slot);
+    delete s;
+  }
+  m->live_streams.clear();
   delete m;
   return CC_OK;
 }
@@ -634,6 +639,10 @@ cc_status cc_stream_create(cc_model* model, uint64_t seed, void* cuda_stream, cc
     delete s;
     return r;
   }
+  {
+    std::lock_guard<std::mutex> g(m->mu);
+    m->live_streams.push_back(s);
+  }
   *out = s;
   return CC_OK;
 }
@@ -643,9 +652,12 @@ cc_status cc_stream_destroy(cc_stream* s) {
   cudaDeviceSynchronize();
   cudaFree(s->d_slot);
   {
-    std::lock_guard<std::mutex> g(s->model->mu);
-    s->model->free_slots.push_back(s->slot);
-    s->model->batch_slots_valid = false;
+    cc::Model* m = s->model;
+    std::lock_guard<std::mutex> g(m->mu);
+    m->free_slots.push_back(s->slot);
+    m->batch_slots_valid = false;
+    m->live_streams.erase(std::remove(m->live_streams.begin(), m->live_streams.end(), s),
+                          m->live_streams.end());
   }
   delete s;
   return CC_OK;

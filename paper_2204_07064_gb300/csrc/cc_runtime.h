@@ -51,6 +51,7 @@ struct Model {
   uint64_t* seeds = nullptr;
   std::mutex mu;
   std::vector<int32_t> free_slots;
+  std::vector<cc_stream*> live_streams;  // destroyed with the model
   // batch slot list (device) and its host mirror
   int32_t* batch_slots = nullptr;
   int32_t* batch_slots_host = nullptr;

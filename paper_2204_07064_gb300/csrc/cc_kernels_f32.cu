@@ -141,97 +141,143 @@ __global__ void __launch_bounds__(kGemvWarps * 32) k_conv_gemv_f32(const ConvArg
 }
 
 // ---------------------------------------------------------------------------
-// Tiled GEMM (many columns: batched streams).  64x64 tile, 16-deep K slices
-// staged through shared memory (double-buffered via registers), 4x4 outputs
-// per thread.  Requires cin % 16 == 0 so that a K slice lies inside one tap.
+// Tiled GEMM (many columns: batched streams).  BM x BN tile, BK-deep K slices
+// staged through shared memory (double-buffered via registers), 256 threads
+// as a 16 x 16 grid, each computing (BM/16) x (BN/16) outputs.  With 8x8
+// outputs a thread takes two groups of four rows (and columns) half a tile
+// apart, so its float4 shared-memory reads stay conflict-free.
+// Requires cin % BK == 0 so that a K slice lies inside one tap.
 // ---------------------------------------------------------------------------
-constexpr int kTM = 64, kTN = 64, kTK = 16;
-
+template <int BM, int BN, int BK>
 __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
-  __shared__ __align__(16) float As[2][kTK][kTM + 4];
-  __shared__ __align__(16) float Bs[2][kTK][kTN + 4];
+  constexpr int TM = BM / 16, TN = BN / 16;  // 4 or 8
+  constexpr int GM = TM / 4, GN = TN / 4;    // groups of four
+  constexpr int A4 = BM * BK / 4 / 256, B4 = BN * BK / 4 / 256;  // float4 per thread
+  static_assert(A4 >= 1 && B4 >= 1, "tile too small for 256 threads");
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
   const int32_t tid = threadIdx.x;
   const int32_t tx = tid & 15, ty = tid >> 4;
-  const int32_t m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  const int32_t m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int32_t N = a.batch.count * a.ncols;
 
-  // loader coordinates: one float4 of A (row lm) and one of B (column ln)
-  const int32_t lm = tid >> 2, lk = (tid & 3) * 4;
-  const int32_t ln = tid >> 2;
-  const bool a_ok = (m0 + lm) < a.M;
-  const float* Arow = a.A + (int64_t)(a_ok ? m0 + lm : 0) * a.Kt;
-  const bool b_ok = (n0 + ln) < N;
-  const float* bcol = nullptr;
-  int32_t br0 = 0;
-  if (b_ok) {
-    const int32_t n = n0 + ln;
-    const int32_t s = n / a.ncols, j = n - s * a.ncols;
-    const int64_t t = steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist;
-    br0 = (int32_t)ring_row(t, a.in.rows);
-    bcol = ring_ptr<const float>(a.batch, s, a.in);
+  // loader coordinates
+  int32_t lrowA[A4], lkA[A4], lrowB[B4], lkB[B4];
+  const float* Arow[A4];
+  bool a_ok[A4], b_ok[B4];
+  const float* bcol[B4];
+  int32_t br0[B4];
+#pragma unroll
+  for (int q = 0; q < A4; ++q) {
+    const int f = tid + q * 256;
+    lrowA[q] = f / (BK / 4);
+    lkA[q] = (f % (BK / 4)) * 4;
+    a_ok[q] = (m0 + lrowA[q]) < a.M;
+    Arow[q] = a.A + (int64_t)(a_ok[q] ? m0 + lrowA[q] : 0) * a.Kt;
   }
-
-  auto load = [&](int32_t kt, float4& ra, float4& rb) {
-    ra = a_ok ? *reinterpret_cast<const float4*>(Arow + kt + lk) : make_float4(0.f, 0.f, 0.f, 0.f);
-    if (b_ok) {
-      const int32_t tap = kt / a.cin, ch = kt - tap * a.cin + lk;
-      const int32_t row = wrap_row(br0 + tap * a.dil, a.in.rows);
-      const float4 x = *reinterpret_cast<const float4*>(bcol + (int64_t)row * a.cin + ch);
-      rb = make_float4(activate(x.x, a.act), activate(x.y, a.act), activate(x.z, a.act),
-                       activate(x.w, a.act));
-    } else {
-      rb = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < B4; ++q) {
+    const int f = tid + q * 256;
+    lrowB[q] = f / (BK / 4);
+    lkB[q] = (f % (BK / 4)) * 4;
+    const int32_t n = n0 + lrowB[q];
+    b_ok[q] = n < N;
+    bcol[q] = nullptr;
+    br0[q] = 0;
+    if (b_ok[q]) {
+      const int32_t s = n / a.ncols, j = n - s * a.ncols;
+      const int64_t t = steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist;
+      br0[q] = (int32_t)ring_row(t, a.in.rows);
+      bcol[q] = ring_ptr<const float>(a.batch, s, a.in);
+    }
+  }
+  float4 ra[A4], rb[B4];
+  auto load = [&](int32_t kt) {
+    const int32_t tap = kt / a.cin, chb = kt - tap * a.cin;
+#pragma unroll
+    for (int q = 0; q < A4; ++q)
+      ra[q] = a_ok[q] ? *reinterpret_cast<const float4*>(Arow[q] + kt + lkA[q])
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < B4; ++q) {
+      if (b_ok[q]) {
+        const int32_t row = wrap_row(br0[q] + tap * a.dil, a.in.rows);
+        const float4 x =
+            *reinterpret_cast<const float4*>(bcol[q] + (int64_t)row * a.cin + chb + lkB[q]);
+        rb[q] = make_float4(activate(x.x, a.act), activate(x.y, a.act), activate(x.z, a.act),
+                            activate(x.w, a.act));
+      } else {
+        rb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
   };
-  auto stash = [&](int buf, const float4& ra, const float4& rb) {
-    As[buf][lk + 0][lm] = ra.x;
-    As[buf][lk + 1][lm] = ra.y;
-    As[buf][lk + 2][lm] = ra.z;
-    As[buf][lk + 3][lm] = ra.w;
-    Bs[buf][lk + 0][ln] = rb.x;
-    Bs[buf][lk + 1][ln] = rb.y;
-    Bs[buf][lk + 2][ln] = rb.z;
-    Bs[buf][lk + 3][ln] = rb.w;
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < A4; ++q) {
+      As[buf][lkA[q] + 0][lrowA[q]] = ra[q].x;
+      As[buf][lkA[q] + 1][lrowA[q]] = ra[q].y;
+      As[buf][lkA[q] + 2][lrowA[q]] = ra[q].z;
+      As[buf][lkA[q] + 3][lrowA[q]] = ra[q].w;
+    }
+#pragma unroll
+    for (int q = 0; q < B4; ++q) {
+      Bs[buf][lkB[q] + 0][lrowB[q]] = rb[q].x;
+      Bs[buf][lkB[q] + 1][lrowB[q]] = rb[q].y;
+      Bs[buf][lkB[q] + 2][lrowB[q]] = rb[q].z;
+      Bs[buf][lkB[q] + 3][lrowB[q]] = rb[q].w;
+    }
   };
 
-  float acc[4][4];
+  float acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
 
-  float4 ra, rb;
-  load(0, ra, rb);
-  stash(0, ra, rb);
+  load(0);
+  stash(0);
   __syncthreads();
   int buf = 0;
-  for (int32_t kt = 0; kt < a.Kt; kt += kTK) {
-    const bool more = kt + kTK < a.Kt;
-    if (more) load(kt + kTK, ra, rb);
+  for (int32_t kt = 0; kt < a.Kt; kt += BK) {
+    const bool more = kt + BK < a.Kt;
+    if (more) load(kt + BK);
 #pragma unroll
-    for (int k = 0; k < kTK; ++k) {
-      const float4 av = *reinterpret_cast<const float4*>(&As[buf][k][tx * 4]);
-      const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][k][ty * 4]);
-      const float am[4] = {av.x, av.y, av.z, av.w};
-      const float bn[4] = {bv.x, bv.y, bv.z, bv.w};
+    for (int k = 0; k < BK; ++k) {
+      float am[TM], bn[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int g = 0; g < GM; ++g) {
+        const float4 v = *reinterpret_cast<const float4*>(&As[buf][k][g * (BM / 2) + tx * 4]);
+        am[g * 4 + 0] = v.x;
+        am[g * 4 + 1] = v.y;
+        am[g * 4 + 2] = v.z;
+        am[g * 4 + 3] = v.w;
+      }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(am[i], bn[j], acc[i][j]);
+      for (int g = 0; g < GN; ++g) {
+        const float4 v = *reinterpret_cast<const float4*>(&Bs[buf][k][g * (BN / 2) + ty * 4]);
+        bn[g * 4 + 0] = v.x;
+        bn[g * 4 + 1] = v.y;
+        bn[g * 4 + 2] = v.z;
+        bn[g * 4 + 3] = v.w;
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(am[i], bn[j], acc[i][j]);
     }
     if (more) {
-      stash(buf ^ 1, ra, rb);
+      stash(buf ^ 1);
       __syncthreads();
       buf ^= 1;
     }
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int32_t n = n0 + ty * 4 + j;
+  for (int j = 0; j < TN; ++j) {
+    const int32_t n = n0 + (j / 4) * (BN / 2) + ty * 4 + (j & 3);
     if (n >= N) continue;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int32_t m = m0 + tx * 4 + i;
+    for (int i = 0; i < TM; ++i) {
+      const int32_t m = m0 + (i / 4) * (BM / 2) + tx * 4 + (i & 3);
       if (m < a.M) store_conv(a, m, n, acc[i][j]);
     }
   }
@@ -337,10 +383,13 @@ int elementwise_grid(int64_t total) {
 cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   if (N <= 0) return cudaSuccess;
-  const int64_t tiles = ((a.M + kTM - 1) / kTM) * ((N + kTN - 1) / kTN);
-  if (a.cin % kTK == 0 && tiles >= 152) {
-    dim3 grid((unsigned)((N + kTN - 1) / kTN), (unsigned)((a.M + kTM - 1) / kTM));
-    k_conv_tile_f32<<<grid, 256, 0, st>>>(a);
+  auto tiles = [&](int bm, int bn) { return ((a.M + bm - 1) / bm) * ((N + bn - 1) / bn); };
+  if (a.cin % 8 == 0 && a.M >= 128 && tiles(128, 128) >= 2 * 152) {
+    dim3 grid((unsigned)((N + 127) / 128), (unsigned)((a.M + 127) / 128));
+    k_conv_tile_f32<128, 128, 8><<<grid, 256, 0, st>>>(a);
+  } else if (a.cin % 16 == 0 && N >= 32) {
+    dim3 grid((unsigned)((N + 63) / 64), (unsigned)((a.M + 63) / 64));
+    k_conv_tile_f32<64, 64, 16><<<grid, 256, 0, st>>>(a);
   } else {
     dim3 grid((unsigned)((N + kGemvCols - 1) / kGemvCols),
               (unsigned)((a.M + kGemvWarps - 1) / kGemvWarps));

@@ -212,3 +212,26 @@ def test_errors(cclib, cuda):
     # empty buffers are a no-op
     s2 = model.stream()
     s2.process(torch.zeros((0, 1), device=cuda), torch.zeros((0, 128), device=cuda))
+
+
+@pytest.mark.parametrize("dtype", ["f32"])
+def test_decoder_full_batch_sampled_streams(cclib, cuda, dtype):
+    """The benchmark's launch configuration (256 streams x one 2048-sample
+    buffer per step, max one step per call): every stream runs on the GPU,
+    a sample of streams is checked sample-by-sample against the oracle."""
+    import torch
+
+    dec, p = _decoder(1)
+    count, steps = 256, 3
+    seeds = W.stream_seeds(1000, count)
+    z = np.random.default_rng(0).standard_normal((steps, count, 1, 128))
+    model = api.Model(dec, p, dtype=dtype, max_streams=count, max_steps_per_call=1)
+    streams = [model.stream(seed=s) for s in seeds]
+    y = torch.empty((count, 2048, 1), dtype=torch.float32, device=cuda)
+    outs = np.zeros((count, steps * 2048))
+    for t in range(steps):
+        model.process_batch(streams, torch.tensor(z[t], dtype=torch.float32, device=cuda), y)
+        outs[:, t * 2048:(t + 1) * 2048] = y[:, :, 0].cpu().numpy()
+    for i in (0, 77, 255):
+        ref = M.run_causal(dec, p, z[:, i, 0, :], seed=seeds[i])[:, 0]
+        _assert_fp32(outs[i], ref, f"stream {i} of {count}")

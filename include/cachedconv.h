@@ -169,6 +169,13 @@ cc_status cc_stream_get_state(cc_stream* stream, void* host_blob, size_t bytes, 
 cc_status cc_stream_set_state(cc_stream* stream, const void* host_blob, size_t bytes,
                               void* cuda_stream);
 
+/* Synchronises the device and reports whether any tensor-core pipeline wait
+ * of this model gave up since the last call (TIMEOUT, *code = bit set of the
+ * waiting roles: 1 producer, 2 epilogue, 4 MMA issuer); clears the record.
+ * Such a wait is bounded (2 s) so that a stalled pipeline returns instead of
+ * hanging the GPU; the affected outputs are then undefined. */
+cc_status cc_model_device_status(cc_model* model, int32_t* code);
+
 /* Per-node device timing (CUDA events recorded around every launch on the
  * launching stream).  enable=1 starts accumulating; cc_model_timing_read
  * synchronises and returns, per node, the summed milliseconds and launch count

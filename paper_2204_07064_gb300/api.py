@@ -64,6 +64,7 @@ _SIGNATURES = {
     "cc_stream_state_size": [_P, C.POINTER(_SZ)],
     "cc_stream_get_state": [_P, _P, _SZ, _P],
     "cc_stream_set_state": [_P, _P, _SZ, _P],
+    "cc_model_device_status": [_P, C.POINTER(_I32)],
     "cc_model_timing": [_P, _I32],
     "cc_model_timing_read": [_P, C.POINTER(_DBL), C.POINTER(_I64), _I32],
     "cc_pqmf_design": [_I32, _I32, _DBL, C.POINTER(_DBL), C.POINTER(_DBL), C.POINTER(_DBL)],
@@ -214,6 +215,12 @@ class Model:
         out_stride = int(np.prod(y.shape[1:]))
         _check(lib().cc_process_batch(self.handle, arr, count, _ptr(x), in_stride, n_in, _ptr(y),
                                       out_stride, n_out, _cuda_stream(cuda_stream)))
+
+    def device_status(self):
+        """Raises CCError(TIMEOUT) if a bounded device wait gave up since the last call."""
+        code = _I32()
+        _check(lib().cc_model_device_status(self.handle, C.byref(code)))
+        return code.value
 
     def timing(self, enable):
         _check(lib().cc_model_timing(self.handle, int(enable)))

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcachedconv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["cc_runtime.cu", "cc_kernels_f32.cu", "cc_pqmf.cpp"]
+SOURCES = ["cc_runtime.cu", "cc_kernels_f32.cu", "cc_kernels_tc.cu", "cc_pqmf.cpp"]
 
 
 def _nvcc():
@@ -47,7 +47,7 @@ def _stale(target, deps):
 def build(verbose=False, force=False, ptxas_verbose=False):
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "cachedconv.h"))
     objs = []
     jobs = []

@@ -1,0 +1,56 @@
+// Device helpers shared by the kernels: ring addressing, activation and the
+// multi-view output store.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "cc_internal.h"
+
+namespace cc {
+
+__device__ __forceinline__ int64_t ring_row(int64_t t, int32_t rows) {
+  int64_t r = t % rows;
+  return r < 0 ? r + rows : r;
+}
+
+__device__ __forceinline__ int32_t wrap_row(int32_t r, int32_t rows) {
+  return r >= rows ? r - rows : r;
+}
+
+__device__ __forceinline__ float leaky(float x) { return x < 0.f ? kLeakySlope * x : x; }
+
+__device__ __forceinline__ float activate(float x, int32_t act) { return act ? leaky(x) : x; }
+
+__device__ __forceinline__ char* slot_base(const Batch& b, int32_t s) {
+  return b.arena + (int64_t)b.slots[s] * b.slot_bytes;
+}
+
+template <typename T>
+__device__ __forceinline__ T* ring_ptr(const Batch& b, int32_t s, const Ring& r) {
+  return reinterpret_cast<T*>(slot_base(b, s) + r.off);
+}
+
+__device__ __forceinline__ int64_t steps_of(const Batch& b, int32_t s) {
+  return b.counters[b.slots[s]];
+}
+
+__device__ __forceinline__ void store_lp(char* base, const Ring& r, int64_t row, int32_t ch, float x) {
+  if (r.dtype == kDtBF16)
+    reinterpret_cast<__nv_bfloat16*>(base + r.off)[row * r.chans + ch] = __float2bfloat16_rn(x);
+  else
+    reinterpret_cast<__half*>(base + r.off)[row * r.chans + ch] = __float2half_rn(x);
+}
+
+// Writes value v of channel ch at absolute time t (local time lt within this
+// call) of stream s into every view of `o`.
+__device__ __forceinline__ void store_views(const Batch& b, int32_t s, const OutViews& o, int64_t t,
+                                            int32_t lt, int32_t ch, int32_t chans, float v) {
+  char* base = slot_base(b, s);
+  if (o.ext) o.ext[(int64_t)s * o.ext_stride + (int64_t)lt * chans + ch] = v;
+  if (o.f32.rows)
+    reinterpret_cast<float*>(base + o.f32.off)[ring_row(t, o.f32.rows) * o.f32.chans + ch] = v;
+  if (o.lp[0].rows) store_lp(base, o.lp[0], ring_row(t, o.lp[0].rows), ch, v);
+  if (o.lp[1].rows) store_lp(base, o.lp[1], ring_row(t, o.lp[1].rows), ch, leaky(v));
+}
+
+}  // namespace cc

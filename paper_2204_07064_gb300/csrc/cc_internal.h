@@ -8,21 +8,37 @@
 // the previous call's tail, still in place, so no copy is ever made.  Rings
 // start zeroed, which is the zero left padding of the causal model (section 3).
 // A stream's absolute time at a node is (steps done) x (frames per step).
+//
+// A node's output may be kept in up to three views: FP32 as computed (read
+// by residual merges, heads and FP32 layers) and low-precision copies with
+// no activation or with LeakyReLU already applied (read by tensor-core
+// layers, which stage them into shared memory unchanged).
 #pragma once
-#include <cstdint>
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 namespace cc {
 
 constexpr float kLeakySlope = 0.2f;
 
-// Where one stream's frames of one node live.
+enum : int32_t { kDtF32 = 0, kDtBF16 = 1, kDtF16 = 2 };
+
+// Where one stream's frames of one view of one node live.  rows == 0: absent.
 struct Ring {
-  int64_t off;   // byte offset inside a slot
-  int32_t rows;  // R
-  int32_t chans; // C
-  int32_t u;     // frames per model step at this node
-  int32_t dtype; // 0 f32, 1 bf16, 2 f16
+  int64_t off;    // byte offset inside a slot
+  int32_t rows;   // R
+  int32_t chans;  // C
+  int32_t u;      // frames per model step at this node
+  int32_t dtype;  // kDt*
+};
+
+// Every destination of a layer's output.
+struct OutViews {
+  Ring f32;            // FP32 as computed
+  Ring lp[2];          // low precision: [0] as computed, [1] LeakyReLU applied
+  float* ext;          // caller's buffer (last node): stream s at ext + s*ext_stride
+  int64_t ext_stride;  //   + local_time*C + channel
 };
 
 // Streams of one launch: slot indices into the arena + per-slot counters.
@@ -43,45 +59,56 @@ struct Batch {
 // ConvT (polyphase): row m = phase*cout + n is channel n at time
 //   t0_out + j*phases + phase.
 struct ConvArgs {
-  const float* A;    // packed FP32 weights [M][Kt], Kt = taps*cin
-  const float* bias; // [cout] or null
+  const float* A;     // packed FP32 weights [M][Kt], Kt = taps*cin
+  const float* bias;  // [cout] or null
   int32_t M, Kt, taps, cin, dil, stride, hist, ncols, act;
-  int32_t cout, phases; // phases = 1 for conv, S for convt
-  Ring in, out;
-  float* ext_out;       // if non-null the output goes here: stream s at
-  int64_t ext_stride;   //   ext_out + s*ext_stride + local_time*cout + n
-  int32_t has_skip;     // fused residual add: + skip[time - skip_A]
+  int32_t cout, phases;  // phases = 1 for conv, S for convt
+  int32_t out_u;         // output frames per step
+  Ring in;               // FP32 view of the input
+  OutViews out;
+  int32_t has_skip;  // fused residual add: + skip[time - skip_A] (FP32 view)
   int32_t skip_A;
   Ring skip;
   Batch batch;
 };
 
+// Tensor-core form of ConvArgs: A is low precision [Mpad][Kt] in a TMA
+// tensor map (128-row boxes, 128-byte swizzle), row m scaled by scale[m];
+// B is read from the input's low-precision view (activation pre-applied).
+struct TcArgs {
+  const float* scale;  // [Mpad]
+  const float* bias;   // [cout] or null
+  int32_t M, Kt, taps, cin, dil, stride, hist, ncols, cout, phases, out_u;
+  Ring in;
+  OutViews out;
+  int32_t has_skip, skip_A;
+  Ring skip;
+  Batch batch;
+  int32_t* err;  // device error word: set when a bounded wait gives up
+};
+
 struct HeadsArgs {
   Ring in[3];
-  int32_t A[3];        // Eq. 3 alignment of each branch
-  int64_t delay;       // cumulated delay at the heads (own frames): noise key offset
-  int32_t bands, ncols, noise;
-  Ring out;
-  float* ext_out;
-  int64_t ext_stride;
+  int32_t A[3];   // Eq. 3 alignment of each branch
+  int64_t delay;  // cumulated delay at the heads (own frames): noise key offset
+  int32_t bands, ncols, noise, out_u;
+  OutViews out;
   Batch batch;
 };
 
 struct AddArgs {
   Ring in[2];
   int32_t A[2];
-  int32_t ncols;
-  Ring out;
-  float* ext_out;
-  int64_t ext_stride;
+  int32_t ncols, chans, out_u;
+  OutViews out;
   Batch batch;
 };
 
 struct InputArgs {
-  const float* src;   // count x [ncols][C]
-  int64_t src_stride; // floats between streams
-  int32_t ncols;
-  Ring out;
+  const float* src;    // count x [ncols][C]
+  int64_t src_stride;  // floats between streams
+  int32_t ncols, chans, out_u;
+  OutViews out;
   Batch batch;
 };
 
@@ -91,5 +118,9 @@ cudaError_t launch_heads(const HeadsArgs& a, cudaStream_t st);
 cudaError_t launch_add(const AddArgs& a, cudaStream_t st);
 cudaError_t launch_input(const InputArgs& a, cudaStream_t st);
 cudaError_t launch_advance(const Batch& b, int64_t steps, cudaStream_t st);
+
+// Tensor-core kernels (cc_kernels_tc.cu).  `tmap` is a CUtensorMap (128 B).
+cudaError_t launch_conv_tc(const void* tmap, const TcArgs& a, int bn, cudaStream_t st);
+int tc_tile_n(int64_t n_cols, int m_tiles);
 
 }  // namespace cc

@@ -3,35 +3,14 @@
 // (Eq. 3) and the RAVE-like heads.  The FP32 path is FFMA only: no TF32.
 #include <cstdint>
 
+#include "cc_device.cuh"
 #include "cc_internal.h"
 
 namespace cc {
 namespace {
 
-__device__ __forceinline__ int64_t ring_row(int64_t t, int32_t rows) {
-  int64_t r = t % rows;
-  return r < 0 ? r + rows : r;
-}
-
-__device__ __forceinline__ int32_t wrap_row(int32_t r, int32_t rows) {
-  return r >= rows ? r - rows : r;
-}
-
-__device__ __forceinline__ float activate(float x, int32_t act) {
-  return (act && x < 0.f) ? kLeakySlope * x : x;
-}
-
-template <typename T>
-__device__ __forceinline__ T* ring_ptr(const Batch& b, int32_t s, const Ring& r) {
-  return reinterpret_cast<T*>(b.arena + (int64_t)b.slots[s] * b.slot_bytes + r.off);
-}
-
-__device__ __forceinline__ int64_t steps_of(const Batch& b, int32_t s) {
-  return b.counters[b.slots[s]];
-}
-
 // Epilogue of a conv / convT GEMM element: bias, fused residual (Eq. 3 aligned
-// skip), store into the output ring or the caller's buffer.
+// skip), store into every output view.
 __device__ __forceinline__ void store_conv(const ConvArgs& a, int32_t m, int32_t n, float v) {
   const int32_t s = n / a.ncols;
   const int32_t j = n - s * a.ncols;
@@ -45,16 +24,12 @@ __device__ __forceinline__ void store_conv(const ConvArgs& a, int32_t m, int32_t
     lt = j * a.phases + ph;
   }
   if (a.bias) v += a.bias[ch];
-  const int64_t t = steps_of(a.batch, s) * a.out.u + lt;
+  const int64_t t = steps_of(a.batch, s) * a.out_u + lt;
   if (a.has_skip) {
     const float* sk = ring_ptr<const float>(a.batch, s, a.skip);
     v += sk[ring_row(t - a.skip_A, a.skip.rows) * a.skip.chans + ch];
   }
-  if (a.ext_out) {
-    a.ext_out[(int64_t)s * a.ext_stride + (int64_t)lt * a.cout + ch] = v;
-  } else {
-    ring_ptr<float>(a.batch, s, a.out)[ring_row(t, a.out.rows) * a.out.chans + ch] = v;
-  }
+  store_views(a.batch, s, a.out, t, lt, ch, a.cout, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -310,7 +285,7 @@ __global__ void k_heads(const HeadsArgs a) {
     const int64_t nj = i / a.bands;
     const int32_t j = (int32_t)(nj % a.ncols);
     const int32_t s = (int32_t)(nj / a.ncols);
-    const int64_t t = steps_of(a.batch, s) * a.out.u + j;
+    const int64_t t = steps_of(a.batch, s) * a.out_u + j;
     float v[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -322,15 +297,12 @@ __global__ void k_heads(const HeadsArgs a) {
       const uint64_t seed = a.batch.seeds[a.batch.slots[s]];
       y += sigmoidf_(v[2]) * noise_uniform(seed, t - a.delay, b, a.bands);
     }
-    if (a.ext_out)
-      a.ext_out[(int64_t)s * a.ext_stride + (int64_t)j * a.bands + b] = y;
-    else
-      ring_ptr<float>(a.batch, s, a.out)[ring_row(t, a.out.rows) * a.out.chans + b] = y;
+    store_views(a.batch, s, a.out, t, j, b, a.bands, y);
   }
 }
 
 __global__ void k_add(const AddArgs a) {
-  const int32_t C = a.out.chans;
+  const int32_t C = a.chans;
   const int64_t total = (int64_t)a.batch.count * a.ncols * C;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -338,22 +310,19 @@ __global__ void k_add(const AddArgs a) {
     const int64_t nj = i / C;
     const int32_t j = (int32_t)(nj % a.ncols);
     const int32_t s = (int32_t)(nj / a.ncols);
-    const int64_t t = steps_of(a.batch, s) * a.out.u + j;
+    const int64_t t = steps_of(a.batch, s) * a.out_u + j;
     float y = 0.f;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const float* p = ring_ptr<const float>(a.batch, s, a.in[q]);
       y += p[ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + c];
     }
-    if (a.ext_out)
-      a.ext_out[(int64_t)s * a.ext_stride + (int64_t)j * C + c] = y;
-    else
-      ring_ptr<float>(a.batch, s, a.out)[ring_row(t, a.out.rows) * C + c] = y;
+    store_views(a.batch, s, a.out, t, j, c, C, y);
   }
 }
 
 __global__ void k_input(const InputArgs a) {
-  const int32_t C = a.out.chans;
+  const int32_t C = a.chans;
   const int64_t total = (int64_t)a.batch.count * a.ncols * C;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -361,9 +330,8 @@ __global__ void k_input(const InputArgs a) {
     const int64_t nj = i / C;
     const int32_t j = (int32_t)(nj % a.ncols);
     const int32_t s = (int32_t)(nj / a.ncols);
-    const int64_t t = steps_of(a.batch, s) * a.out.u + j;
-    ring_ptr<float>(a.batch, s, a.out)[ring_row(t, a.out.rows) * C + c] =
-        a.src[(int64_t)s * a.src_stride + (int64_t)j * C + c];
+    const int64_t t = steps_of(a.batch, s) * a.out_u + j;
+    store_views(a.batch, s, a.out, t, j, c, C, a.src[(int64_t)s * a.src_stride + (int64_t)j * C + c]);
   }
 }
 
@@ -409,14 +377,14 @@ cudaError_t launch_heads(const HeadsArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_add(const AddArgs& a, cudaStream_t st) {
-  const int64_t total = (int64_t)a.batch.count * a.ncols * a.out.chans;
+  const int64_t total = (int64_t)a.batch.count * a.ncols * a.chans;
   if (total <= 0) return cudaSuccess;
   k_add<<<elementwise_grid(total), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_input(const InputArgs& a, cudaStream_t st) {
-  const int64_t total = (int64_t)a.batch.count * a.ncols * a.out.chans;
+  const int64_t total = (int64_t)a.batch.count * a.ncols * a.chans;
   if (total <= 0) return cudaSuccess;
   k_input<<<elementwise_grid(total), 256, 0, st>>>(a);
   return cudaGetLastError();

@@ -3,6 +3,9 @@
 // left; Eq. 2 stride alignment; cumulated lag; Eq. 3 branch alignment), the
 // per-stream ring-buffer arena (cached padding, section 2.2), weight packing
 // and the launch chain of one buffer.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -137,14 +140,26 @@ static cc_status validate_and_analyze(Model& m) {
   if (ips > (1 << 24)) return fail(CC_ERR_BAD_GRAPH, "model step of %lld input frames is too long", (long long)ips);
   m.in_per_step = (int32_t)ips;
   for (auto& p : m.nodes) p.u = (int32_t)(ips * p.rnum / p.rden);
-  // history each producer keeps = max over its consumers' needs
+  // engines: contractions whose input channels fill whole 64-wide K slices
+  // run on tensor cores in the low-precision modes
+  for (auto& p : m.nodes)
+    p.engine = (m.dtype != CC_F32 && (p.d.op == CC_OP_CONV || p.d.op == CC_OP_CONVT) &&
+                p.d.c_in % 64 == 0)
+                   ? 1
+                   : 0;
+  // history each producer keeps = max over its consumers' needs, per view
   for (int i = 0; i < n; ++i) {
-    const cc_node_desc& d = m.nodes[i].d;
+    const NodePlan& c = m.nodes[i];
+    const cc_node_desc& d = c.d;
     for (int q = 0; q < d.n_inputs; ++q) {
       NodePlan& src = m.nodes[d.inputs[q]];
       src.consumers.push_back(i);
-      const int need = (d.op == CC_OP_ADD || d.op == CC_OP_HEADS) ? m.nodes[i].A[q] : m.nodes[i].hist_need;
+      const bool merge = d.op == CC_OP_ADD || d.op == CC_OP_HEADS;
+      const int need = merge ? c.A[q] : c.hist_need;
+      const int v = (!merge && c.engine == 1) ? 1 + d.act_in : 0;
       src.keep = std::max(src.keep, need);
+      src.keep_view[v] = std::max(src.keep_view[v], need);
+      src.used_view[v] = true;
     }
   }
   return CC_OK;
@@ -180,16 +195,84 @@ static cc_status plan_arena(Model& m) {
     const bool needs_ring = !p.consumers.empty() && p.fused_add < 0;
     if (!needs_ring) continue;
     p.has_ring = true;
-    p.ring.rows = p.keep + p.u * m.max_steps;
-    p.ring.chans = p.d.c_out;
-    p.ring.u = p.u;
-    p.ring.dtype = 0;
-    p.ring.off = (int64_t)off;
-    off = align_up(off + (size_t)p.ring.rows * p.ring.chans * sizeof(float), 256);
-    state += (size_t)p.keep * p.d.c_out * sizeof(float);
+    for (int v = 0; v < 3; ++v) {
+      if (!p.used_view[v]) continue;
+      Ring& r = p.view[v];
+      r.rows = p.keep_view[v] + p.u * m.max_steps;
+      r.chans = p.d.c_out;
+      r.u = p.u;
+      r.dtype = v == 0 ? kDtF32 : m.lp_dtype;
+      const size_t elem = v == 0 ? 4 : 2;
+      r.off = (int64_t)off;
+      off = align_up(off + (size_t)r.rows * r.chans * elem, 256);
+      state += (size_t)p.keep_view[v] * p.d.c_out * elem;
+    }
   }
   m.slot_bytes = std::max<size_t>(align_up(off, 256), 256);
   m.state_bytes = state;
+  return CC_OK;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Low-precision tensor-core copy of a packed FP32 GEMM operand: rows scaled
+// to max |w| = 1 (the scale is re-applied in FP32 by the epilogue), padded to
+// 128-row tiles, described by a TMA map of 128 x 64 boxes, 128-byte swizzle.
+static cc_status upload_tc_operand(Model& m, NodePlan& p, const std::vector<float>& A) {
+  p.Mpad = (p.M + 127) / 128 * 128;
+  std::vector<uint16_t> lp((size_t)p.Mpad * p.Kt, 0);
+  std::vector<float> scale(p.Mpad, 1.0f);
+  for (int r = 0; r < p.M; ++r) {
+    float mx = 0.f;
+    for (int k = 0; k < p.Kt; ++k) mx = std::max(mx, std::fabs(A[(size_t)r * p.Kt + k]));
+    const float sc = mx > 0.f ? mx : 1.0f;
+    scale[r] = sc;
+    for (int k = 0; k < p.Kt; ++k) {
+      const float x = A[(size_t)r * p.Kt + k] / sc;
+      uint16_t bits;
+      if (m.lp_dtype == kDtBF16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        std::memcpy(&bits, &h, 2);
+      } else {
+        const __half h = __float2half_rn(x);
+        std::memcpy(&bits, &h, 2);
+      }
+      lp[(size_t)r * p.Kt + k] = bits;
+    }
+  }
+  CC_CUDA(cudaMalloc(&p.dA_lp, lp.size() * 2));
+  CC_CUDA(cudaMemcpy(p.dA_lp, lp.data(), lp.size() * 2, cudaMemcpyHostToDevice));
+  CC_CUDA(cudaMalloc(&p.dscale, scale.size() * sizeof(float)));
+  CC_CUDA(cudaMemcpy(p.dscale, scale.data(), scale.size() * sizeof(float), cudaMemcpyHostToDevice));
+  m.weight_bytes += lp.size() * 2;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return fail(CC_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[2] = {(cuuint64_t)p.Kt, (cuuint64_t)p.Mpad};
+  const cuuint64_t strides[1] = {(cuuint64_t)p.Kt * 2};
+  const cuuint32_t box[2] = {64, 128};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(reinterpret_cast<CUtensorMap*>(p.tmap),
+                         m.lp_dtype == kDtBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                         2, p.dA_lp, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(CC_ERR_CUDA, "tensor map encoding failed (%d)", (int)r);
   return CC_OK;
 }
 
@@ -231,9 +314,14 @@ static cc_status pack_and_upload(Model& m, const float* const* weights, const fl
                   w[((size_t)c * d.c_out + o) * d.kernel + k];
             }
     }
-    CC_CUDA(cudaMalloc(&p.dA, A.size() * sizeof(float)));
-    CC_CUDA(cudaMemcpy(p.dA, A.data(), A.size() * sizeof(float), cudaMemcpyHostToDevice));
-    m.weight_bytes += A.size() * sizeof(float);
+    if (p.engine == 1) {
+      cc_status s = upload_tc_operand(m, p, A);
+      if (s) return s;
+    } else {
+      CC_CUDA(cudaMalloc(&p.dA, A.size() * sizeof(float)));
+      CC_CUDA(cudaMemcpy(p.dA, A.data(), A.size() * sizeof(float), cudaMemcpyHostToDevice));
+      m.weight_bytes += A.size() * sizeof(float);
+    }
     if (d.has_bias) {
       CC_CUDA(cudaMalloc(&p.dbias, d.c_out * sizeof(float)));
       CC_CUDA(cudaMemcpy(p.dbias, biases[i], d.c_out * sizeof(float), cudaMemcpyHostToDevice));
@@ -264,6 +352,16 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
     if (timing_on) CC_CUDA(cudaEventRecord(timing_recs.back().stop, st));
     return CC_OK;
   };
+  auto views_of = [&](int wi) {
+    OutViews o{};
+    const NodePlan& w = nodes[wi];
+    o.f32 = w.view[0];
+    o.lp[0] = w.view[1];
+    o.lp[1] = w.view[2];
+    o.ext = wi == last ? out : nullptr;
+    o.ext_stride = out_stride;
+    return o;
+  };
   for (int i = 0; i < n; ++i) {
     NodePlan& p = nodes[i];
     const cc_node_desc& d = p.d;
@@ -272,7 +370,9 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
       a.src = in;
       a.src_stride = in_stride;
       a.ncols = p.u * steps;
-      a.out = p.ring;
+      a.chans = d.c_out;
+      a.out_u = p.u;
+      a.out = views_of(i);
       a.batch = batch;
       cc_status s = begin(i);
       if (s) return s;
@@ -284,73 +384,91 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
     // the node whose output this launch writes (a fused add writes for its conv)
     const int wi = (d.op == CC_OP_CONV || d.op == CC_OP_CONVT) && p.fused_add >= 0 ? p.fused_add : i;
     const NodePlan& w = nodes[wi];
-    float* ext = wi == last ? out : nullptr;
-    if (!ext && !w.has_ring) continue;  // dead branch
+    if (wi != last && !w.has_ring) continue;  // dead branch
+    const OutViews ov = views_of(wi);
     cc_status s = begin(i);
     if (s) return s;
     if (d.op == CC_OP_CONV || d.op == CC_OP_CONVT) {
       const NodePlan& src = nodes[d.inputs[0]];
-      ConvArgs a{};
-      a.A = p.dA;
-      a.bias = p.dbias;
-      a.M = p.M;
-      a.Kt = p.Kt;
-      a.taps = p.taps;
-      a.cin = d.c_in;
-      a.act = d.act_in;
-      a.cout = d.c_out;
-      a.phases = p.phases;
-      if (d.op == CC_OP_CONV) {
-        a.dil = d.dilation;
-        a.stride = d.stride;
+      const bool convt = d.op == CC_OP_CONVT;
+      const int32_t ncols = convt ? src.u * steps : p.u * steps;
+      const int32_t dil = convt ? 1 : d.dilation, stride = convt ? 1 : d.stride;
+      if (p.engine == 1) {
+        TcArgs a{};
+        a.scale = p.dscale;
+        a.bias = p.dbias;
+        a.M = p.M;
+        a.Kt = p.Kt;
+        a.taps = p.taps;
+        a.cin = d.c_in;
+        a.dil = dil;
+        a.stride = stride;
         a.hist = p.hist_need;
-        a.ncols = p.u * steps;
+        a.ncols = ncols;
+        a.cout = d.c_out;
+        a.phases = p.phases;
+        a.out_u = w.u;
+        a.in = src.view[1 + d.act_in];
+        a.out = ov;
+        if (p.fused_add >= 0) {
+          a.has_skip = 1;
+          a.skip = nodes[p.fused_skip].view[0];
+          a.skip_A = p.fused_skip_A;
+        }
+        a.batch = batch;
+        a.err = err;
+        const int bn = tc_tile_n((int64_t)batch.count * ncols, p.Mpad / 128);
+        CC_CUDA(launch_conv_tc(p.tmap, a, bn, st));
       } else {
-        a.dil = 1;
-        a.stride = 1;
+        ConvArgs a{};
+        a.A = p.dA;
+        a.bias = p.dbias;
+        a.M = p.M;
+        a.Kt = p.Kt;
+        a.taps = p.taps;
+        a.cin = d.c_in;
+        a.act = d.act_in;
+        a.cout = d.c_out;
+        a.phases = p.phases;
+        a.dil = dil;
+        a.stride = stride;
         a.hist = p.hist_need;
-        a.ncols = src.u * steps;
+        a.ncols = ncols;
+        a.out_u = w.u;
+        a.in = src.view[0];
+        a.out = ov;
+        if (p.fused_add >= 0) {
+          a.has_skip = 1;
+          a.skip = nodes[p.fused_skip].view[0];
+          a.skip_A = p.fused_skip_A;
+        }
+        a.batch = batch;
+        CC_CUDA(launch_conv_f32(a, st));
       }
-      a.in = src.ring;
-      a.out = w.ring;
-      a.out.u = w.u;
-      a.ext_out = ext;
-      a.ext_stride = out_stride;
-      if (p.fused_add >= 0) {
-        a.has_skip = 1;
-        a.skip = nodes[p.fused_skip].ring;
-        a.skip_A = p.fused_skip_A;
-      }
-      a.batch = batch;
-      CC_CUDA(launch_conv_f32(a, st));
     } else if (d.op == CC_OP_ADD) {
       AddArgs a{};
       for (int q = 0; q < 2; ++q) {
-        a.in[q] = nodes[d.inputs[q]].ring;
+        a.in[q] = nodes[d.inputs[q]].view[0];
         a.A[q] = p.A[q];
       }
       a.ncols = p.u * steps;
-      a.out = p.ring;
-      a.out.u = p.u;
-      a.out.chans = d.c_out;
-      a.ext_out = ext;
-      a.ext_stride = out_stride;
+      a.chans = d.c_out;
+      a.out_u = p.u;
+      a.out = ov;
       a.batch = batch;
       CC_CUDA(launch_add(a, st));
     } else {
       HeadsArgs a{};
       for (int q = 0; q < 3; ++q) {
-        a.in[q] = nodes[d.inputs[q]].ring;
+        a.in[q] = nodes[d.inputs[q]].view[0];
         a.A[q] = p.A[q];
       }
       a.delay = p.D;
       a.bands = d.c_out;
       a.ncols = p.u * steps;
       a.noise = noise;
-      a.out = p.ring;
-      a.out.u = p.u;
-      a.ext_out = ext;
-      a.ext_stride = out_stride;
+      a.out_u = p.u;
+      a.out = ov;
       a.batch = batch;
       CC_CUDA(launch_heads(a, st));
     }
@@ -452,7 +570,10 @@ Model::~Model() {
   for (auto& p : nodes) {
     if (p.dA) cudaFree(p.dA);
     if (p.dbias) cudaFree(p.dbias);
+    if (p.dA_lp) cudaFree(p.dA_lp);
+    if (p.dscale) cudaFree(p.dscale);
   }
+  if (err) cudaFree(err);
   if (arena) cudaFree(arena);
   if (counters) cudaFree(counters);
   if (seeds) cudaFree(seeds);
@@ -500,11 +621,13 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
                           const float* const* biases, const cc_model_config* config, cc_model** out) {
   if (!nodes || !config || !out || n_nodes <= 0) return fail(CC_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
-  if (config->compute != CC_F32) return fail(CC_ERR_INVALID_ARG, "compute dtype %d not built", config->compute);
+  if (config->compute != CC_F32 && config->compute != CC_BF16 && config->compute != CC_F16)
+    return fail(CC_ERR_INVALID_ARG, "unknown compute dtype %d", config->compute);
   if (config->max_streams < 0 || config->max_steps_per_call <= 0)
     return fail(CC_ERR_INVALID_ARG, "max_streams must be >= 0 and max_steps_per_call > 0");
   auto* m = new cc::Model();
   m->dtype = config->compute;
+  m->lp_dtype = config->compute == CC_F16 ? cc::kDtF16 : cc::kDtBF16;
   m->max_streams = config->max_streams;
   m->max_steps = config->max_steps_per_call;
   m->noise = config->noise ? 1 : 0;
@@ -532,10 +655,12 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
   if (!s && (cudaMalloc(&m->counters, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
              cudaMalloc(&m->seeds, sizeof(uint64_t) * m->max_streams) != cudaSuccess ||
              cudaMalloc(&m->batch_slots, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
+             cudaMalloc(&m->err, sizeof(int32_t)) != cudaSuccess ||
              cudaMallocHost(&m->batch_slots_host, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
              cudaEventCreateWithFlags(&m->batch_upload_done, cudaEventDisableTiming) != cudaSuccess))
     s = fail(CC_ERR_NO_MEMORY, "model bookkeeping allocation failed");
   if (!s && (cudaMemset(m->counters, 0, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
+             cudaMemset(m->err, 0, sizeof(int32_t)) != cudaSuccess ||
              cudaMemset(m->seeds, 0, sizeof(uint64_t) * m->max_streams) != cudaSuccess))
     s = fail(CC_ERR_CUDA, "memset failed");
   if (s) {
@@ -740,6 +865,20 @@ cc_status cc_stream_set_state(cc_stream* s, const void* blob, size_t bytes, void
                           cudaMemcpyHostToDevice, st));
   CC_CUDA(cudaStreamSynchronize(st));
   std::memcpy(&s->seed, b + 8, sizeof(uint64_t));
+  return CC_OK;
+}
+
+cc_status cc_model_device_status(cc_model* model, int32_t* code) {
+  if (!model) return fail(CC_ERR_INVALID_ARG, "null model");
+  auto* m = reinterpret_cast<cc::Model*>(model);
+  int32_t v = 0;
+  if (m->err) {
+    CC_CUDA(cudaDeviceSynchronize());
+    CC_CUDA(cudaMemcpy(&v, m->err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CC_CUDA(cudaMemset(m->err, 0, sizeof(int32_t)));
+  }
+  if (code) *code = v;
+  if (v) return fail(CC_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", v);
   return CC_OK;
 }
 

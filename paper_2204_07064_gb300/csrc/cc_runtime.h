@@ -24,8 +24,13 @@ struct NodePlan {
   int32_t hist_need = 0;       // cached frames this layer reads before its window
   int32_t keep = 0;            // frames of this node's output kept for consumers
   std::vector<int> consumers;
+  // output views: 0 FP32, 1 low precision as computed, 2 low precision after
+  // LeakyReLU; keep_view = history kept for the consumers of that view
   bool has_ring = false;
-  Ring ring{};
+  bool used_view[3] = {false, false, false};
+  int32_t keep_view[3] = {0, 0, 0};
+  Ring view[3]{};
+  int32_t engine = 0;  // 0: FP32 FFMA kernels, 1: tcgen05 tensor cores
   // residual add folded into this conv's epilogue
   int32_t fused_add = -1, fused_skip = -1, fused_skip_A = 0;
   bool fused = false;  // (add) computed by its producer's epilogue
@@ -33,6 +38,11 @@ struct NodePlan {
   int32_t M = 0, Kt = 0, taps = 0, phases = 1;
   float* dA = nullptr;
   float* dbias = nullptr;
+  // tensor-core operand: low-precision [Mpad][Kt], per-row scale, TMA map
+  int32_t Mpad = 0;
+  void* dA_lp = nullptr;
+  float* dscale = nullptr;
+  alignas(64) unsigned char tmap[128] = {};
 };
 
 struct TimingRec {
@@ -42,11 +52,13 @@ struct TimingRec {
 
 struct Model {
   int32_t dtype = CC_F32;
+  int32_t lp_dtype = kDtBF16;  // element type of low-precision views
   int32_t max_streams = 0, max_steps = 1, noise = 1;
   int32_t in_per_step = 1;
   std::vector<NodePlan> nodes;
   size_t slot_bytes = 0, state_bytes = 0, weight_bytes = 0;
   char* arena = nullptr;
+  int32_t* err = nullptr;  // device error word (bounded waits that gave up)
   int64_t* counters = nullptr;
   uint64_t* seeds = nullptr;
   std::mutex mu;

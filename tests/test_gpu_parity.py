@@ -16,6 +16,21 @@ from paper_2204_07064_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-5
+LP_SNR_DB = 35.0
+LP_MAXABS = 2e-2
+
+
+def _assert_lowp(out, ref, what=""):
+    """BF16 / FP16 bar: SNR >= 35 dB and max-abs <= 2e-2 x peak |ref|."""
+    out = np.asarray(out, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert out.shape == ref.shape, (out.shape, ref.shape)
+    snr = metrics.snr_db(ref, out)
+    err = metrics.max_abs(ref, out)
+    peak = float(np.max(np.abs(ref)))
+    assert snr >= LP_SNR_DB, f"{what}: SNR {snr:.1f} dB < {LP_SNR_DB}"
+    assert err <= LP_MAXABS * peak, f"{what}: max-abs {err:.3e} > {LP_MAXABS} x peak {peak:.3e}"
+    return snr, err / peak
 
 
 def _assert_fp32(out, ref, what=""):
@@ -214,7 +229,7 @@ def test_errors(cclib, cuda):
     s2.process(torch.zeros((0, 1), device=cuda), torch.zeros((0, 128), device=cuda))
 
 
-@pytest.mark.parametrize("dtype", ["f32"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f16"])
 def test_decoder_full_batch_sampled_streams(cclib, cuda, dtype):
     """The benchmark's launch configuration (256 streams x one 2048-sample
     buffer per step, max one step per call): every stream runs on the GPU,
@@ -232,6 +247,41 @@ def test_decoder_full_batch_sampled_streams(cclib, cuda, dtype):
     for t in range(steps):
         model.process_batch(streams, torch.tensor(z[t], dtype=torch.float32, device=cuda), y)
         outs[:, t * 2048:(t + 1) * 2048] = y[:, :, 0].cpu().numpy()
+    assert model.device_status() == 0
     for i in (0, 77, 255):
         ref = M.run_causal(dec, p, z[:, i, 0, :], seed=seeds[i])[:, 0]
-        _assert_fp32(outs[i], ref, f"stream {i} of {count}")
+        if dtype == "f32":
+            _assert_fp32(outs[i], ref, f"stream {i} of {count}")
+        else:
+            _assert_lowp(outs[i], ref, f"{dtype} stream {i} of {count}")
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_decoder_lowp_single_stream_partitions(cclib, cuda, dtype):
+    """Tensor-core path with one stream (partial tiles everywhere) and ragged
+    buffers; per-buffer-size invariance within the precision bar."""
+    import torch
+
+    dec, p = _decoder(6)
+    z = W.signal(8, 10, 128)
+    ref = M.run_causal(dec, p, z, seed=4)
+    for part, ms in (([1] * 10, 1), ([3, 2, 5], 3)):
+        model = api.Model(dec, p, dtype=dtype, max_streams=1, max_steps_per_call=ms)
+        y = _run_stream(model, model.stream(seed=4), z, part, torch, cuda)
+        assert model.device_status() == 0
+        _assert_lowp(y, ref, f"{dtype} partition {part}")
+        model.close()
+
+
+def test_decoder_bf16_noise_off_vs_original(cclib, cuda):
+    """Section 4.2 setting (noise synthesiser off): BF16 streamed output vs the
+    original non-causal model, delayed by the computed latency."""
+    import torch
+
+    dec, p = _decoder(7)
+    z = W.signal(9, 16, 128)
+    model = api.Model(dec, p, dtype="bf16", max_streams=1, max_steps_per_call=2, noise=False)
+    y = _run_stream(model, model.stream(seed=1), z, [2] * 8, torch, cuda)
+    yo = M.run_original(dec, p, z, seed=1, noise_on=False)
+    d, w = model.total_delay, M.warmup_frames(dec)
+    _assert_lowp(y[d + w:], yo[w:len(yo) - d], "bf16 vs original delayed")

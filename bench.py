@@ -33,10 +33,14 @@ FP32_LANES_PER_SM = 128
 
 WORKLOADS = {
     # name: (dtype, streams, buffer latent frames)
+    "decoder-bf16-b256": ("bf16", 256, 1),
+    "decoder-f16-b256": ("f16", 256, 1),
     "decoder-fp32-b256": ("f32", 256, 1),
     "decoder-fp32-b1": ("f32", 1, 1),
+    "decoder-bf16-b1024": ("bf16", 1024, 1),
+    "decoder-bf16-b2048": ("bf16", 2048, 1),
 }
-DEFAULT_WORKLOAD = "decoder-fp32-b256"
+DEFAULT_WORKLOAD = "decoder-bf16-b256"
 
 
 def peaks():
@@ -224,6 +228,7 @@ def main():
     for i in range(args.warmup):
         model.process_batch(ss, z[i], y)
     torch.cuda.synchronize()
+    model.device_status()
 
     # timed region: K steps bracketed by per-step events on the launching stream
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -300,6 +305,27 @@ def main():
     roof["launches"] = conv_launches
     roof["avg_launch_us"] = 1000.0 * conv_ms / conv_launches if conv_launches else None
 
+    model.device_status()  # raises if a bounded device wait gave up
+
+    # the same batch through the FP32 (FFMA) path: the metric compares both
+    fp32_cmp = None
+    if dtype != "f32":
+        model32 = build_decoder("f32", streams)[2]
+        ss32 = [model32.stream(seed=s) for s in seeds]
+        for i in range(args.warmup):
+            model32.process_batch(ss32, z[i], y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for k in range(args.steps):
+            model32.process_batch(ss32, z[args.warmup + k], y)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms32 = e0.elapsed_time(e1) / args.steps
+        fp32_cmp = {"value": streams * 2048 * frames * world / (ms32 / 1000.0) / SR, "unit": "streams",
+                    "ms_per_step": ms32, "dtype": "f32", "speedup_lowp_over_fp32": (ms32 / (total_ms / args.steps))}
+        model32.close()
+
     step_sorted = sorted(step_ms)
     p50 = float(np.percentile(step_ms, 50))
     p99 = float(np.percentile(step_ms, 99))
@@ -320,6 +346,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": "streams",
                 "h2d_bytes_per_step": int(zh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)},
         "roofline": roof,
+        "fp32_same_batch": fp32_cmp,
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
     }

@@ -32,6 +32,93 @@ __device__ __forceinline__ void store_conv(const ConvArgs& a, int32_t m, int32_t
   store_views(a.batch, s, a.out, t, lt, ch, a.cout, v);
 }
 
+// Epilogue of TM rows of one GEMM column (rows come in groups of four
+// consecutive output rows): the column's ring rows are computed once (one
+// modulo per view), every bias / residual load is issued before the first
+// store, then the values go to every output view -- as float4 / 4-element
+// low-precision stores when the channel count allows it.
+template <int TM>
+__device__ __forceinline__ void store_column(const ConvArgs& a, int32_t n, const int32_t (&m)[TM],
+                                             float (&v)[TM], bool vec) {
+  const int32_t s = n / a.ncols;
+  const int32_t j = n - s * a.ncols;
+  char* base = slot_base(a.batch, s);
+  const int64_t tb = steps_of(a.batch, s) * a.out_u + (int64_t)j * a.phases;
+  const int32_t rf = a.out.f32.rows ? (int32_t)ring_row(tb, a.out.f32.rows) : 0;
+  const int32_t r0 = a.out.lp[0].rows ? (int32_t)ring_row(tb, a.out.lp[0].rows) : 0;
+  const int32_t r1 = a.out.lp[1].rows ? (int32_t)ring_row(tb, a.out.lp[1].rows) : 0;
+  const int32_t rs = a.has_skip ? (int32_t)ring_row(tb - a.skip_A, a.skip.rows) : 0;
+  int32_t ph[TM], ch[TM];
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    ph[i] = a.phases == 1 ? 0 : m[i] / a.cout;
+    ch[i] = m[i] - ph[i] * a.cout;
+  }
+  float add[TM];
+  if (vec) {
+#pragma unroll
+    for (int g = 0; g < TM; g += 4) {
+      float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m[g] < a.M) {
+        if (a.bias) b4 = __ldg(reinterpret_cast<const float4*>(a.bias + ch[g]));
+        if (a.has_skip) {
+          const float4 s4 = __ldg(reinterpret_cast<const float4*>(
+              reinterpret_cast<const float*>(base + a.skip.off) +
+              (int64_t)wrap_row(rs + ph[g], a.skip.rows) * a.skip.chans + ch[g]));
+          b4.x += s4.x; b4.y += s4.y; b4.z += s4.z; b4.w += s4.w;
+        }
+      }
+      add[g] = b4.x; add[g + 1] = b4.y; add[g + 2] = b4.z; add[g + 3] = b4.w;
+    }
+#pragma unroll
+    for (int g = 0; g < TM; g += 4) {
+      if (m[g] >= a.M) continue;
+      float x[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) x[k] = v[g + k] + add[g + k];
+      if (a.out.f32.rows)
+        *reinterpret_cast<float4*>(reinterpret_cast<float*>(base + a.out.f32.off) +
+                                   (int64_t)wrap_row(rf + ph[g], a.out.f32.rows) * a.out.f32.chans + ch[g]) =
+            make_float4(x[0], x[1], x[2], x[3]);
+      if (a.out.ext) {
+        float* e = a.out.ext + (int64_t)s * a.out.ext_stride + ((int64_t)j * a.phases + ph[g]) * a.cout + ch[g];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e[k] = x[k];
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const Ring& lr = a.out.lp[q];
+        if (!lr.rows) continue;
+        const int32_t row = wrap_row((q ? r1 : r0) + ph[g], lr.rows);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) store_lp(base, lr, row, ch[g] + k, q ? leaky(x[k]) : x[k]);
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    add[i] = 0.f;
+    if (m[i] < a.M) {
+      if (a.bias) add[i] = __ldg(a.bias + ch[i]);
+      if (a.has_skip)
+        add[i] += __ldg(reinterpret_cast<const float*>(base + a.skip.off) +
+                        (int64_t)wrap_row(rs + ph[i], a.skip.rows) * a.skip.chans + ch[i]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    if (m[i] >= a.M) continue;
+    const float x = v[i] + add[i];
+    if (a.out.ext) a.out.ext[(int64_t)s * a.out.ext_stride + ((int64_t)j * a.phases + ph[i]) * a.cout + ch[i]] = x;
+    if (a.out.f32.rows)
+      reinterpret_cast<float*>(base + a.out.f32.off)[(int64_t)wrap_row(rf + ph[i], a.out.f32.rows) *
+                                                         a.out.f32.chans + ch[i]] = x;
+    if (a.out.lp[0].rows) store_lp(base, a.out.lp[0], wrap_row(r0 + ph[i], a.out.lp[0].rows), ch[i], x);
+    if (a.out.lp[1].rows) store_lp(base, a.out.lp[1], wrap_row(r1 + ph[i], a.out.lp[1].rows), ch[i], leaky(x));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Skinny GEMM (few columns per launch: single-stream steps).  One warp per
 // output row m, eight columns per block column; the reduction over (tap,
@@ -246,15 +333,18 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
       buf ^= 1;
     }
   }
+  int32_t ms[TM];
+#pragma unroll
+  for (int i = 0; i < TM; ++i) ms[i] = m0 + (i / 4) * (BM / 2) + tx * 4 + (i & 3);
+  const bool vec = (a.cout % 4 == 0) && (a.M % 4 == 0);
 #pragma unroll
   for (int j = 0; j < TN; ++j) {
     const int32_t n = n0 + (j / 4) * (BN / 2) + ty * 4 + (j & 3);
     if (n >= N) continue;
+    float col[TM];
 #pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      const int32_t m = m0 + (i / 4) * (BM / 2) + tx * 4 + (i & 3);
-      if (m < a.M) store_conv(a, m, n, acc[i][j]);
-    }
+    for (int i = 0; i < TM; ++i) col[i] = acc[i][j];
+    store_column<TM>(a, n, ms, col, vec);
   }
 }
 

@@ -25,13 +25,16 @@ namespace {
 
 using namespace sm100;
 
-constexpr int kStages = 4;
 constexpr int kBM = 128;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
+// BN = 128: 3 stages (two CTAs per SM, so one CTA's epilogue overlaps the
+// other's main loop); BN = 256: 4 stages, one CTA per SM.
 template <int BN>
 struct TcLayout {
-  static constexpr int kA = kBM * 128;  // one 128 x 64 low-precision tile
+  static constexpr int kStages = BN == 128 ? 3 : 4;
+  static constexpr int kLag = kStages - 1;  // gather stages in flight per thread
+  static constexpr int kA = kBM * 128;      // one 128 x 64 low-precision tile
   static constexpr int kB = BN * 128;
   static constexpr int kBars = (2 * kStages + 1) * 8 + 8;
   static constexpr int kCols = BN * (8 + 8 + 4 * 4);
@@ -39,9 +42,10 @@ struct TcLayout {
 };
 
 template <int BN>
-__global__ void __launch_bounds__(160, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(160, BN == 128 ? 2 : 1) k_conv_tc(const __grid_constant__ CUtensorMap tmA,
                                                     const TcArgs a) {
   using L = TcLayout<BN>;
+  constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -143,60 +147,116 @@ __global__ void __launch_bounds__(160, 1) k_conv_tc(const __grid_constant__ CUte
         for (int c = 0; c < 8; ++c) cp_async_16(dst + sw128_offset(r, c), src + c * 8, bok[rr] ? 16u : 0u);
       }
       cp_async_commit();
-      if (kc > 0) {
-        cp_async_wait<1>();
+      // a stage is handed to the MMA issuer once this thread's copies for it
+      // have landed; kLag stages stay in flight
+      if (kc >= L::kLag) {
+        cp_async_wait<L::kLag>();
         fence_proxy_async_smem();
-        mbar_arrive(full + (kc - 1) % kStages);
+        mbar_arrive(full + (kc - L::kLag) % kStages);
       }
     }
     cp_async_wait<0>();
     fence_proxy_async_smem();
-    if (ok && nk > 0) mbar_arrive(full + (nk - 1) % kStages);
+    if (ok)
+      for (int kc = nk > L::kLag ? nk - L::kLag : 0; kc < nk; ++kc) mbar_arrive(full + kc % kStages);
     if (!ok) atomicOr(a.err, 1);
 
     // ---- epilogue
-    asm volatile("bar.sync 1, 128;" ::: "memory");  // column table written by all producers
-    bool got = mbar_wait(tfull, 0, kWaitNs);
-    got = __all_sync(0xffffffffu, got);
+    // one verdict for all 128 epilogue threads (a reduction barrier, which also
+    // publishes the column table), so the named barriers below always match
+    const bool waited = mbar_wait(tfull, 0, kWaitNs);
+    uint32_t all_ok;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, 1, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(all_ok)
+        : "r"((uint32_t)waited)
+        : "memory");
+    const bool got = all_ok != 0;
     tc_fence_after();
     if (!got) {
       if (lane == 0) atomicOr(a.err, 2);
     } else {
-      const int32_t m = m0 + warp * 32 + lane;
+      // Two passes per 32-column TMEM chunk.  Pass 1: thread = output row,
+      // scaled + biased values go transposed into shared memory (the free
+      // pipeline buffers).  Pass 2: thread = (column, 8 consecutive rows):
+      // 16/32-byte residual loads and view stores, coalesced along channels.
+      const int32_t rloc = warp * 32 + lane;
+      const int32_t m = m0 + rloc;
       const bool mok = m < a.M;
-      int32_t ph = 0, ch = m;
-      if (a.phases > 1) {
-        ph = m / a.cout;
-        ch = m - ph * a.cout;
-      }
+      int32_t ch = m;
+      if (a.phases > 1) ch = m - (m / a.cout) * a.cout;
       const float sc = mok ? a.scale[m] : 0.f;
       const float bi = (mok && a.bias) ? a.bias[ch] : 0.f;
-      for (int cb = 0; cb < BN; cb += 32) {
-        if (n0 + cb >= N) break;
+      float* stage = reinterpret_cast<float*>(sA);  // 2 x 32 x 128 floats
+      for (int cb = 0, it = 0; cb < BN; cb += 32, ++it) {
+        if (n0 + cb >= N) break;  // uniform over the 128 epilogue threads
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, r);
         tmem_ld_wait();
-        if (!mok) continue;
+        float* stg = stage + (it & 1) * 32 * kBM;
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          const int c = cb + jj;
-          if (n0 + c >= N) continue;
-          float v = __uint_as_float(r[jj]) * sc + bi;
-          char* base = a.batch.arena + col_slot[c];
+        for (int jj = 0; jj < 32; ++jj) stg[jj * kBM + rloc] = __uint_as_float(r[jj]) * sc + bi;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int p = t + q * 128;
+          const int c = p >> 4, g = p & 15;
+          const int32_t mb = m0 + g * 8;
+          if (n0 + cb + c >= N || mb >= a.M) continue;
+          float x[8];
+          const float4 x0 = *reinterpret_cast<const float4*>(stg + c * kBM + g * 8);
+          const float4 x1 = *reinterpret_cast<const float4*>(stg + c * kBM + g * 8 + 4);
+          x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
+          x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
+          const int32_t ph = a.phases > 1 ? mb / a.cout : 0;
+          const int32_t cg = mb - ph * a.cout;  // first channel of the group
+          const int col = cb + c;
+          char* base = a.batch.arena + col_slot[col];
           if (a.has_skip) {
-            const int32_t row = wrap_row(col_row[3 * BN + c] + ph, a.skip.rows);
-            v += reinterpret_cast<const float*>(base + a.skip.off)[(int64_t)row * a.skip.chans + ch];
+            const int32_t row = wrap_row(col_row[3 * BN + col] + ph, a.skip.rows);
+            const float4* sp = reinterpret_cast<const float4*>(
+                base + a.skip.off + ((int64_t)row * a.skip.chans + cg) * 4);
+            const float4 s0 = __ldg(sp), s1 = __ldg(sp + 1);
+            x[0] += s0.x; x[1] += s0.y; x[2] += s0.z; x[3] += s0.w;
+            x[4] += s1.x; x[5] += s1.y; x[6] += s1.z; x[7] += s1.w;
           }
-          if (a.out.ext) a.out.ext[col_ext[c] + (int64_t)ph * a.cout + ch] = v;
+          if (a.out.ext) {
+            float* e = a.out.ext + col_ext[col] + (int64_t)ph * a.cout + cg;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) e[k] = x[k];
+          }
           if (a.out.f32.rows) {
-            const int32_t row = wrap_row(col_row[c] + ph, a.out.f32.rows);
-            reinterpret_cast<float*>(base + a.out.f32.off)[(int64_t)row * a.out.f32.chans + ch] = v;
+            const int32_t row = wrap_row(col_row[col] + ph, a.out.f32.rows);
+            float4* d = reinterpret_cast<float4*>(base + a.out.f32.off +
+                                                  ((int64_t)row * a.out.f32.chans + cg) * 4);
+            d[0] = make_float4(x[0], x[1], x[2], x[3]);
+            d[1] = make_float4(x[4], x[5], x[6], x[7]);
           }
-          if (a.out.lp[0].rows)
-            store_lp(base, a.out.lp[0], wrap_row(col_row[BN + c] + ph, a.out.lp[0].rows), ch, v);
-          if (a.out.lp[1].rows)
-            store_lp(base, a.out.lp[1], wrap_row(col_row[2 * BN + c] + ph, a.out.lp[1].rows), ch,
-                     leaky(v));
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            const Ring& lr = a.out.lp[v];
+            if (!lr.rows) continue;
+            const int32_t row = wrap_row(col_row[(1 + v) * BN + col] + ph, lr.rows);
+            float y[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) y[k] = v ? leaky(x[k]) : x[k];
+            uint4 pk;
+            if (lr.dtype == kDtBF16) {
+              __nv_bfloat162 h0 = __floats2bfloat162_rn(y[0], y[1]), h1 = __floats2bfloat162_rn(y[2], y[3]);
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(y[4], y[5]), h3 = __floats2bfloat162_rn(y[6], y[7]);
+              pk.x = *reinterpret_cast<uint32_t*>(&h0); pk.y = *reinterpret_cast<uint32_t*>(&h1);
+              pk.z = *reinterpret_cast<uint32_t*>(&h2); pk.w = *reinterpret_cast<uint32_t*>(&h3);
+            } else {
+              __half2 h0 = __floats2half2_rn(y[0], y[1]), h1 = __floats2half2_rn(y[2], y[3]);
+              __half2 h2 = __floats2half2_rn(y[4], y[5]), h3 = __floats2half2_rn(y[6], y[7]);
+              pk.x = *reinterpret_cast<uint32_t*>(&h0); pk.y = *reinterpret_cast<uint32_t*>(&h1);
+              pk.z = *reinterpret_cast<uint32_t*>(&h2); pk.w = *reinterpret_cast<uint32_t*>(&h3);
+            }
+            *reinterpret_cast<uint4*>(base + lr.off + ((int64_t)row * lr.chans + cg) * 2) = pk;
+          }
         }
       }
     }

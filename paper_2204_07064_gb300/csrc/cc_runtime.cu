@@ -144,7 +144,7 @@ static cc_status validate_and_analyze(Model& m) {
   // run on tensor cores in the low-precision modes
   for (auto& p : m.nodes)
     p.engine = (m.dtype != CC_F32 && (p.d.op == CC_OP_CONV || p.d.op == CC_OP_CONVT) &&
-                p.d.c_in % 64 == 0)
+                p.d.c_in % 64 == 0 && p.d.c_out % 8 == 0)
                    ? 1
                    : 0;
   // history each producer keeps = max over its consumers' needs, per view

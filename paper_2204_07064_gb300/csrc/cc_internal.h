@@ -80,6 +80,8 @@ struct TcArgs {
   const float* bias;   // [cout] or null
   int32_t M, Kt, taps, cin, dil, stride, hist, ncols, cout, phases, out_u;
   Ring in;
+  int32_t in_rows_per_slot;  // the input view seen as rows of the whole arena:
+  int32_t in_row_off;        //   row = slot*in_rows_per_slot + in_row_off + ring row
   OutViews out;
   int32_t has_skip, skip_A;
   Ring skip;
@@ -119,8 +121,11 @@ cudaError_t launch_add(const AddArgs& a, cudaStream_t st);
 cudaError_t launch_input(const InputArgs& a, cudaStream_t st);
 cudaError_t launch_advance(const Batch& b, int64_t steps, cudaStream_t st);
 
-// Tensor-core kernels (cc_kernels_tc.cu).  `tmap` is a CUtensorMap (128 B).
-cudaError_t launch_conv_tc(const void* tmap, const TcArgs& a, int bn, cudaStream_t st);
+// Tensor-core kernels (cc_kernels_tc.cu).  tmap_a: weights [Mpad][Kt] in
+// 128 x 64 boxes; tmap_b: the input view as arena rows of C elements, one-row
+// boxes of 64 (gathered four rows at a time).  Both CUtensorMap (128 B).
+cudaError_t launch_conv_tc(const void* tmap_a, const void* tmap_b, const TcArgs& a, int bn,
+                           cudaStream_t st);
 int tc_tile_n(int64_t n_cols, int m_tiles);
 
 }  // namespace cc

@@ -5,15 +5,18 @@
 // of that stream at time t0 + j*stride + k*dil - hist (cached padding,
 // section 2.2, read in place).
 //
-// One CTA computes a 128 x BN tile:
-//   warps 0-3  producers: TMA for the weight tile (128 rows x 64 K, 128-byte
-//              swizzle), cp.async gathers of the BN window rows into the same
-//              swizzled layout; then the epilogue (TMEM -> registers ->
-//              scale, bias, aligned residual, every output view)
-//   warp 4     TMEM allocation; lane 0 issues tcgen05.mma (128 x BN x 16,
+// One CTA computes a 128 x BN tile with three roles:
+//   warp 0     TMA producer: per 64-wide K slice, the weight tile (128 rows,
+//              128-byte swizzle) and the BN window rows, gathered four at a
+//              time (tile::gather4) from the stream rings into the same
+//              swizzled layout; one expect-tx per stage, no thread waits on
+//              its own copies, so every stage can be in flight
+//   warp 1     TMEM allocation; lane 0 issues tcgen05.mma (128 x BN x 16,
 //              BF16 or FP16 operands, FP32 accumulation in TMEM)
-// Stages are handed over with mbarriers; every wait is bounded in time and
-// records an error in the model's device error word instead of hanging.
+//   warps 2-5  epilogue: TMEM -> registers -> transposed shared memory ->
+//              scale, bias, aligned residual, 16/32-byte stores of every view
+// Every mbarrier wait is bounded in time and records an error in the model's
+// device error word instead of hanging.
 #include <cuda.h>
 
 #include "cc_device.cuh"
@@ -26,6 +29,7 @@ namespace {
 using namespace sm100;
 
 constexpr int kBM = 128;
+constexpr int kThreads = 192;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
 // BN = 128: 3 stages (two CTAs per SM, so one CTA's epilogue overlaps the
@@ -33,8 +37,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 template <int BN>
 struct TcLayout {
   static constexpr int kStages = BN == 128 ? 3 : 4;
-  static constexpr int kLag = kStages - 1;  // gather stages in flight per thread
-  static constexpr int kA = kBM * 128;      // one 128 x 64 low-precision tile
+  static constexpr int kA = kBM * 128;  // one 128 x 64 low-precision tile
   static constexpr int kB = BN * 128;
   static constexpr int kBars = (2 * kStages + 1) * 8 + 8;
   static constexpr int kCols = BN * (8 + 8 + 4 * 4);
@@ -42,8 +45,9 @@ struct TcLayout {
 };
 
 template <int BN>
-__global__ void __launch_bounds__(160, BN == 128 ? 2 : 1) k_conv_tc(const __grid_constant__ CUtensorMap tmA,
-                                                    const TcArgs a) {
+__global__ void __launch_bounds__(kThreads, BN == 128 ? 2 : 1)
+    k_conv_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const TcArgs a) {
   using L = TcLayout<BN>;
   constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
@@ -68,14 +72,15 @@ __global__ void __launch_bounds__(160, BN == 128 ? 2 : 1) k_conv_tc(const __grid
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(full + s, 129);  // 128 gather arrivals + 1 expect_tx arrival
+      mbar_init(full + s, 1);  // the producer's expect-tx arrival; TMA completes the bytes
       mbar_init(empty + s, 1);
     }
     mbar_init(tfull, 1);
     fence_mbar_init();
     prefetch_tmap(&tmA);
+    prefetch_tmap(&tmB);
   }
-  if (warp == 4) {
+  if (warp == 1) {
     tmem_alloc(tbase, BN);
     tmem_relinquish();
   }
@@ -84,9 +89,86 @@ __global__ void __launch_bounds__(160, BN == 128 ? 2 : 1) k_conv_tc(const __grid
   tc_fence_after();
   const uint32_t tmem = *tbase;
 
-  if (warp < 4) {
-    const int t = threadIdx.x;
-    // ---- per-column epilogue addressing (stream slot, output rows per view)
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    // lane l gathers tile rows 4*(l + 32*g) .. +3 for g < BN/128
+    constexpr int G = BN / 128;
+    int32_t ybase[G][4], r0[G][4];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int64_t n = n0 + 4 * (lane + 32 * g) + i;
+        ybase[g][i] = 0;
+        r0[g][i] = -1;  // column past the batch: read arena row 0, result discarded
+        if (n < N) {
+          const int32_t s = (int32_t)(n / a.ncols);
+          const int32_t j = (int32_t)(n - (int64_t)s * a.ncols);
+          ybase[g][i] = a.batch.slots[s] * a.in_rows_per_slot + a.in_row_off;
+          r0[g][i] = (int32_t)ring_row(steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist,
+                                       a.in.rows);
+        }
+      }
+    bool ok = true;
+    int issued = 0;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int st = kc % kStages;
+      const uint32_t ph = (kc / kStages) & 1;
+      if (!mbar_wait(empty + st, ph ^ 1, kWaitNs)) {
+        ok = false;
+        break;
+      }
+      const int tap = kc / cchunks;
+      const int c0 = (kc - tap * cchunks) * 64;
+      if (lane == 0) {
+        mbar_arrive_expect_tx(full + st, L::kA + L::kB);
+        tma_load_2d(sA + st * L::kA, &tmA, full + st, kc * 64, m0);
+      }
+      __syncwarp();
+      uint8_t* dst = sB + st * L::kB;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        int32_t y[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          y[i] = r0[g][i] < 0 ? 0 : ybase[g][i] + wrap_row(r0[g][i] + tap * a.dil, a.in.rows);
+        tma_gather4(dst + (lane + 32 * g) * 512, &tmB, full + st, c0, y[0], y[1], y[2], y[3]);
+      }
+      issued = kc + 1;
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(a.err, 1);
+      // let the copies already issued land before the CTA's shared memory goes away
+      for (int kc = issued - kStages < 0 ? 0 : issued - kStages; kc < issued; ++kc)
+        mbar_wait(full + kc % kStages, (kc / kStages) & 1, kWaitNs);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = idesc_f16(kBM, BN, a.in.dtype == kDtBF16);
+      bool ok = true;
+      for (int kc = 0; kc < nk; ++kc) {
+        const int st = kc % kStages;
+        const uint32_t ph = (kc / kStages) & 1;
+        if (!mbar_wait(full + st, ph, kWaitNs)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(sA + st * L::kA), sb = smem_u32(sB + st * L::kB);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_f16(tmem, sw128_kmajor_desc(sa + k * 32), sw128_kmajor_desc(sb + k * 32), idesc,
+                  (kc | k) != 0);
+        mma_commit(empty + st);
+      }
+      mma_commit(tfull);
+      if (!ok) atomicOr(a.err, 4);
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int t = threadIdx.x - 64;  // 0..127
+    const int sub = warp & 3;        // TMEM lane quarter this warp may access
     for (int c = t; c < BN; c += 128) {
       const int64_t n = n0 + c;
       if (n < N) {
@@ -101,67 +183,6 @@ __global__ void __launch_bounds__(160, BN == 128 ? 2 : 1) k_conv_tc(const __grid
         col_row[3 * BN + c] = a.has_skip ? (int32_t)ring_row(tb - a.skip_A, a.skip.rows) : 0;
       }
     }
-    // ---- producer: gather rows of the cached window
-    constexpr int RPT = BN / 128;
-    const uint16_t* bbase[RPT];
-    int32_t br0[RPT];
-    bool bok[RPT];
-#pragma unroll
-    for (int rr = 0; rr < RPT; ++rr) {
-      const int64_t n = n0 + t + rr * 128;
-      bok[rr] = n < N;
-      bbase[rr] = nullptr;
-      br0[rr] = 0;
-      if (bok[rr]) {
-        const int32_t s = (int32_t)(n / a.ncols);
-        const int32_t j = (int32_t)(n - (int64_t)s * a.ncols);
-        bbase[rr] = reinterpret_cast<const uint16_t*>(slot_base(a.batch, s) + a.in.off);
-        const int64_t tin = steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist;
-        br0[rr] = (int32_t)ring_row(tin, a.in.rows);
-      }
-    }
-    bool ok = true;
-    for (int kc = 0; kc < nk; ++kc) {
-      const int st = kc % kStages;
-      const uint32_t ph = (kc / kStages) & 1;
-      if (!mbar_wait(empty + st, ph ^ 1, kWaitNs)) {
-        ok = false;
-        break;
-      }
-      const int tap = kc / cchunks;
-      const int c0 = (kc - tap * cchunks) * 64;
-      if (t == 0) {
-        mbar_arrive_expect_tx(full + st, L::kA);
-        tma_load_2d(sA + st * L::kA, &tmA, full + st, kc * 64, m0);
-      }
-#pragma unroll
-      for (int rr = 0; rr < RPT; ++rr) {
-        const int r = t + rr * 128;
-        const uint16_t* src = reinterpret_cast<const uint16_t*>(a.scale);  // any valid address
-        if (bok[rr]) {
-          const int32_t row = wrap_row(br0[rr] + tap * a.dil, a.in.rows);
-          src = bbase[rr] + (int64_t)row * a.cin + c0;
-        }
-        uint8_t* dst = sB + st * L::kB;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) cp_async_16(dst + sw128_offset(r, c), src + c * 8, bok[rr] ? 16u : 0u);
-      }
-      cp_async_commit();
-      // a stage is handed to the MMA issuer once this thread's copies for it
-      // have landed; kLag stages stay in flight
-      if (kc >= L::kLag) {
-        cp_async_wait<L::kLag>();
-        fence_proxy_async_smem();
-        mbar_arrive(full + (kc - L::kLag) % kStages);
-      }
-    }
-    cp_async_wait<0>();
-    fence_proxy_async_smem();
-    if (ok)
-      for (int kc = nk > L::kLag ? nk - L::kLag : 0; kc < nk; ++kc) mbar_arrive(full + kc % kStages);
-    if (!ok) atomicOr(a.err, 1);
-
-    // ---- epilogue
     // one verdict for all 128 epilogue threads (a reduction barrier, which also
     // publishes the column table), so the named barriers below always match
     const bool waited = mbar_wait(tfull, 0, kWaitNs);
@@ -174,16 +195,15 @@ __global__ void __launch_bounds__(160, BN == 128 ? 2 : 1) k_conv_tc(const __grid
         : "=r"(all_ok)
         : "r"((uint32_t)waited)
         : "memory");
-    const bool got = all_ok != 0;
     tc_fence_after();
-    if (!got) {
-      if (lane == 0) atomicOr(a.err, 2);
+    if (!all_ok) {
+      if (t == 0) atomicOr(a.err, 2);
     } else {
       // Two passes per 32-column TMEM chunk.  Pass 1: thread = output row,
       // scaled + biased values go transposed into shared memory (the free
       // pipeline buffers).  Pass 2: thread = (column, 8 consecutive rows):
       // 16/32-byte residual loads and view stores, coalesced along channels.
-      const int32_t rloc = warp * 32 + lane;
+      const int32_t rloc = sub * 32 + lane;
       const int32_t m = m0 + rloc;
       const bool mok = m < a.M;
       int32_t ch = m;
@@ -194,7 +214,7 @@ __global__ void __launch_bounds__(160, BN == 128 ? 2 : 1) k_conv_tc(const __grid
       for (int cb = 0, it = 0; cb < BN; cb += 32, ++it) {
         if (n0 + cb >= N) break;  // uniform over the 128 epilogue threads
         uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, r);
+        tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)cb, r);
         tmem_ld_wait();
         float* stg = stage + (it & 1) * 32 * kBM;
 #pragma unroll
@@ -260,36 +280,15 @@ __global__ void __launch_bounds__(160, BN == 128 ? 2 : 1) k_conv_tc(const __grid
         }
       }
     }
-  } else if (warp == 4 && lane == 0) {
-    // ---- MMA issuer
-    const uint32_t idesc = idesc_f16(kBM, BN, a.in.dtype == kDtBF16);
-    bool ok = true;
-    for (int kc = 0; kc < nk; ++kc) {
-      const int st = kc % kStages;
-      const uint32_t ph = (kc / kStages) & 1;
-      if (!mbar_wait(full + st, ph, kWaitNs)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t sa = smem_u32(sA + st * L::kA), sb = smem_u32(sB + st * L::kB);
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        mma_f16(tmem, sw128_kmajor_desc(sa + k * 32), sw128_kmajor_desc(sb + k * 32), idesc,
-                (kc | k) != 0);
-      mma_commit(empty + st);
-    }
-    mma_commit(tfull);
-    if (!ok) atomicOr(a.err, 4);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 4) tmem_dealloc(tmem, BN);
+  if (warp == 1) tmem_dealloc(tmem, BN);
 }
 
 template <int BN>
-cudaError_t launch_bn(const CUtensorMap& tm, const TcArgs& a, cudaStream_t st) {
+cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, cudaStream_t st) {
   static bool configured = false;
   constexpr int bytes = TcLayout<BN>::kBytes;
   if (!configured) {
@@ -300,7 +299,7 @@ cudaError_t launch_bn(const CUtensorMap& tm, const TcArgs& a, cudaStream_t st) {
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   const int mtiles = (a.M + kBM - 1) / kBM;
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)mtiles);
-  k_conv_tc<BN><<<grid, 160, bytes, st>>>(tm, a);
+  k_conv_tc<BN><<<grid, kThreads, bytes, st>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
@@ -310,11 +309,13 @@ int tc_tile_n(int64_t n_cols, int m_tiles) {
   return ((n_cols + 255) / 256) * m_tiles >= 152 ? 256 : 128;
 }
 
-cudaError_t launch_conv_tc(const void* tmap, const TcArgs& a, int bn, cudaStream_t st) {
+cudaError_t launch_conv_tc(const void* tmap_a, const void* tmap_b, const TcArgs& a, int bn,
+                           cudaStream_t st) {
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   if (N <= 0) return cudaSuccess;
-  const CUtensorMap& tm = *reinterpret_cast<const CUtensorMap*>(tmap);
-  return bn == 256 ? launch_bn<256>(tm, a, st) : launch_bn<128>(tm, a, st);
+  const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(tmap_a);
+  const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(tmap_b);
+  return bn == 256 ? launch_bn<256>(ta, tb, a, st) : launch_bn<128>(ta, tb, a, st);
 }
 
 }  // namespace cc

@@ -187,8 +187,21 @@ static void plan_fusion(Model& m) {
   }
 }
 
+static size_t lcm_size(size_t a, size_t b) {
+  size_t x = a, y = b;
+  while (y) {
+    const size_t t = x % y;
+    x = y;
+    y = t;
+  }
+  return a / x * b;
+}
+
+// Low-precision views are aligned to their row pitch (and the slot size to
+// every such pitch) so that a single 2D tensor map over the arena addresses
+// the rows of that view in every stream's slot.
 static cc_status plan_arena(Model& m) {
-  size_t off = 0, state = 0;
+  size_t off = 0, state = 0, slot_align = 256;
   const int n = (int)m.nodes.size();
   for (int i = 0; i < n; ++i) {
     NodePlan& p = m.nodes[i];
@@ -203,12 +216,17 @@ static cc_status plan_arena(Model& m) {
       r.u = p.u;
       r.dtype = v == 0 ? kDtF32 : m.lp_dtype;
       const size_t elem = v == 0 ? 4 : 2;
+      if (v > 0) {
+        const size_t pitch = (size_t)r.chans * elem;
+        off = align_up(off, lcm_size(256, pitch));
+        slot_align = lcm_size(slot_align, pitch);
+      }
       r.off = (int64_t)off;
       off = align_up(off + (size_t)r.rows * r.chans * elem, 256);
       state += (size_t)p.keep_view[v] * p.d.c_out * elem;
     }
   }
-  m.slot_bytes = std::max<size_t>(align_up(off, 256), 256);
+  m.slot_bytes = std::max<size_t>(align_up(off, slot_align), slot_align);
   m.state_bytes = state;
   return CC_OK;
 }
@@ -273,6 +291,34 @@ static cc_status upload_tc_operand(Model& m, NodePlan& p, const std::vector<floa
                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(CC_ERR_CUDA, "tensor map encoding failed (%d)", (int)r);
+  return CC_OK;
+}
+
+// Tensor map of a tensor-core layer's input view: the whole arena as rows of
+// C low-precision elements, one-row boxes of 64 elements, 128-byte swizzle.
+static cc_status encode_gather_maps(Model& m) {
+  EncodeTiledFn enc = encode_tiled();
+  for (auto& p : m.nodes) {
+    if (p.engine != 1) continue;
+    const Ring& in = m.nodes[p.d.inputs[0]].view[1 + p.d.act_in];
+    const size_t pitch = (size_t)in.chans * 2;
+    if (!enc) return fail(CC_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if (m.slot_bytes % pitch || in.off % pitch) return fail(CC_ERR_STATE, "arena view not row aligned");
+    const uint64_t rows = (uint64_t)m.max_streams * (m.slot_bytes / pitch);
+    if (rows >= (1ull << 31)) return fail(CC_ERR_NO_MEMORY, "arena too large for 32-bit row indices");
+    p.in_rows_per_slot = (int32_t)(m.slot_bytes / pitch);
+    p.in_row_off = (int32_t)(in.off / pitch);
+    const cuuint64_t dims[2] = {(cuuint64_t)in.chans, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {64, 1};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(reinterpret_cast<CUtensorMap*>(p.tmapB),
+                           m.lp_dtype == kDtBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                           2, m.arena, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(CC_ERR_CUDA, "gather tensor map encoding failed (%d)", (int)r);
+  }
   return CC_OK;
 }
 
@@ -409,6 +455,8 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
         a.phases = p.phases;
         a.out_u = w.u;
         a.in = src.view[1 + d.act_in];
+        a.in_rows_per_slot = p.in_rows_per_slot;
+        a.in_row_off = p.in_row_off;
         a.out = ov;
         if (p.fused_add >= 0) {
           a.has_skip = 1;
@@ -418,7 +466,7 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
         a.batch = batch;
         a.err = err;
         const int bn = tc_tile_n((int64_t)batch.count * ncols, p.Mpad / 128);
-        CC_CUDA(launch_conv_tc(p.tmap, a, bn, st));
+        CC_CUDA(launch_conv_tc(p.tmap, p.tmapB, a, bn, st));
       } else {
         ConvArgs a{};
         a.A = p.dA;
@@ -652,6 +700,7 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
       s = fail(CC_ERR_NO_MEMORY, "arena of %zu bytes: %s", arena_bytes, cudaGetErrorString(e));
     }
   }
+  if (!s) s = cc::encode_gather_maps(*m);
   if (!s && (cudaMalloc(&m->counters, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
              cudaMalloc(&m->seeds, sizeof(uint64_t) * m->max_streams) != cudaSuccess ||
              cudaMalloc(&m->batch_slots, sizeof(int32_t) * m->max_streams) != cudaSuccess ||

@@ -42,7 +42,9 @@ struct NodePlan {
   int32_t Mpad = 0;
   void* dA_lp = nullptr;
   float* dscale = nullptr;
-  alignas(64) unsigned char tmap[128] = {};
+  alignas(64) unsigned char tmap[128] = {};   // weights
+  alignas(64) unsigned char tmapB[128] = {};  // input view as arena rows
+  int32_t in_rows_per_slot = 0, in_row_off = 0;
 };
 
 struct TimingRec {

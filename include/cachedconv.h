@@ -192,6 +192,33 @@ cc_status cc_model_timing_read(cc_model* model, double* ms_per_node, int64_t* la
 cc_status cc_pqmf_design(int32_t bands, int32_t taps, double beta, double* analysis,
                          double* synthesis, double* cutoff);
 
+/* One cached Conv1d step that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * when they process a buffer, such as a real-time audio callback (cudaMalloc
+ * may synchronise the device and take an unbounded time, heard as a dropout)
+ * or a plug-in living inside a fixed, pre-reserved memory budget.
+ *
+ * Computes the same layer as a model [input, conv] through cc_stream_process:
+ * y[t] = bias + sum_k W[:, :, k] . act(z[t + k*dilation]), where z is the
+ * cached frames followed by x.  All device pointers, caller-owned:
+ *   x      [n][c_in] input frames; y [n][c_out] output frames
+ *   weight [c_out][c_in][kernel]; bias [c_out] or NULL
+ *   cache  [pad_left + pad_right][c_in], oldest frame first: in/out, the
+ *          frames kept between calls; all zero at the start of a stream
+ * Scratch (packed weights and the window) lives in a 16 MiB device array
+ * that every GPU loading this library holds until the process exits; a layer
+ * needing more is rejected with CC_ERR_INVALID_ARG (message in
+ * cc_last_error).  The call makes no cudaMalloc / cudaFree or other
+ * allocating call.  Its first call on a device looks up that device's copy
+ * of the array (with the device current); make this first call before any
+ * stream capture.  All calls share the one array and each overwrites it:
+ * calls that overlap on the GPU (different CUDA streams, or other threads)
+ * race; serialise them on one stream.  Asynchronous on cuda_stream. */
+cc_status cc_cached_conv1d_static(const float* x, int64_t n, int32_t c_in, int32_t c_out,
+                                  int32_t kernel, int32_t dilation, int32_t pad_left,
+                                  int32_t pad_right, int32_t act_in, const float* weight,
+                                  const float* bias, float* cache, float* y, void* cuda_stream);
+
 const char* cc_status_str(cc_status status);
 const char* cc_last_error(void);
 

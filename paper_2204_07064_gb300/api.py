@@ -68,6 +68,8 @@ _SIGNATURES = {
     "cc_model_timing": [_P, _I32],
     "cc_model_timing_read": [_P, C.POINTER(_DBL), C.POINTER(_I64), _I32],
     "cc_pqmf_design": [_I32, _I32, _DBL, C.POINTER(_DBL), C.POINTER(_DBL), C.POINTER(_DBL)],
+    "cc_cached_conv1d_static": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _P, _P,
+                                _P, _P],
     "cc_status_str": [_I32],
     "cc_last_error": [],
 }
@@ -304,3 +306,17 @@ def pqmf_analysis_weights(g):
     """Conv(1 -> bands) kernel [bands][1][taps] = g_b (correlating with g_b
     filters by its time reverse, the analysis filter h_b)."""
     return g[:, None, :].copy()
+
+
+def cached_conv1d_static(x, weight, bias, cache, y, dilation=1, pad_left=0, pad_right=0,
+                         act_in=None, cuda_stream=None):
+    """One cached Conv1d step without any device allocation (see
+    cc_cached_conv1d_static in include/cachedconv.h).  x [n][c_in],
+    weight [c_out][c_in][K], bias [c_out] or None, cache [pad_left+pad_right][c_in]
+    (updated in place), y [n][c_out]: float32 CUDA tensors."""
+    n, c_in = x.shape
+    c_out, _, k = weight.shape
+    _check(lib().cc_cached_conv1d_static(
+        _ptr(x), n, c_in, c_out, k, dilation, pad_left, pad_right, ACTS[act_in], _ptr(weight),
+        None if bias is None else _ptr(bias), _ptr(cache) if cache.numel() else None, _ptr(y),
+        _cuda_stream(cuda_stream)))

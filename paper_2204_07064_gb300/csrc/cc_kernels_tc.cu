@@ -32,11 +32,11 @@ constexpr int kBM = 128;
 constexpr int kThreads = 192;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
-// BN = 128: 3 stages (two CTAs per SM, so one CTA's epilogue overlaps the
-// other's main loop); BN = 256: 4 stages, one CTA per SM.
+// BN = 128: 2 stages (three CTAs per SM, so the CTAs' epilogues overlap
+// each other's main loops); BN = 256: 4 stages, one CTA per SM.
 template <int BN>
 struct TcLayout {
-  static constexpr int kStages = BN == 128 ? 3 : 4;
+  static constexpr int kStages = BN == 128 ? 2 : 4;
   static constexpr int kA = kBM * 128;  // one 128 x 64 low-precision tile
   static constexpr int kB = BN * 128;
   static constexpr int kBars = (2 * kStages + 1) * 8 + 8;
@@ -45,7 +45,7 @@ struct TcLayout {
 };
 
 template <int BN>
-__global__ void __launch_bounds__(kThreads, BN == 128 ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, BN == 128 ? 3 : 1)
     k_conv_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const TcArgs a) {
   using L = TcLayout<BN>;
@@ -183,8 +183,31 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 2 : 1)
         col_row[3 * BN + c] = a.has_skip ? (int32_t)ring_row(tb - a.skip_A, a.skip.rows) : 0;
       }
     }
-    // one verdict for all 128 epilogue threads (a reduction barrier, which also
-    // publishes the column table), so the named barriers below always match
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // column table complete
+    // Residual values of pass 2 (below), software-pipelined one 32-column
+    // chunk ahead: chunk 0's are requested before the accumulator is ready.
+    float4 skip_next[4][2];
+    auto fetch_skip = [&](int cb, float4 (&dst)[4][2]) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int p = t + q * 128;
+        const int c = p >> 4, g = p & 15;
+        const int32_t mb = m0 + g * 8;
+        dst[q][0] = dst[q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!a.has_skip || cb >= BN || n0 + cb + c >= N || mb >= a.M) continue;
+        const int32_t ph = a.phases > 1 ? mb / a.cout : 0;
+        const int32_t cg = mb - ph * a.cout;
+        const int col = cb + c;
+        const int32_t row = wrap_row(col_row[3 * BN + col] + ph, a.skip.rows);
+        const float4* sp = reinterpret_cast<const float4*>(a.batch.arena + col_slot[col] + a.skip.off +
+                                                           ((int64_t)row * a.skip.chans + cg) * 4);
+        dst[q][0] = __ldg(sp);
+        dst[q][1] = __ldg(sp + 1);
+      }
+    };
+    fetch_skip(0, skip_next);
+    // one verdict for all 128 epilogue threads (a reduction barrier), so the
+    // named barriers below always match
     const bool waited = mbar_wait(tfull, 0, kWaitNs);
     uint32_t all_ok;
     asm volatile(
@@ -219,6 +242,13 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 2 : 1)
         float* stg = stage + (it & 1) * 32 * kBM;
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj) stg[jj * kBM + rloc] = __uint_as_float(r[jj]) * sc + bi;
+        float4 skip_cur[4][2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          skip_cur[q][0] = skip_next[q][0];
+          skip_cur[q][1] = skip_next[q][1];
+        }
+        fetch_skip(cb + 32, skip_next);
         asm volatile("bar.sync 1, 128;" ::: "memory");
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -236,10 +266,7 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 2 : 1)
           const int col = cb + c;
           char* base = a.batch.arena + col_slot[col];
           if (a.has_skip) {
-            const int32_t row = wrap_row(col_row[3 * BN + col] + ph, a.skip.rows);
-            const float4* sp = reinterpret_cast<const float4*>(
-                base + a.skip.off + ((int64_t)row * a.skip.chans + cg) * 4);
-            const float4 s0 = __ldg(sp), s1 = __ldg(sp + 1);
+            const float4 s0 = skip_cur[q][0], s1 = skip_cur[q][1];
             x[0] += s0.x; x[1] += s0.y; x[2] += s0.z; x[3] += s0.w;
             x[4] += s1.x; x[5] += s1.y; x[6] += s1.z; x[7] += s1.w;
           }

@@ -184,6 +184,50 @@ cc_status cc_model_timing(cc_model* model, int32_t enable);
 cc_status cc_model_timing_read(cc_model* model, double* ms_per_node, int64_t* launches_per_node,
                                int32_t n_nodes);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of many real-time streams of one model.  Clients submit
+ * requests from any thread; a scheduler thread repeatedly advances, by one
+ * model step and in one batched launch chain, every stream that has a request
+ * still owed output and a full step of input buffered (oldest request first,
+ * at most max_batch streams).  Streams that arrive while a batch is on the GPU
+ * join the next batch; caches stay resident in the arena slots.  Output
+ * beyond what a request asked for waits in the stream's FIFO, so requests
+ * shorter than a model step are served from it.  Batch sizes are padded to a
+ * multiple of `bucket` with a scratch stream slot (taken at creation); the
+ * launch chain of each bucket is replayed from a CUDA graph (use_graphs) and
+ * its tile shapes come from the model's autotuner (autotune: each
+ * tensor-core layer is timed with 128- and 256-column tiles on the scratch
+ * slot and the faster is kept). */
+typedef struct cc_server cc_server;
+typedef struct {
+  int32_t max_batch;  /* streams per launch chain, <= the model's max_streams - 1 */
+  int32_t bucket;     /* batch sizes are padded to a multiple of this (0: 32)      */
+  int32_t use_graphs; /* replay each bucket's launch chain from a CUDA graph        */
+  int32_t autotune;   /* choose tensor-core tile shapes per bucket by timing         */
+} cc_server_config;
+
+/* Needs one free stream slot (the padding scratch); NO_MEMORY otherwise. */
+cc_status cc_server_create(cc_model* model, const cc_server_config* config, cc_server** out);
+/* Stops the scheduler after its current batch; pending requests are dropped. */
+cc_status cc_server_destroy(cc_server* server);
+/* count requests: request i gives stream streams[i] n_in[i] input frames
+ * (host, [n_in][in_channels], copied in) and asks for n_out[i] output frames
+ * written to the host buffer out[i] ([n_out][out_channels], written by the
+ * scheduler thread; valid once cc_server_poll reports tags[i]).  A stream's
+ * requests complete in order. */
+cc_status cc_server_submit(cc_server* server, int32_t count, cc_stream* const* streams,
+                           const float* const* in, const int64_t* n_in, float* const* out,
+                           const int64_t* n_out, const uint64_t* tags);
+/* Up to max completed requests: tag, submit and completion times (ns,
+ * steady clock).  Returns the scheduler's error if it stopped on one. */
+cc_status cc_server_poll(cc_server* server, int32_t max, uint64_t* tags, int64_t* submit_ns,
+                         int64_t* done_ns, int32_t* got);
+/* Forgets a stream (its pending requests are dropped) once it is not in the
+ * batch on the GPU; call before cc_stream_destroy of a served stream. */
+cc_status cc_server_remove(cc_server* server, cc_stream* stream);
+cc_status cc_server_stats(cc_server* server, int64_t* batches, int64_t* stream_steps,
+                          int64_t* gpu_ns, int64_t* max_batch);
+
 /* Host utility: a cosine-modulated pseudo-QMF bank (bands x taps) with a
  * Kaiser(beta) prototype whose cutoff minimises the prototype autocorrelation
  * at lags 2*bands*l (Lin & Vaidyanathan 1998).  analysis / synthesis:

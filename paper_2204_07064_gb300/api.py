@@ -70,6 +70,12 @@ _SIGNATURES = {
     "cc_pqmf_design": [_I32, _I32, _DBL, C.POINTER(_DBL), C.POINTER(_DBL), C.POINTER(_DBL)],
     "cc_cached_conv1d_static": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _P, _P,
                                 _P, _P],
+    "cc_server_create": [_P, C.c_void_p, C.POINTER(_P)],
+    "cc_server_destroy": [_P],
+    "cc_server_submit": [_P, _I32, _P, _P, _P, _P, _P, _P],
+    "cc_server_poll": [_P, _I32, _P, _P, _P, C.POINTER(_I32)],
+    "cc_server_remove": [_P, _P],
+    "cc_server_stats": [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
     "cc_status_str": [_I32],
     "cc_last_error": [],
 }
@@ -320,3 +326,76 @@ def cached_conv1d_static(x, weight, bias, cache, y, dilation=1, pad_left=0, pad_
         _ptr(x), n, c_in, c_out, k, dilation, pad_left, pad_right, ACTS[act_in], _ptr(weight),
         None if bias is None else _ptr(bias), _ptr(cache) if cache.numel() else None, _ptr(y),
         _cuda_stream(cuda_stream)))
+
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("bucket", C.c_int32), ("use_graphs", C.c_int32),
+                ("autotune", C.c_int32)]
+
+
+class Server:
+    """Continuous-batching scheduler of the library (cc_server_*): requests
+    are host numpy buffers; completion times come back from poll()."""
+
+    def __init__(self, model, max_batch, bucket=32, use_graphs=True, autotune=True):
+        cfg = ServerConfig(max_batch, bucket, int(bool(use_graphs)), int(bool(autotune)))
+        h = _P()
+        _check(lib().cc_server_create(model.handle, C.byref(cfg), C.byref(h)))
+        self.handle = h
+        self.model = model
+        self._keep = []
+
+    def submit(self, streams, ins, n_in, outs, n_out, tags):
+        """streams: list of Stream; ins / outs: sequences of float32 numpy
+        arrays (or raw addresses as uint64) -- the caller keeps them alive until
+        completion; n_in / n_out: frames; tags: uint64."""
+        count = len(streams)
+        if count == 0:
+            return
+        sp = np.array([s.handle.value for s in streams], dtype=np.uint64)
+        ip = np.asarray([x if isinstance(x, (int, np.integer)) else (0 if x is None else x.ctypes.data)
+                         for x in ins], dtype=np.uint64)
+        op = np.asarray([x if isinstance(x, (int, np.integer)) else (0 if x is None else x.ctypes.data)
+                         for x in outs], dtype=np.uint64)
+        ni = np.ascontiguousarray(n_in, dtype=np.int64)
+        no = np.ascontiguousarray(n_out, dtype=np.int64)
+        tg = np.ascontiguousarray(tags, dtype=np.uint64)
+        _check(lib().cc_server_submit(self.handle, count, sp.ctypes.data, ip.ctypes.data, ni.ctypes.data,
+                                      op.ctypes.data, no.ctypes.data, tg.ctypes.data))
+
+    def submit_raw(self, count, stream_ptrs, in_ptrs, n_in, out_ptrs, n_out, tags):
+        """Same as submit() with uint64 / int64 numpy arrays of addresses."""
+        if count:
+            _check(lib().cc_server_submit(self.handle, count, stream_ptrs.ctypes.data, in_ptrs.ctypes.data,
+                                          n_in.ctypes.data, out_ptrs.ctypes.data, n_out.ctypes.data,
+                                          tags.ctypes.data))
+
+    def poll(self, max_items=65536):
+        tags = np.empty(max_items, np.uint64)
+        sub = np.empty(max_items, np.int64)
+        done = np.empty(max_items, np.int64)
+        got = _I32()
+        _check(lib().cc_server_poll(self.handle, max_items, tags.ctypes.data, sub.ctypes.data, done.ctypes.data,
+                                    C.byref(got)))
+        n = got.value
+        return tags[:n], sub[:n], done[:n]
+
+    def remove(self, stream):
+        _check(lib().cc_server_remove(self.handle, stream.handle))
+
+    def stats(self):
+        v = [_I64() for _ in range(4)]
+        _check(lib().cc_server_stats(self.handle, *[C.byref(x) for x in v]))
+        return dict(batches=v[0].value, stream_steps=v[1].value, gpu_ns=v[2].value, max_batch=v[3].value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().cc_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

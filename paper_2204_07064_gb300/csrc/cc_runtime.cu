@@ -465,7 +465,7 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
         }
         a.batch = batch;
         a.err = err;
-        const int bn = tc_tile_n((int64_t)batch.count * ncols, p.Mpad / 128);
+        const int bn = tile_n_for(p, (int64_t)batch.count * ncols);
         CC_CUDA(launch_conv_tc(p.tmap, p.tmapB, a, bn, st));
       } else {
         ConvArgs a{};
@@ -523,6 +523,64 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
     if ((s = end())) return s;
   }
   CC_CUDA(launch_advance(batch, steps, st));
+  return CC_OK;
+}
+
+int32_t Model::tile_n_for(const NodePlan& p, int64_t n_cols) const {
+  if (force_tile_n) return force_tile_n;
+  auto it = p.tile_n.find(n_cols);
+  if (it != p.tile_n.end()) return it->second;
+  return tc_tile_n(n_cols, p.Mpad / 128);
+}
+
+// Project autotuner: times one launch chain with every tensor-core layer on
+// 128-column tiles and one with 256-column tiles (CUDA events around each
+// launch), and keeps the faster shape per layer for this launch width.  The
+// chain runs on the given slots, whose rings and step counters it advances:
+// callers pass scratch slots.
+cc_status Model::autotune(const int32_t* d_slots, int32_t count, const float* in, int64_t in_stride,
+                          float* out, int64_t out_stride, cudaStream_t st) {
+  const int n = (int)nodes.size();
+  std::vector<double> best(n, 1e30);
+  std::vector<int32_t> pick(n, 0);
+  const Batch b = batch_for(d_slots, count);
+  for (const int32_t cand : {128, 256}) {
+    force_tile_n = cand;
+    cc_status s = run_chain(b, in, in_stride, out, out_stride, 1, st);  // warm (kernel attributes)
+    if (s) {
+      force_tile_n = 0;
+      return s;
+    }
+    CC_CUDA(cudaStreamSynchronize(st));
+    timing_on = true;
+    timing_recs.clear();
+    event_pool_used = 0;
+    s = run_chain(b, in, in_stride, out, out_stride, 1, st);
+    timing_on = false;
+    force_tile_n = 0;
+    if (s) return s;
+    CC_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> ms(n, 0.0);
+    for (auto& rec : timing_recs) {
+      float t = 0.f;
+      CC_CUDA(cudaEventElapsedTime(&t, rec.start, rec.stop));
+      ms[rec.node] += t;
+    }
+    for (int i = 0; i < n; ++i)
+      if (nodes[i].engine == 1 && ms[i] < best[i]) {
+        best[i] = ms[i];
+        pick[i] = cand;
+      }
+  }
+  timing_recs.clear();
+  event_pool_used = 0;
+  for (int i = 0; i < n; ++i) {
+    NodePlan& p = nodes[i];
+    if (p.engine != 1) continue;
+    const NodePlan& src = nodes[p.d.inputs[0]];
+    const int64_t cols = (int64_t)count * (p.d.op == CC_OP_CONVT ? src.u : p.u);
+    p.tile_n[cols] = pick[i];
+  }
   return CC_OK;
 }
 
@@ -646,6 +704,11 @@ struct cc_stream {
   uint64_t seed;
   int32_t* d_slot;
 };
+
+namespace cc {
+int32_t stream_slot(const cc_stream* s) { return s->slot; }
+Model* stream_model(const cc_stream* s) { return s->model; }
+}  // namespace cc
 
 extern "C" {
 

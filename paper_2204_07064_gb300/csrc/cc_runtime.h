@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -45,6 +46,7 @@ struct NodePlan {
   alignas(64) unsigned char tmap[128] = {};   // weights
   alignas(64) unsigned char tmapB[128] = {};  // input view as arena rows
   int32_t in_rows_per_slot = 0, in_row_off = 0;
+  std::map<int64_t, int32_t> tile_n;  // autotuned N tile by launch width (columns), 0: heuristic
 };
 
 struct TimingRec {
@@ -82,7 +84,12 @@ struct Model {
   std::vector<cudaEvent_t> event_pool;
   size_t event_pool_used = 0;
 
+  int32_t force_tile_n = 0;  // autotuning: every tensor-core layer uses this N tile
+
   ~Model();
+  int32_t tile_n_for(const NodePlan& p, int64_t n_cols) const;
+  cc_status autotune(const int32_t* d_slots, int32_t count, const float* in, int64_t in_stride, float* out,
+                     int64_t out_stride, cudaStream_t st);
   Batch batch_for(const int32_t* d_slots, int32_t count) const;
   cc_status process(const int32_t* d_slots, int32_t count, const float* in, int64_t in_stride,
                     int64_t n_in, float* out, int64_t out_stride, int64_t n_out, cudaStream_t st);

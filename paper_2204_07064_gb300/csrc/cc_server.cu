@@ -1,0 +1,397 @@
+// Serving loop: continuous batching of many real-time streams of one model.
+//
+// Clients submit requests (a stream, some input frames, a number of output
+// frames wanted) from any thread.  A scheduler thread repeatedly takes every
+// stream that has a request still waiting for output and at least one model
+// step of input buffered, and advances all of them by one step in a single
+// launch chain (the streams' caches stay resident in their arena slots; the
+// batch is a device list of slots).  Streams that arrive while a batch is on
+// the GPU join the next one.  Output beyond what a request asked for waits in
+// the stream's FIFO for its next request, so requests shorter than a model
+// step (e.g. 512-sample buffers of a decoder that emits 2048 samples per
+// step) are served from the FIFO.  Each batch size is padded to a bucket with
+// a scratch slot and its launch chain is replayed from a CUDA graph; the tile
+// shapes of each bucket come from the model's autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/cachedconv.h"
+#include "cc_internal.h"
+#include "cc_runtime.h"
+
+namespace cc {
+extern thread_local std::string g_last_error;
+int32_t stream_slot(const cc_stream* s);
+Model* stream_model(const cc_stream* s);
+}  // namespace cc
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Request {
+  float* out;
+  int64_t n_out;  // output frames still owed
+  int64_t done_frames = 0;
+  uint64_t tag;
+  int64_t submit_ns;
+};
+
+struct StreamQueue {
+  std::deque<float> in;   // buffered input (interleaved frames)
+  std::deque<float> out;  // produced, not yet delivered output
+  std::deque<Request> reqs;
+  int64_t owed = 0;  // output frames requested but not delivered
+};
+
+struct Completion {
+  uint64_t tag;
+  int64_t submit_ns, done_ns;
+};
+
+}  // namespace
+
+struct cc_server {
+  cc::Model* m = nullptr;
+  cc_server_config cfg{};
+  int32_t cin = 0, cout = 0, in_step = 0, out_step = 0;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  // device / pinned staging
+  float *d_in = nullptr, *d_out = nullptr, *h_in = nullptr, *h_out = nullptr;
+  int32_t *d_slots = nullptr, *h_slots = nullptr;
+  int32_t* d_scratch_slots = nullptr;  // cap copies of the scratch slot
+  int32_t cap = 0;  // padded batch capacity
+  cc_stream* scratch = nullptr;
+  std::map<int32_t, cudaGraphExec_t> graphs;
+  std::unordered_set<int32_t> tuned;
+  // client state
+  std::mutex mu;
+  std::condition_variable cv, idle_cv;
+  std::unordered_map<cc_stream*, StreamQueue> q;
+  std::unordered_set<cc_stream*> in_flight;
+  std::vector<Completion> done;
+  bool stop = false;
+  cc_status error = CC_OK;
+  std::string error_msg;
+  std::thread th;
+  // statistics
+  int64_t batches = 0, stream_steps = 0, gpu_ns = 0, max_batch_seen = 0;
+
+  int32_t bucket(int32_t count) const {
+    const int32_t g = cfg.bucket > 0 ? cfg.bucket : 32;
+    int32_t b = (count + g - 1) / g * g;
+    return std::min(b, cap);
+  }
+  bool needs_step(const StreamQueue& s) const {
+    return s.owed * cout > (int64_t)s.out.size() && (int64_t)s.in.size() >= (int64_t)in_step * cin;
+  }
+  void serve_fifo(StreamQueue& s, int64_t t) {
+    while (!s.reqs.empty()) {
+      Request& r = s.reqs.front();
+      const int64_t avail = (int64_t)s.out.size() / cout;
+      const int64_t take = std::min(avail, r.n_out - r.done_frames);
+      for (int64_t i = 0; i < take * cout; ++i) {
+        r.out[r.done_frames * cout + i] = s.out.front();
+        s.out.pop_front();
+      }
+      r.done_frames += take;
+      s.owed -= take;
+      if (r.done_frames < r.n_out) break;
+      done.push_back(Completion{r.tag, r.submit_ns, t});
+      s.reqs.pop_front();
+    }
+  }
+  cc_status gpu_step(int32_t count, int32_t padded);
+  void loop();
+};
+
+namespace {
+
+#define SRV_CUDA(call)                                                                             \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return cc::fail(CC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+}  // namespace
+
+cc_status cc_server::gpu_step(int32_t count, int32_t padded) {
+  const int64_t is = (int64_t)in_step * cin, os = (int64_t)out_step * cout;
+  if ((cfg.autotune && !tuned.count(padded)) || (cfg.use_graphs && !graphs.count(padded))) {
+    // First batch of this bucket: tune tile shapes and warm the kernels up on
+    // a batch made of the scratch slot only (its rings are never read back).
+    const cc::Batch scratch_batch = m->batch_for(d_scratch_slots, padded);
+    if (cfg.autotune && !tuned.count(padded)) {
+      cc_status s = m->autotune(d_scratch_slots, padded, d_in, is, d_out, os, st);
+      if (s) return s;
+      tuned.insert(padded);
+    } else {
+      cc_status s = m->run_chain(scratch_batch, d_in, is, d_out, os, 1, st);
+      if (s) return s;
+    }
+    SRV_CUDA(cudaStreamSynchronize(st));
+    if (cfg.use_graphs) {
+      // capture the chain of this bucket; it reads the slot list from d_slots
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      SRV_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      cc_status s = m->run_chain(m->batch_for(d_slots, padded), d_in, is, d_out, os, 1, st);
+      cudaError_t ce = cudaStreamEndCapture(st, &g);
+      if (s) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (ce != cudaSuccess) return cc::fail(CC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+      ce = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) return cc::fail(CC_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ce));
+      graphs.emplace(padded, ge);
+    }
+  }
+  SRV_CUDA(cudaMemcpyAsync(d_slots, h_slots, sizeof(int32_t) * padded, cudaMemcpyHostToDevice, st));
+  SRV_CUDA(cudaMemcpyAsync(d_in, h_in, sizeof(float) * (size_t)padded * is, cudaMemcpyHostToDevice, st));
+  if (cfg.use_graphs) {
+    SRV_CUDA(cudaGraphLaunch(graphs.at(padded), st));
+  } else {
+    cc_status s = m->run_chain(m->batch_for(d_slots, padded), d_in, is, d_out, os, 1, st);
+    if (s) return s;
+  }
+  SRV_CUDA(cudaMemcpyAsync(h_out, d_out, sizeof(float) * (size_t)count * os, cudaMemcpyDeviceToHost, st));
+  SRV_CUDA(cudaStreamSynchronize(st));
+  return CC_OK;
+}
+
+void cc_server::loop() {
+  std::vector<cc_stream*> batch;
+  std::unique_lock<std::mutex> lk(mu);
+  while (!stop) {
+    // every stream with a request waiting and a step of input, oldest request first
+    batch.clear();
+    for (auto& kv : q)
+      if (needs_step(kv.second)) batch.push_back(kv.first);
+    if ((int32_t)batch.size() > cfg.max_batch) {
+      std::nth_element(batch.begin(), batch.begin() + cfg.max_batch, batch.end(),
+                       [&](cc_stream* x, cc_stream* y) {
+                         return q[x].reqs.front().submit_ns < q[y].reqs.front().submit_ns;
+                       });
+      batch.resize(cfg.max_batch);
+    }
+    if (batch.empty()) {
+      cv.wait_for(lk, std::chrono::milliseconds(2));
+      continue;
+    }
+    const int32_t count = (int32_t)batch.size();
+    const int32_t padded = bucket(count);
+    const size_t step_in = (size_t)in_step * cin;
+    for (int32_t i = 0; i < count; ++i) {
+      StreamQueue& s = q[batch[i]];
+      h_slots[i] = cc::stream_slot(batch[i]);
+      for (size_t k = 0; k < step_in; ++k) {
+        h_in[i * step_in + k] = s.in.front();
+        s.in.pop_front();
+      }
+      in_flight.insert(batch[i]);
+    }
+    const int32_t sslot = cc::stream_slot(scratch);
+    for (int32_t i = count; i < padded; ++i) {
+      h_slots[i] = sslot;
+      std::memset(h_in + i * step_in, 0, step_in * sizeof(float));
+    }
+    lk.unlock();
+    const int64_t t0 = now_ns();
+    cc_status s = gpu_step(count, padded);
+    const int64_t t1 = now_ns();
+    lk.lock();
+    if (s) {
+      error = s;
+      error_msg = cc::g_last_error;
+      stop = true;
+      in_flight.clear();
+      idle_cv.notify_all();
+      break;
+    }
+    ++batches;
+    stream_steps += count;
+    gpu_ns += t1 - t0;
+    max_batch_seen = std::max<int64_t>(max_batch_seen, count);
+    const size_t step_out = (size_t)out_step * cout;
+    for (int32_t i = 0; i < count; ++i) {
+      auto it = q.find(batch[i]);
+      if (it == q.end()) continue;
+      StreamQueue& sq = it->second;
+      sq.out.insert(sq.out.end(), h_out + i * step_out, h_out + (i + 1) * step_out);
+      serve_fifo(sq, t1);
+    }
+    in_flight.clear();
+    idle_cv.notify_all();
+  }
+}
+
+extern "C" {
+
+cc_status cc_server_create(cc_model* model, const cc_server_config* config, cc_server** out) {
+  using cc::fail;
+  if (!model || !config || !out) return fail(CC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  auto* m = reinterpret_cast<cc::Model*>(model);
+  if (config->max_batch <= 0 || config->max_batch > m->max_streams)
+    return fail(CC_ERR_INVALID_ARG, "max_batch must be in [1, max_streams]");
+  auto* s = new cc_server();
+  s->m = m;
+  s->cfg = *config;
+  s->cin = m->nodes.front().d.c_in;
+  s->cout = m->nodes.back().d.c_out;
+  s->in_step = m->in_per_step;
+  s->out_step = m->nodes.back().u;
+  const int32_t g = config->bucket > 0 ? config->bucket : 32;
+  s->cap = (config->max_batch + g - 1) / g * g;
+  cc_status r = CC_OK;
+  auto cleanup = [&]() {
+    if (s->scratch) cc_stream_destroy(s->scratch);
+    if (s->d_in) cudaFree(s->d_in);
+    if (s->d_out) cudaFree(s->d_out);
+    if (s->d_slots) cudaFree(s->d_slots);
+    if (s->h_in) cudaFreeHost(s->h_in);
+    if (s->h_out) cudaFreeHost(s->h_out);
+    if (s->h_slots) cudaFreeHost(s->h_slots);
+    if (s->d_scratch_slots) cudaFree(s->d_scratch_slots);
+    if (s->st) cudaStreamDestroy(s->st);
+    delete s;
+  };
+  // the scratch slot pads batches to their bucket (its contents are never read back)
+  r = cc_stream_create(model, 0, nullptr, &s->scratch);
+  if (r) {
+    cleanup();
+    return fail(CC_ERR_NO_MEMORY, "the server needs one free stream slot for padding: %s",
+                cc::g_last_error.c_str());
+  }
+  const size_t nin = (size_t)s->cap * s->in_step * s->cin, nout = (size_t)s->cap * s->out_step * s->cout;
+  if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&s->d_in, nin * 4) != cudaSuccess || cudaMalloc(&s->d_out, nout * 4) != cudaSuccess ||
+      cudaMalloc(&s->d_slots, sizeof(int32_t) * s->cap) != cudaSuccess ||
+      cudaMallocHost(&s->h_in, nin * 4) != cudaSuccess || cudaMallocHost(&s->h_out, nout * 4) != cudaSuccess ||
+      cudaMallocHost(&s->h_slots, sizeof(int32_t) * s->cap) != cudaSuccess ||
+      cudaMalloc(&s->d_scratch_slots, sizeof(int32_t) * s->cap) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return fail(CC_ERR_NO_MEMORY, "server buffers");
+  }
+  {
+    std::vector<int32_t> fill(s->cap, cc::stream_slot(s->scratch));
+    if (cudaMemcpy(s->d_scratch_slots, fill.data(), sizeof(int32_t) * s->cap, cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      cleanup();
+      return fail(CC_ERR_CUDA, "server scratch slot list upload failed");
+    }
+  }
+  cudaGetDevice(&s->device);
+  s->th = std::thread([s]() {
+    cudaSetDevice(s->device);
+    s->loop();
+  });
+  *out = s;
+  return CC_OK;
+}
+
+cc_status cc_server_destroy(cc_server* s) {
+  if (!s) return cc::fail(CC_ERR_INVALID_ARG, "null server");
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->th.joinable()) s->th.join();
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  cc_stream_destroy(s->scratch);
+  cudaFree(s->d_in);
+  cudaFree(s->d_out);
+  cudaFree(s->d_slots);
+  cudaFreeHost(s->h_in);
+  cudaFreeHost(s->h_out);
+  cudaFreeHost(s->h_slots);
+  cudaFree(s->d_scratch_slots);
+  cudaStreamDestroy(s->st);
+  delete s;
+  return CC_OK;
+}
+
+cc_status cc_server_submit(cc_server* s, int32_t count, cc_stream* const* streams, const float* const* in,
+                           const int64_t* n_in, float* const* out, const int64_t* n_out,
+                           const uint64_t* tags) {
+  using cc::fail;
+  if (!s || count < 0 || (count && (!streams || !n_in || !n_out || !tags)))
+    return fail(CC_ERR_INVALID_ARG, "null argument");
+  const int64_t t = now_ns();
+  std::lock_guard<std::mutex> g(s->mu);
+  if (s->error) return fail(s->error, "server stopped: %s", s->error_msg.c_str());
+  for (int32_t i = 0; i < count; ++i) {
+    cc_stream* st = streams[i];
+    if (!st || cc::stream_model(st) != s->m) return fail(CC_ERR_INVALID_ARG, "request %d: stream of another model", i);
+    if (n_in[i] < 0 || n_out[i] < 0) return fail(CC_ERR_INVALID_ARG, "request %d: negative length", i);
+    if ((n_in[i] && (!in || !in[i])) || (n_out[i] && (!out || !out[i])))
+      return fail(CC_ERR_INVALID_ARG, "request %d: null buffer", i);
+  }
+  for (int32_t i = 0; i < count; ++i) {
+    StreamQueue& q = s->q[streams[i]];
+    if (n_in[i]) q.in.insert(q.in.end(), in[i], in[i] + n_in[i] * s->cin);
+    q.owed += n_out[i];
+    q.reqs.push_back(Request{n_out[i] ? out[i] : nullptr, n_out[i], 0, tags[i], t});
+    s->serve_fifo(q, t);
+  }
+  s->cv.notify_one();
+  return CC_OK;
+}
+
+cc_status cc_server_poll(cc_server* s, int32_t max, uint64_t* tags, int64_t* submit_ns, int64_t* done_ns,
+                         int32_t* got) {
+  if (!s || !got || max < 0) return cc::fail(CC_ERR_INVALID_ARG, "null argument");
+  std::lock_guard<std::mutex> g(s->mu);
+  const int32_t n = std::min<int32_t>(max, (int32_t)s->done.size());
+  for (int32_t i = 0; i < n; ++i) {
+    if (tags) tags[i] = s->done[i].tag;
+    if (submit_ns) submit_ns[i] = s->done[i].submit_ns;
+    if (done_ns) done_ns[i] = s->done[i].done_ns;
+  }
+  s->done.erase(s->done.begin(), s->done.begin() + n);
+  *got = n;
+  if (s->error) return cc::fail(s->error, "server stopped: %s", s->error_msg.c_str());
+  return CC_OK;
+}
+
+cc_status cc_server_remove(cc_server* s, cc_stream* stream) {
+  if (!s || !stream) return cc::fail(CC_ERR_INVALID_ARG, "null argument");
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->idle_cv.wait(lk, [&] { return !s->in_flight.count(stream) || s->stop; });
+  s->q.erase(stream);
+  return CC_OK;
+}
+
+cc_status cc_server_stats(cc_server* s, int64_t* batches, int64_t* stream_steps, int64_t* gpu_ns,
+                          int64_t* max_batch) {
+  if (!s) return cc::fail(CC_ERR_INVALID_ARG, "null server");
+  std::lock_guard<std::mutex> g(s->mu);
+  if (batches) *batches = s->batches;
+  if (stream_steps) *stream_steps = s->stream_steps;
+  if (gpu_ns) *gpu_ns = s->gpu_ns;
+  if (max_batch) *max_batch = s->max_batch_seen;
+  return CC_OK;
+}
+
+}  // extern "C"

@@ -181,6 +181,154 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_serving(args):
+    """Serving run through the library's scheduler (cc_server_*): streams
+    arrive Poisson(lambda), live U[5, 60] s, draw a buffer size from
+    {512, 1024, 2048, 4096} and submit one request per buffer period, paced in
+    wall-clock time; admission by arena slots (cap concurrent streams).  With
+    --serve-fixed N, N streams of 2048-sample buffers run for the whole time.
+    Latency = submit -> output ready, per request; deadline = buffer duration."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2204_07064_gb300 import api
+
+    torch.cuda.set_device(0)
+    cap = args.serve_cap if not args.serve_fixed else args.serve_fixed
+    nodes, params, model = build_decoder("bf16", cap + 1)
+    server = api.Server(model, max_batch=cap, bucket=32, use_graphs=True, autotune=True)
+    rng = np.random.default_rng(3)
+    lam = 200.0
+    sizes = np.array([512, 1024, 2048, 4096])
+    ring = 4  # output buffers per stream (requests in flight per stream)
+    pool = rng.standard_normal((4096, 128)).astype(np.float32)
+    outs = np.zeros((cap, ring, 4096), np.float32)
+    pool_base, out_base = pool.ctypes.data, outs.ctypes.data
+    active = np.zeros(cap, bool)
+    handles = [None] * cap
+    hptr = np.zeros(cap, np.uint64)
+    B = np.zeros(cap, np.int64)
+    next_due = np.zeros(cap, np.int64)
+    end_ns = np.zeros(cap, np.int64)
+    asked = np.zeros(cap, np.int64)
+    sent = np.zeros(cap, np.int64)
+    nreq = np.zeros(cap, np.int64)
+    outstanding = np.zeros(cap, np.int64)
+    gen = np.zeros(cap, np.int64)
+    warm_s, run_s = args.serve_warmup, args.serve_seconds
+    t_start = time.perf_counter_ns()
+    t_meas = t_start + int(warm_s * 1e9)
+    t_end = t_meas + int(run_s * 1e9)
+    lat, lat_b, conc = [], [], []
+    rejected = admitted = 0
+    delivered = 0
+    clocks = ClockSampler(0)
+    sampled = False
+    last = t_start
+    if args.serve_fixed:
+        for i in range(cap):
+            handles[i] = model.stream(seed=i)
+            hptr[i] = handles[i].handle.value
+            active[i], B[i], next_due[i], end_ns[i] = True, 2048, t_start + int(rng.uniform(0, 2048 / SR) * 1e9), 1 << 62
+    while True:
+        now = time.perf_counter_ns()
+        if now >= t_end:
+            break
+        if not sampled and now >= t_meas:
+            clocks.start()
+            sampled = True
+        dt = (now - last) / 1e9
+        last = now
+        if not args.serve_fixed:
+            # departures (once nothing is in flight), then Poisson arrivals
+            gone = np.nonzero(active & (end_ns <= now) & (outstanding == 0))[0]
+            for i in gone:
+                server.remove(handles[i])
+                handles[i].close()
+                handles[i] = None
+                active[i] = False
+            for _ in range(rng.poisson(lam * dt)):
+                free = np.nonzero(~active)[0]
+                if len(free) == 0:
+                    rejected += 1
+                    continue
+                i = int(free[0])
+                try:
+                    handles[i] = model.stream(seed=int(rng.integers(1 << 62)))
+                except api.CCError:
+                    rejected += 1
+                    continue
+                admitted += 1
+                hptr[i] = handles[i].handle.value
+                active[i], B[i] = True, int(rng.choice(sizes))
+                next_due[i] = now
+                end_ns[i] = now + int(rng.uniform(5, 60) * 1e9)
+                asked[i] = sent[i] = nreq[i] = outstanding[i] = 0
+                gen[i] += 1
+        due = np.nonzero(active & (next_due <= now) & (outstanding < ring))[0]
+        if len(due):
+            b = B[due]
+            asked[due] += b
+            need = -(-asked[due] // 2048)
+            n_in = need - sent[due]
+            sent[due] = need
+            frame = (due * 61 + nreq[due] * 3) % (4096 - 2)
+            in_ptr = (pool_base + frame * 128 * 4).astype(np.uint64)
+            out_ptr = (out_base + ((due * ring + nreq[due] % ring) * 4096) * 4).astype(np.uint64)
+            tags = ((gen[due] << 40) | (due << 24) | (nreq[due] & 0xFFFFFF)).astype(np.uint64)
+            server.submit_raw(len(due), np.ascontiguousarray(hptr[due]), in_ptr, n_in.astype(np.int64),
+                              out_ptr, b.astype(np.int64), tags)
+            nreq[due] += 1
+            outstanding[due] += 1
+            next_due[due] += (b * 1e9 / SR).astype(np.int64)
+        tags, sub, fin = server.poll()
+        if len(tags):
+            idx = ((tags >> 24) & 0xFFFF).astype(np.int64)
+            g = (tags >> 40).astype(np.int64)
+            live = g == gen[idx]
+            np.subtract.at(outstanding, idx[live], 1)
+            if now >= t_meas:
+                lat.extend(((fin - sub) / 1e6).tolist())
+                lat_b.extend(B[idx].tolist())
+                delivered += int(B[idx].sum())
+        if now >= t_meas:
+            conc.append(int(active.sum()))
+        time.sleep(0.0005)
+    clk = clocks.stop() if sampled else None
+    st = server.stats()
+    server.close()
+    lat = np.asarray(lat)
+    lat_b = np.asarray(lat_b)
+    per_b = {}
+    for b in sizes:
+        m = lat_b == b
+        if m.any():
+            per_b[str(int(b))] = {"p50_ms": float(np.percentile(lat[m], 50)),
+                                  "p99_ms": float(np.percentile(lat[m], 99)),
+                                  "deadline_ms": 1000.0 * b / SR,
+                                  "met": float(np.mean(lat[m] < 1000.0 * b / SR)), "requests": int(m.sum())}
+    line = {
+        "metric": METRIC, "value": delivered / run_s / SR, "unit": "streams", "n_gpus": 1,
+        "steps": int(st["batches"]), "warmup": warm_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "serving-bf16" if not args.serve_fixed else f"serving-bf16-fixed{cap}",
+                   "arrivals_per_s": 0 if args.serve_fixed else lam, "cap_streams": cap,
+                   "buffer_samples": "2048" if args.serve_fixed else "U{512,1024,2048,4096}",
+                   "lifetime_s": None if args.serve_fixed else "U[5,60]", "seconds": run_s},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)) if len(lat) else None,
+                       "p99": float(np.percentile(lat, 99)) if len(lat) else None, "per_buffer": per_b,
+                       "met_deadline": float(np.mean([v["met"] for v in per_b.values()])) if per_b else None},
+        "streams": {"mean_concurrent": float(np.mean(conc)) if conc else 0, "max_concurrent": int(max(conc or [0])),
+                    "admitted": admitted, "rejected": rejected},
+        "server": {"batches": st["batches"], "stream_steps": st["stream_steps"], "max_batch": st["max_batch"],
+                   "gpu_busy": st["gpu_ns"] / ((warm_s + run_s) * 1e9)},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -192,11 +340,18 @@ def main():
     ap.add_argument("--flush-l2", action="store_true", help="write 256 MB between steps")
     ap.add_argument("--only-timed", action="store_true",
                     help="skip the e2e, FP32-comparison and CPU-baseline measurements (profiling)")
+    ap.add_argument("--serving", action="store_true", help="run the serving simulation instead")
+    ap.add_argument("--serve-seconds", type=float, default=120.0)
+    ap.add_argument("--serve-warmup", type=float, default=10.0)
+    ap.add_argument("--serve-cap", type=int, default=2048)
+    ap.add_argument("--serve-fixed", type=int, default=0, help="N fixed streams of 2048-sample buffers")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.serving:
+        return run_serving(args)
 
     import torch
 

@@ -53,9 +53,28 @@ struct Request {
   int64_t submit_ns;
 };
 
+// Contiguous float FIFO (block copies; the consumed prefix is dropped lazily).
+struct FloatFifo {
+  std::vector<float> buf;
+  size_t head = 0;
+  size_t size() const { return buf.size() - head; }
+  void push(const float* p, size_t n) { buf.insert(buf.end(), p, p + n); }
+  void pop(float* dst, size_t n) {
+    std::memcpy(dst, buf.data() + head, n * sizeof(float));
+    head += n;
+    if (head == buf.size()) {
+      buf.clear();
+      head = 0;
+    } else if (head > 4096 && head * 2 > buf.size()) {
+      buf.erase(buf.begin(), buf.begin() + head);
+      head = 0;
+    }
+  }
+};
+
 struct StreamQueue {
-  std::deque<float> in;   // buffered input (interleaved frames)
-  std::deque<float> out;  // produced, not yet delivered output
+  FloatFifo in;   // buffered input (interleaved frames)
+  FloatFifo out;  // produced, not yet delivered output
   std::deque<Request> reqs;
   int64_t owed = 0;  // output frames requested but not delivered
 };
@@ -107,10 +126,7 @@ struct cc_server {
       Request& r = s.reqs.front();
       const int64_t avail = (int64_t)s.out.size() / cout;
       const int64_t take = std::min(avail, r.n_out - r.done_frames);
-      for (int64_t i = 0; i < take * cout; ++i) {
-        r.out[r.done_frames * cout + i] = s.out.front();
-        s.out.pop_front();
-      }
+      if (take > 0) s.out.pop(r.out + r.done_frames * cout, (size_t)(take * cout));
       r.done_frames += take;
       s.owed -= take;
       if (r.done_frames < r.n_out) break;
@@ -203,10 +219,7 @@ void cc_server::loop() {
     for (int32_t i = 0; i < count; ++i) {
       StreamQueue& s = q[batch[i]];
       h_slots[i] = cc::stream_slot(batch[i]);
-      for (size_t k = 0; k < step_in; ++k) {
-        h_in[i * step_in + k] = s.in.front();
-        s.in.pop_front();
-      }
+      s.in.pop(h_in + i * step_in, step_in);
       in_flight.insert(batch[i]);
     }
     const int32_t sslot = cc::stream_slot(scratch);
@@ -236,7 +249,7 @@ void cc_server::loop() {
       auto it = q.find(batch[i]);
       if (it == q.end()) continue;
       StreamQueue& sq = it->second;
-      sq.out.insert(sq.out.end(), h_out + i * step_out, h_out + (i + 1) * step_out);
+      sq.out.push(h_out + i * step_out, step_out);
       serve_fifo(sq, t1);
     }
     in_flight.clear();
@@ -350,7 +363,7 @@ cc_status cc_server_submit(cc_server* s, int32_t count, cc_stream* const* stream
   }
   for (int32_t i = 0; i < count; ++i) {
     StreamQueue& q = s->q[streams[i]];
-    if (n_in[i]) q.in.insert(q.in.end(), in[i], in[i] + n_in[i] * s->cin);
+    if (n_in[i]) q.in.push(in[i], (size_t)(n_in[i] * s->cin));
     q.owed += n_out[i];
     q.reqs.push_back(Request{n_out[i] ? out[i] : nullptr, n_out[i], 0, tags[i], t});
     s->serve_fifo(q, t);

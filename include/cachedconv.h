@@ -184,6 +184,43 @@ cc_status cc_model_timing(cc_model* model, int32_t enable);
 cc_status cc_model_timing_read(cc_model* model, double* ms_per_node, int64_t* launches_per_node,
                                int32_t n_nodes);
 
+/* ---------------------------------------------------------------- backward
+ * Gradients of a loss over a long streamed signal, chunk by chunk in reverse
+ * time order with per-chunk activation checkpointing.  The streamed output
+ * equals the causal offline model (section 4.2), so these are that model's
+ * gradients with respect to the input and to every weight and bias.
+ *
+ * Protocol, for streams processed forward chunk by chunk:
+ *   forward:  before chunk c, cc_stream_snapshot each stream into a device
+ *             buffer (cc_model_state_bytes slot + 16 bytes); process the chunk.
+ *   backward: cc_backward_begin once; then for c = last .. first:
+ *             cc_stream_restore the chunk-c snapshots and call
+ *             cc_backward_chunk with chunk c's input and output gradient.
+ * cc_backward_chunk recomputes the chunk's forward (the rings then hold its
+ * activations), clears the adjoint rows no later chunk could have reached,
+ * and propagates adjoints through the nodes in reverse order; the adjoint of
+ * the cached frames a chunk read stays in the adjoint arena for the previous
+ * chunk.  Weight / bias gradients accumulate in the cc_grads buffers.
+ * FP32 models only (STATE otherwise).  All signal pointers are device memory:
+ * x [n_in][in_channels], grad_y [n_out][out_channels], grad_x (may be NULL)
+ * [n_in][in_channels], stream i at base + i*stride.  n_in is a whole number
+ * of model steps, at most max_steps_per_call. */
+typedef struct cc_grads cc_grads;
+/* weights: the trained-layout float32 host weights the model was created with. */
+cc_status cc_grads_create(cc_model* model, const float* const* weights, cc_grads** out);
+cc_status cc_grads_destroy(cc_grads* grads);
+cc_status cc_grads_zero(cc_grads* grads);
+/* Host copies of one node's accumulated gradients (trained layouts); db may be NULL. */
+cc_status cc_grads_read(cc_grads* grads, int32_t node, float* dw, float* db);
+cc_status cc_backward_begin(cc_grads* grads, cc_stream* const* streams, int32_t count, void* cuda_stream);
+cc_status cc_backward_chunk(cc_grads* grads, cc_stream* const* streams, int32_t count, const float* x,
+                            int64_t x_stride, int64_t n_in, const float* grad_y, int64_t gy_stride,
+                            int64_t n_out, float* grad_x, int64_t gx_stride, void* cuda_stream);
+/* Device-side stream state copies (slot + step counter + noise seed), for
+ * per-chunk checkpoints in bounded device memory; bytes = slot bytes + 16. */
+cc_status cc_stream_snapshot(cc_stream* stream, void* dev_buf, size_t bytes, void* cuda_stream);
+cc_status cc_stream_restore(cc_stream* stream, const void* dev_buf, size_t bytes, void* cuda_stream);
+
 /* ---------------------------------------------------------------- serving
  * Continuous batching of many real-time streams of one model.  Clients submit
  * requests from any thread; a scheduler thread repeatedly advances, by one

@@ -76,6 +76,14 @@ _SIGNATURES = {
     "cc_server_poll": [_P, _I32, _P, _P, _P, C.POINTER(_I32)],
     "cc_server_remove": [_P, _P],
     "cc_server_stats": [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
+    "cc_grads_create": [_P, C.POINTER(_P), C.POINTER(_P)],
+    "cc_grads_destroy": [_P],
+    "cc_grads_zero": [_P],
+    "cc_grads_read": [_P, _I32, _P, _P],
+    "cc_backward_begin": [_P, _P, _I32, _P],
+    "cc_backward_chunk": [_P, _P, _I32, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _P],
+    "cc_stream_snapshot": [_P, _P, _SZ, _P],
+    "cc_stream_restore": [_P, _P, _SZ, _P],
     "cc_status_str": [_I32],
     "cc_last_error": [],
 }
@@ -399,3 +407,70 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+
+def snapshot_bytes(model):
+    return model.state_bytes[1] + 16
+
+
+class Grads:
+    """Gradient accumulators + adjoint arena of an FP32 model (cc_grads_*)."""
+
+    def __init__(self, model, params):
+        n = len(model.nodes)
+        wp = (_P * n)()
+        self._keep = []
+        for i in range(n):
+            if i in params:
+                w32 = np.ascontiguousarray(params[i][0], dtype=np.float32)
+                self._keep.append(w32)
+                wp[i] = w32.ctypes.data
+        h = _P()
+        _check(lib().cc_grads_create(model.handle, wp, C.byref(h)))
+        self._keep = None
+        self.handle = h
+        self.model = model
+
+    def zero(self):
+        _check(lib().cc_grads_zero(self.handle))
+
+    def read(self, node):
+        nd = self.model.nodes[node]
+        from .workloads import weight_shape
+        dw = np.zeros(weight_shape(nd), np.float32)
+        db = np.zeros(nd["c_out"], np.float32) if nd["bias"] else None
+        _check(lib().cc_grads_read(self.handle, node, dw.ctypes.data, None if db is None else db.ctypes.data))
+        return dw, db
+
+    def begin(self, streams, cuda_stream=None):
+        arr = (_P * len(streams))(*[s.handle for s in streams])
+        _check(lib().cc_backward_begin(self.handle, arr, len(streams), _cuda_stream(cuda_stream)))
+
+    def chunk(self, streams, x, gy, gx=None, cuda_stream=None):
+        """x [count][n_in][C_in], gy [count][n_out][C_out], gx like x (or None): CUDA tensors."""
+        arr = (_P * len(streams))(*[s.handle for s in streams])
+        _check(lib().cc_backward_chunk(self.handle, arr, len(streams), _ptr(x), int(np.prod(x.shape[1:])),
+                                       x.shape[1], _ptr(gy), int(np.prod(gy.shape[1:])), gy.shape[1],
+                                       None if gx is None else _ptr(gx),
+                                       int(np.prod(x.shape[1:])), _cuda_stream(cuda_stream)))
+
+    def close(self):
+        if getattr(self, "handle", None) and getattr(self.model, "handle", None):
+            _check(lib().cc_grads_destroy(self.handle))
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stream_snapshot(stream, buf, cuda_stream=None):
+    """Device copy of a stream's state into a uint8 CUDA tensor of snapshot_bytes()."""
+    _check(lib().cc_stream_snapshot(stream.handle, buf.data_ptr(), buf.numel(), _cuda_stream(cuda_stream)))
+
+
+def stream_restore(stream, buf, cuda_stream=None):
+    _check(lib().cc_stream_restore(stream.handle, buf.data_ptr(), buf.numel(), _cuda_stream(cuda_stream)))

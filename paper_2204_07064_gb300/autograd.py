@@ -1,0 +1,83 @@
+"""torch.autograd.Function over the streamed model (chunked, checkpointed).
+
+Forward: the input is streamed chunk by chunk through the library
+(cc_process_batch); before each chunk every stream's state is copied into a
+device checkpoint (cc_stream_snapshot), so memory grows with the number of
+chunks times the per-stream cache, not with the signal's activations.
+Backward: the checkpoints are restored in reverse order and the library's
+hand-written backward (cc_backward_chunk) recomputes each chunk and
+propagates the adjoints, carrying the cache adjoint from chunk to chunk;
+weight and bias gradients accumulate in a Grads object.  After the backward
+the streams are back in the state the forward left them in.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import api
+
+
+class StreamedRunner:
+    """An FP32 model, its streams, gradient buffers and the chunk length."""
+
+    def __init__(self, model, params, streams, chunk_steps):
+        self.model = model
+        self.streams = list(streams)
+        self.grads = api.Grads(model, params)
+        io = model.io
+        self.in_chunk = chunk_steps * io["in_per_step"]
+        self.out_chunk = chunk_steps * io["out_per_step"]
+        self.io = io
+
+
+class _Streamed(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, runner):
+        count, n_in, cin = x.shape
+        io = runner.io
+        if n_in % runner.in_chunk:
+            raise ValueError("input length must be a whole number of chunks")
+        chunks = n_in // runner.in_chunk
+        nb = api.snapshot_bytes(runner.model)
+        ckpt = torch.empty((chunks + 1, count, nb), dtype=torch.uint8, device=x.device)
+        y = torch.empty((count, chunks * runner.out_chunk, io["out_channels"]), dtype=torch.float32,
+                        device=x.device)
+        xs = x.detach().contiguous()
+        for c in range(chunks):
+            for k, s in enumerate(runner.streams):
+                api.stream_snapshot(s, ckpt[c, k])
+            xc = xs[:, c * runner.in_chunk:(c + 1) * runner.in_chunk].contiguous()
+            yc = torch.empty((count, runner.out_chunk, io["out_channels"]), dtype=torch.float32, device=x.device)
+            runner.model.process_batch(runner.streams, xc, yc)
+            y[:, c * runner.out_chunk:(c + 1) * runner.out_chunk] = yc
+        for k, s in enumerate(runner.streams):
+            api.stream_snapshot(s, ckpt[chunks, k])
+        ctx.save_for_backward(xs, ckpt)
+        ctx.runner = runner
+        ctx.chunks = chunks
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        xs, ckpt = ctx.saved_tensors
+        runner = ctx.runner
+        gy = gy.contiguous()
+        gx = torch.zeros_like(xs)
+        runner.grads.begin(runner.streams)
+        for c in reversed(range(ctx.chunks)):
+            for k, s in enumerate(runner.streams):
+                api.stream_restore(s, ckpt[c, k])
+            xc = xs[:, c * runner.in_chunk:(c + 1) * runner.in_chunk].contiguous()
+            gyc = gy[:, c * runner.out_chunk:(c + 1) * runner.out_chunk].contiguous()
+            gxc = torch.empty_like(xc)
+            runner.grads.chunk(runner.streams, xc, gyc, gxc)
+            gx[:, c * runner.in_chunk:(c + 1) * runner.in_chunk] = gxc
+        for k, s in enumerate(runner.streams):
+            api.stream_restore(s, ckpt[ctx.chunks, k])
+        return gx, None
+
+
+def streamed(x, runner):
+    """y = the streamed model applied to x [count][n_in][C_in] (differentiable in x;
+    weight gradients accumulate in runner.grads)."""
+    return _Streamed.apply(x, runner)

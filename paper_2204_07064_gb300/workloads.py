@@ -233,3 +233,15 @@ def buffer_partition(total, seed, choices):
         parts.append(b)
         left -= b
     return parts
+
+
+def chain(first, second):
+    """One layer list feeding ``first``'s last node into ``second`` (whose input
+    node is dropped): e.g. encoder then decoder, an audio -> audio model."""
+    off = len(first) - 1  # second's node k (k >= 1) becomes node off + k
+    out = [dict(n) for n in first]
+    for n in second[1:]:
+        m = dict(n)
+        m["inputs"] = [off if u == 0 else off + u for u in n["inputs"]]
+        out.append(m)
+    return out

@@ -31,6 +31,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
+SUB_BATCHES = {"f32": 1, "bf16": 4, "f16": 4}  # concurrent launch chains per step (default)
+
 WORKLOADS = {
     # name: (dtype, streams, buffer latent frames)
     "decoder-bf16-b256": ("bf16", 256, 1),
@@ -338,6 +340,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--flush-l2", action="store_true", help="write 256 MB between steps")
+    ap.add_argument("--sub-batches", type=int, default=0,
+                    help="split each step's streams over this many CUDA streams (0: workload default)")
+    ap.add_argument("--no-graph", action="store_true", help="launch each step's chains directly")
     ap.add_argument("--only-timed", action="store_true",
                     help="skip the e2e, FP32-comparison and CPU-baseline measurements (profiling)")
     ap.add_argument("--serving", action="store_true", help="run the serving simulation instead")
@@ -382,8 +387,51 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if args.flush_l2 else None
     st = torch.cuda.current_stream()
 
+    # one step = every stream advances one buffer; the streams are split into
+    # sub-batches launched on separate CUDA streams so that the launch chains
+    # overlap (each chain is latency-bound at this batch size)
+    nsub = args.sub_batches or SUB_BATCHES[dtype]
+    nsub = max(1, min(nsub, streams))
+    bounds = [round(k * streams / nsub) for k in range(nsub + 1)]
+    side = [torch.cuda.Stream() for _ in range(nsub)]
+    x_in = torch.empty_like(z[0])  # the step's input buffer (filled each step)
+
+    def launch_step(main):
+        fork = torch.cuda.Event()
+        fork.record(main)
+        for k in range(nsub):
+            a, b = bounds[k], bounds[k + 1]
+            side[k].wait_event(fork)
+            model.process_batch(ss[a:b], x_in[a:b], y[a:b], cuda_stream=side[k])
+        for k in range(nsub):
+            main.wait_stream(side[k])
+
     for i in range(args.warmup):
-        model.process_batch(ss, z[i], y)
+        x_in.copy_(z[i])
+        launch_step(st)
+    torch.cuda.synchronize()
+    model.device_status()
+    graph = None
+    if not args.no_graph:
+        # the whole step (fork, every sub-batch's launch chain, join) as one
+        # CUDA graph; the batch slot lists were uploaded during the warm-up
+        graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        cap.wait_stream(st)
+        with torch.cuda.graph(graph, stream=cap, capture_error_mode="relaxed"):
+            launch_step(cap)
+        st.wait_stream(cap)
+        torch.cuda.synchronize()
+
+    def step(i):
+        x_in.copy_(z[i])
+        if graph is not None:
+            graph.replay()
+        else:
+            launch_step(st)
+
+    for i in range(args.warmup):
+        step(i)
     torch.cuda.synchronize()
     model.device_status()
 
@@ -400,7 +448,7 @@ def main():
         if flush is not None:
             flush.zero_()
         starts[k].record(st)
-        model.process_batch(ss, z[args.warmup + k], y)
+        step(args.warmup + k)
         ends[k].record(st)
     torch.cuda.synchronize()
     if dist:
@@ -499,6 +547,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": {"workload": args.workload, "model": "RAVE-like decoder, random init",
                    "streams_per_gpu": streams, "buffer_samples": 2048 * frames, "sample_rate": SR,
+                   "concurrent_chains": nsub, "cuda_graph": graph is not None,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between steps" if flush is not None else
                    "working set per step > L2 (arena + weights)",

@@ -17,6 +17,16 @@ __device__ __forceinline__ int32_t wrap_row(int32_t r, int32_t rows) {
   return r >= rows ? r - rows : r;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream is still
+// running.  pdl_wait() blocks until the predecessor grid has completed and its
+// memory is visible; everything before it may only touch data no earlier
+// kernel of the chain writes (weights, tensor maps, shared memory, TMEM).
+// pdl_release() lets the next kernel start launching; it is issued only after
+// pdl_wait(), so a kernel never overlaps a kernel two places earlier.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float leaky(float x) { return x < 0.f ? kLeakySlope * x : x; }
 
 __device__ __forceinline__ float activate(float x, int32_t act) { return act ? leaky(x) : x; }

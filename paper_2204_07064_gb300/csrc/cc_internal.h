@@ -114,6 +114,24 @@ struct InputArgs {
   Batch batch;
 };
 
+// Launch with programmatic stream serialization (see pdl_wait / pdl_release):
+// the kernel's prologue may overlap the previous kernel of the stream.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // FP32 kernels (cc_kernels_f32.cu)
 cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st);
 cudaError_t launch_heads(const HeadsArgs& a, cudaStream_t st);

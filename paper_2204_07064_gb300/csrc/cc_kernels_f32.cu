@@ -129,6 +129,8 @@ constexpr int kGemvWarps = 8;
 
 template <bool kVec>
 __global__ void __launch_bounds__(kGemvWarps * 32) k_conv_gemv_f32(const ConvArgs a) {
+  pdl_wait();
+  pdl_release();
   const int32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t m = blockIdx.y * kGemvWarps + warp;
   const int32_t n0 = blockIdx.x * kGemvCols;
@@ -218,6 +220,8 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
   static_assert(A4 >= 1 && B4 >= 1, "tile too small for 256 threads");
   __shared__ __align__(16) float As[2][BK][BM + 4];
   __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  pdl_wait();
+  pdl_release();
   const int32_t tid = threadIdx.x;
   const int32_t tx = tid & 15, ty = tid >> 4;
   const int32_t m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -368,6 +372,8 @@ __device__ __forceinline__ float noise_uniform(uint64_t seed, int64_t frame, int
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 __global__ void k_heads(const HeadsArgs a) {
+  pdl_wait();
+  pdl_release();
   const int64_t total = (int64_t)a.batch.count * a.ncols * a.bands;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -392,6 +398,8 @@ __global__ void k_heads(const HeadsArgs a) {
 }
 
 __global__ void k_add(const AddArgs a) {
+  pdl_wait();
+  pdl_release();
   const int32_t C = a.chans;
   const int64_t total = (int64_t)a.batch.count * a.ncols * C;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -412,6 +420,8 @@ __global__ void k_add(const AddArgs a) {
 }
 
 __global__ void k_input(const InputArgs a) {
+  pdl_wait();
+  pdl_release();
   const int32_t C = a.chans;
   const int64_t total = (int64_t)a.batch.count * a.ncols * C;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -426,6 +436,8 @@ __global__ void k_input(const InputArgs a) {
 }
 
 __global__ void k_advance(const Batch b, int64_t steps) {
+  pdl_wait();
+  pdl_release();
   const int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < b.count) const_cast<int64_t*>(b.counters)[b.slots[s]] += steps;
 }
@@ -444,17 +456,17 @@ cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
   auto tiles = [&](int bm, int bn) { return ((a.M + bm - 1) / bm) * ((N + bn - 1) / bn); };
   if (a.cin % 8 == 0 && a.M >= 128 && tiles(128, 128) >= 2 * 152) {
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((a.M + 127) / 128));
-    k_conv_tile_f32<128, 128, 8><<<grid, 256, 0, st>>>(a);
+    return launch_pdl(k_conv_tile_f32<128, 128, 8>, grid, dim3(256), 0, st, a);
   } else if (a.cin % 16 == 0 && N >= 32) {
     dim3 grid((unsigned)((N + 63) / 64), (unsigned)((a.M + 63) / 64));
-    k_conv_tile_f32<64, 64, 16><<<grid, 256, 0, st>>>(a);
+    return launch_pdl(k_conv_tile_f32<64, 64, 16>, grid, dim3(256), 0, st, a);
   } else {
     dim3 grid((unsigned)((N + kGemvCols - 1) / kGemvCols),
               (unsigned)((a.M + kGemvWarps - 1) / kGemvWarps));
     if (a.cin % 4 == 0 && a.cin >= 64)
-      k_conv_gemv_f32<true><<<grid, kGemvWarps * 32, 0, st>>>(a);
+      return launch_pdl(k_conv_gemv_f32<true>, grid, dim3(kGemvWarps * 32), 0, st, a);
     else
-      k_conv_gemv_f32<false><<<grid, kGemvWarps * 32, 0, st>>>(a);
+      return launch_pdl(k_conv_gemv_f32<false>, grid, dim3(kGemvWarps * 32), 0, st, a);
   }
   return cudaGetLastError();
 }
@@ -462,28 +474,24 @@ cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
 cudaError_t launch_heads(const HeadsArgs& a, cudaStream_t st) {
   const int64_t total = (int64_t)a.batch.count * a.ncols * a.bands;
   if (total <= 0) return cudaSuccess;
-  k_heads<<<elementwise_grid(total), 256, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_heads, dim3(elementwise_grid(total)), dim3(256), 0, st, a);
 }
 
 cudaError_t launch_add(const AddArgs& a, cudaStream_t st) {
   const int64_t total = (int64_t)a.batch.count * a.ncols * a.chans;
   if (total <= 0) return cudaSuccess;
-  k_add<<<elementwise_grid(total), 256, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_add, dim3(elementwise_grid(total)), dim3(256), 0, st, a);
 }
 
 cudaError_t launch_input(const InputArgs& a, cudaStream_t st) {
   const int64_t total = (int64_t)a.batch.count * a.ncols * a.chans;
   if (total <= 0) return cudaSuccess;
-  k_input<<<elementwise_grid(total), 256, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_input, dim3(elementwise_grid(total)), dim3(256), 0, st, a);
 }
 
 cudaError_t launch_advance(const Batch& b, int64_t steps, cudaStream_t st) {
   if (b.count <= 0) return cudaSuccess;
-  k_advance<<<(b.count + 255) / 256, 256, 0, st>>>(b, steps);
-  return cudaGetLastError();
+  return launch_pdl(k_advance, dim3((b.count + 255) / 256), dim3(256), 0, st, b, steps);
 }
 
 }  // namespace cc

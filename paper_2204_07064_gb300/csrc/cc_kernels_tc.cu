@@ -91,6 +91,16 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 3 : 1)
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
+    // The weight tiles of the first stages do not depend on earlier kernels:
+    // they are requested before waiting for the previous layer.
+    const int pre = nk < kStages ? nk : kStages;
+    if (lane == 0)
+      for (int kc = 0; kc < pre; ++kc) {
+        mbar_arrive_expect_tx(full + kc, L::kA + L::kB);
+        tma_load_2d(sA + kc * L::kA, &tmA, full + kc, kc * 64, m0);
+      }
+    pdl_wait();
+    pdl_release();
     // lane l gathers tile rows 4*(l + 32*g) .. +3 for g < BN/128
     constexpr int G = BN / 128;
     int32_t ybase[G][4], r0[G][4];
@@ -120,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 3 : 1)
       }
       const int tap = kc / cchunks;
       const int c0 = (kc - tap * cchunks) * 64;
-      if (lane == 0) {
+      if (lane == 0 && kc >= pre) {
         mbar_arrive_expect_tx(full + st, L::kA + L::kB);
         tma_load_2d(sA + st * L::kA, &tmA, full + st, kc * 64, m0);
       }
@@ -144,6 +154,8 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 3 : 1)
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
+    pdl_wait();
+    pdl_release();
     if (lane == 0) {
       const uint32_t idesc = idesc_f16(kBM, BN, a.in.dtype == kDtBF16);
       bool ok = true;
@@ -169,6 +181,8 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 3 : 1)
     // ---------------------------------------------------------------- epilogue
     const int t = threadIdx.x - 64;  // 0..127
     const int sub = warp & 3;        // TMEM lane quarter this warp may access
+    pdl_wait();
+    pdl_release();
     for (int c = t; c < BN; c += 128) {
       const int64_t n = n0 + c;
       if (n < N) {
@@ -326,8 +340,7 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   const int mtiles = (a.M + kBM - 1) / kBM;
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)mtiles);
-  k_conv_tc<BN><<<grid, kThreads, bytes, st>>>(ta, tb, a);
-  return cudaGetLastError();
+  return launch_pdl(k_conv_tc<BN>, grid, dim3(kThreads), (size_t)bytes, st, ta, tb, a);
 }
 
 }  // namespace

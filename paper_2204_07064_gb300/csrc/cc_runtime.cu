@@ -683,9 +683,11 @@ Model::~Model() {
   if (arena) cudaFree(arena);
   if (counters) cudaFree(counters);
   if (seeds) cudaFree(seeds);
-  if (batch_slots) cudaFree(batch_slots);
-  if (batch_slots_host) cudaFreeHost(batch_slots_host);
-  if (batch_upload_done) cudaEventDestroy(batch_upload_done);
+  for (auto& kv : slot_lists) {
+    if (kv.second.d) cudaFree(kv.second.d);
+    if (kv.second.h) cudaFreeHost(kv.second.h);
+    if (kv.second.uploaded) cudaEventDestroy(kv.second.uploaded);
+  }
   if (stage_in) cudaFree(stage_in);
   if (stage_out) cudaFree(stage_out);
   for (auto e : event_pool) cudaEventDestroy(e);
@@ -766,10 +768,9 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
   if (!s) s = cc::encode_gather_maps(*m);
   if (!s && (cudaMalloc(&m->counters, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
              cudaMalloc(&m->seeds, sizeof(uint64_t) * m->max_streams) != cudaSuccess ||
-             cudaMalloc(&m->batch_slots, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
+
              cudaMalloc(&m->err, sizeof(int32_t)) != cudaSuccess ||
-             cudaMallocHost(&m->batch_slots_host, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
-             cudaEventCreateWithFlags(&m->batch_upload_done, cudaEventDisableTiming) != cudaSuccess))
+             false))
     s = fail(CC_ERR_NO_MEMORY, "model bookkeeping allocation failed");
   if (!s && (cudaMemset(m->counters, 0, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
              cudaMemset(m->err, 0, sizeof(int32_t)) != cudaSuccess ||
@@ -892,7 +893,7 @@ cc_status cc_stream_destroy(cc_stream* s) {
     cc::Model* m = s->model;
     std::lock_guard<std::mutex> g(m->mu);
     m->free_slots.push_back(s->slot);
-    m->batch_slots_valid = false;
+    for (auto& kv : m->slot_lists) kv.second.valid = false;
     m->live_streams.erase(std::remove(m->live_streams.begin(), m->live_streams.end(), s),
                           m->live_streams.end());
   }
@@ -932,17 +933,29 @@ cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, int32_t c
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
       return fail(CC_ERR_INVALID_ARG, "a stream appears twice in one batch");
   }
-  if (!m->batch_slots_valid || m->batch_slots_cache != slots) {
-    // the pinned staging buffer may still feed the previous upload
-    CC_CUDA(cudaEventSynchronize(m->batch_upload_done));
-    std::memcpy(m->batch_slots_host, slots.data(), sizeof(int32_t) * count);
-    CC_CUDA(cudaMemcpyAsync(m->batch_slots, m->batch_slots_host, sizeof(int32_t) * count,
-                            cudaMemcpyHostToDevice, st));
-    CC_CUDA(cudaEventRecord(m->batch_upload_done, st));
-    m->batch_slots_cache = slots;
-    m->batch_slots_valid = true;
+  cc::Model::SlotList* L;
+  {
+    std::lock_guard<std::mutex> g(m->mu);
+    L = &m->slot_lists[st];
+    if (!L->d) {
+      if (cudaMalloc(&L->d, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
+          cudaMallocHost(&L->h, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
+          cudaEventCreateWithFlags(&L->uploaded, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CC_ERR_NO_MEMORY, "batch slot list");
+      }
+    }
   }
-  return m->process(m->batch_slots, count, in, in_stride, n_in, out, out_stride, n_out, st);
+  if (!L->valid || L->cache != slots) {
+    // the pinned staging buffer may still feed this CUDA stream's previous upload
+    CC_CUDA(cudaEventSynchronize(L->uploaded));
+    std::memcpy(L->h, slots.data(), sizeof(int32_t) * count);
+    CC_CUDA(cudaMemcpyAsync(L->d, L->h, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
+    CC_CUDA(cudaEventRecord(L->uploaded, st));
+    L->cache = slots;
+    L->valid = true;
+  }
+  return m->process(L->d, count, in, in_stride, n_in, out, out_stride, n_out, st);
 }
 
 cc_status cc_stream_state_size(const cc_stream* s, size_t* bytes) {

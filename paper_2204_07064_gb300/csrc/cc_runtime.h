@@ -68,12 +68,18 @@ struct Model {
   std::mutex mu;
   std::vector<int32_t> free_slots;
   std::vector<cc_stream*> live_streams;  // destroyed with the model
-  // batch slot list (device) and its host mirror
-  int32_t* batch_slots = nullptr;
-  int32_t* batch_slots_host = nullptr;
-  cudaEvent_t batch_upload_done = nullptr;
-  std::vector<int32_t> batch_slots_cache;
-  bool batch_slots_valid = false;
+  // batch slot lists, one per CUDA stream (batches on different CUDA
+  // streams may run concurrently): device list, pinned staging, the event
+  // guarding the staging, and the last list uploaded
+  struct SlotList {
+    int32_t* d = nullptr;
+    int32_t* h = nullptr;
+    cudaEvent_t uploaded = nullptr;
+    std::vector<int32_t> cache;
+    bool valid = false;
+  };
+  std::map<cudaStream_t, SlotList> slot_lists;
+  int32_t* batch_slots = nullptr;  // the default CUDA stream's list (allocated at creation)
   // host I/O staging
   float* stage_in = nullptr;
   float* stage_out = nullptr;

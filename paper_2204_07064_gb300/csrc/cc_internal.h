@@ -72,11 +72,13 @@ struct ConvArgs {
   Batch batch;
 };
 
-// Tensor-core form of ConvArgs: A is low precision [Mpad][Kt] in a TMA
-// tensor map (128-row boxes, 128-byte swizzle), row m scaled by scale[m];
-// B is read from the input's low-precision view (activation pre-applied).
+// Tensor-core form of ConvArgs: A is low precision [Mpad][Kt] stored as
+// pre-swizzled 128 x 64 blocks, row m scaled by scale[m]; B is read from the
+// input's low-precision view (activation pre-applied).
 struct TcArgs {
-  const float* scale;  // [Mpad]
+  const void* A_tiled;  // weights as [Mpad/128][Kt/64] blocks of 128 x 64, each 16 KB in the
+                        // 128-byte-swizzled K-major order (one bulk copy per block)
+  const float* scale;   // [Mpad]
   const float* bias;   // [cout] or null
   int32_t M, Kt, taps, cin, dil, stride, hist, ncols, cout, phases, out_u;
   Ring in;

@@ -6,11 +6,12 @@
 // section 2.2, read in place).
 //
 // One CTA computes a 128 x BN tile with three roles:
-//   warp 0     TMA producer: per 64-wide K slice, the weight tile (128 rows,
-//              128-byte swizzle) and the BN window rows, gathered four at a
-//              time (tile::gather4) from the stream rings into the same
-//              swizzled layout; one expect-tx per stage, no thread waits on
-//              its own copies, so every stage can be in flight
+//   warp 0     TMA producer: per 64-wide K slice, the weight tile (stored
+//              pre-tiled and pre-swizzled, so one 16 KB bulk copy) and the BN
+//              window rows, gathered four at a time (tile::gather4) from the
+//              stream rings into the 128-byte-swizzled operand layout; one
+//              expect-tx per stage, no thread waits on its own copies, so
+//              every stage can be in flight
 //   warp 1     TMEM allocation; lane 0 issues tcgen05.mma (128 x BN x 16,
 //              BF16 or FP16 operands, FP32 accumulation in TMEM)
 //   warps 2-5  epilogue: TMEM -> registers -> transposed shared memory ->
@@ -32,11 +33,12 @@ constexpr int kBM = 128;
 constexpr int kThreads = 192;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
-// BN = 128: 2 stages (three CTAs per SM, so the CTAs' epilogues overlap
-// each other's main loops); BN = 256: 4 stages, one CTA per SM.
-template <int BN>
+// Pipeline depth: 128-column tiles run with 2 stages (three CTAs per SM, so
+// the CTAs' epilogues overlap each other's main loops; deeper pipelines with
+// fewer CTAs measured no faster); 256-column tiles use 4 stages, one CTA per SM.
+template <int BN, int STAGES>
 struct TcLayout {
-  static constexpr int kStages = BN == 128 ? 2 : 4;
+  static constexpr int kStages = STAGES;
   static constexpr int kA = kBM * 128;  // one 128 x 64 low-precision tile
   static constexpr int kB = BN * 128;
   static constexpr int kBars = (2 * kStages + 1) * 8 + 8;
@@ -44,11 +46,11 @@ struct TcLayout {
   static constexpr int kBytes = 1024 + kStages * (kA + kB) + kBars + kCols + 64;
 };
 
-template <int BN>
-__global__ void __launch_bounds__(kThreads, BN == 128 ? 3 : 1)
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
     k_conv_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const TcArgs a) {
-  using L = TcLayout<BN>;
+  using L = TcLayout<BN, STAGES>;
   constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -77,7 +79,6 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 3 : 1)
     }
     mbar_init(tfull, 1);
     fence_mbar_init();
-    prefetch_tmap(&tmA);
     prefetch_tmap(&tmB);
   }
   if (warp == 1) {
@@ -94,10 +95,11 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 3 : 1)
     // The weight tiles of the first stages do not depend on earlier kernels:
     // they are requested before waiting for the previous layer.
     const int pre = nk < kStages ? nk : kStages;
+    const uint8_t* atile = static_cast<const uint8_t*>(a.A_tiled) + (size_t)blockIdx.y * nk * L::kA;
     if (lane == 0)
       for (int kc = 0; kc < pre; ++kc) {
         mbar_arrive_expect_tx(full + kc, L::kA + L::kB);
-        tma_load_2d(sA + kc * L::kA, &tmA, full + kc, kc * 64, m0);
+        bulk_load(sA + kc * L::kA, atile + (size_t)kc * L::kA, L::kA, full + kc);
       }
     pdl_wait();
     pdl_release();
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 3 : 1)
       const int c0 = (kc - tap * cchunks) * 64;
       if (lane == 0 && kc >= pre) {
         mbar_arrive_expect_tx(full + st, L::kA + L::kB);
-        tma_load_2d(sA + st * L::kA, &tmA, full + st, kc * 64, m0);
+        bulk_load(sA + st * L::kA, atile + (size_t)kc * L::kA, L::kA, full + st);
       }
       __syncwarp();
       uint8_t* dst = sB + st * L::kB;
@@ -328,19 +330,20 @@ __global__ void __launch_bounds__(kThreads, BN == 128 ? 3 : 1)
   if (warp == 1) tmem_dealloc(tmem, BN);
 }
 
-template <int BN>
+template <int BN, int STAGES>
 cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, cudaStream_t st) {
   static bool configured = false;
-  constexpr int bytes = TcLayout<BN>::kBytes;
+  constexpr int bytes = TcLayout<BN, STAGES>::kBytes;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_conv_tc<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   const int mtiles = (a.M + kBM - 1) / kBM;
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)mtiles);
-  return launch_pdl(k_conv_tc<BN>, grid, dim3(kThreads), (size_t)bytes, st, ta, tb, a);
+  return launch_pdl(k_conv_tc<BN, STAGES>, grid, dim3(kThreads), (size_t)bytes, st, ta, tb, a);
 }
 
 }  // namespace
@@ -355,7 +358,8 @@ cudaError_t launch_conv_tc(const void* tmap_a, const void* tmap_b, const TcArgs&
   if (N <= 0) return cudaSuccess;
   const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(tmap_a);
   const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(tmap_b);
-  return bn == 256 ? launch_bn<256>(ta, tb, a, st) : launch_bn<128>(ta, tb, a, st);
+  if (bn == 256) return launch_bn<256, 4>(ta, tb, a, st);
+  return launch_bn<128, 2>(ta, tb, a, st);
 }
 
 }  // namespace cc

@@ -276,6 +276,24 @@ static cc_status upload_tc_operand(Model& m, NodePlan& p, const std::vector<floa
   }
   CC_CUDA(cudaMalloc(&p.dA_lp, lp.size() * 2));
   CC_CUDA(cudaMemcpy(p.dA_lp, lp.data(), lp.size() * 2, cudaMemcpyHostToDevice));
+  // the same operand as contiguous 128 x 64 blocks (16 KB), block (mt, kc) at
+  // (mt * Kt/64 + kc) * 16 KB; inside a block row r's 16-byte chunk c sits at
+  // r*128 + ((c ^ (r & 7)) * 16): the shared-memory image of a 128-byte-swizzled
+  // K-major tile, so one bulk copy reproduces it
+  {
+    const int nk = p.Kt / 64, mt_n = p.Mpad / 128;
+    std::vector<uint16_t> tiled(lp.size());
+    for (int mt = 0; mt < mt_n; ++mt)
+      for (int kc = 0; kc < nk; ++kc) {
+        uint16_t* blk = tiled.data() + ((size_t)mt * nk + kc) * 128 * 64;
+        for (int r = 0; r < 128; ++r)
+          for (int c = 0; c < 8; ++c)
+            std::memcpy(blk + r * 64 + ((c ^ (r & 7)) * 8),
+                        lp.data() + (size_t)(mt * 128 + r) * p.Kt + kc * 64 + c * 8, 16);
+      }
+    CC_CUDA(cudaMalloc(&p.dA_tiled, tiled.size() * 2));
+    CC_CUDA(cudaMemcpy(p.dA_tiled, tiled.data(), tiled.size() * 2, cudaMemcpyHostToDevice));
+  }
   CC_CUDA(cudaMalloc(&p.dscale, scale.size() * sizeof(float)));
   CC_CUDA(cudaMemcpy(p.dscale, scale.data(), scale.size() * sizeof(float), cudaMemcpyHostToDevice));
   m.weight_bytes += lp.size() * 2;
@@ -441,6 +459,7 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
       const int32_t dil = convt ? 1 : d.dilation, stride = convt ? 1 : d.stride;
       if (p.engine == 1) {
         TcArgs a{};
+        a.A_tiled = p.dA_tiled;
         a.scale = p.dscale;
         a.bias = p.dbias;
         a.M = p.M;
@@ -677,6 +696,7 @@ Model::~Model() {
     if (p.dA) cudaFree(p.dA);
     if (p.dbias) cudaFree(p.dbias);
     if (p.dA_lp) cudaFree(p.dA_lp);
+    if (p.dA_tiled) cudaFree(p.dA_tiled);
     if (p.dscale) cudaFree(p.dscale);
   }
   if (err) cudaFree(err);

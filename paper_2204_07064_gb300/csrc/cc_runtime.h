@@ -42,6 +42,7 @@ struct NodePlan {
   // tensor-core operand: low-precision [Mpad][Kt], per-row scale, TMA map
   int32_t Mpad = 0;
   void* dA_lp = nullptr;
+  void* dA_tiled = nullptr;
   float* dscale = nullptr;
   alignas(64) unsigned char tmap[128] = {};   // weights
   alignas(64) unsigned char tmapB[128] = {};  // input view as arena rows

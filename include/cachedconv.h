@@ -105,7 +105,7 @@ typedef struct cc_stream cc_stream;
  * has none): conv [c_out][c_in][kernel], convt [c_in][c_out][kernel],
  * bias [c_out].  They are copied; the caller may free them on return.
  * Errors: INVALID_ARG, BAD_GRAPH (with the offending node in cc_last_error),
- * NO_MEMORY, CUDA. */
+ * NO_MEMORY (also for an arena of 64 GiB or more: max_streams x slot size), CUDA. */
 cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes,
                           const float* const* weights, const float* const* biases,
                           const cc_model_config* config, cc_model** out);

@@ -44,11 +44,21 @@ __device__ __forceinline__ int64_t steps_of(const Batch& b, int32_t s) {
   return b.counters[b.slots[s]];
 }
 
+// Low-precision store of ring row `row` (0 <= row < R), and of its mirror
+// row - R when the row lies in the ring's mirrored tail.
 __device__ __forceinline__ void store_lp(char* base, const Ring& r, int64_t row, int32_t ch, float x) {
-  if (r.dtype == kDtBF16)
-    reinterpret_cast<__nv_bfloat16*>(base + r.off)[row * r.chans + ch] = __float2bfloat16_rn(x);
-  else
-    reinterpret_cast<__half*>(base + r.off)[row * r.chans + ch] = __float2half_rn(x);
+  const bool mirror = row >= r.rows - r.pre;
+  if (r.dtype == kDtBF16) {
+    __nv_bfloat16* p = reinterpret_cast<__nv_bfloat16*>(base + r.off);
+    const __nv_bfloat16 v = __float2bfloat16_rn(x);
+    p[row * r.chans + ch] = v;
+    if (mirror) p[(row - r.rows) * r.chans + ch] = v;
+  } else {
+    __half* p = reinterpret_cast<__half*>(base + r.off);
+    const __half v = __float2half_rn(x);
+    p[row * r.chans + ch] = v;
+    if (mirror) p[(row - r.rows) * r.chans + ch] = v;
+  }
 }
 
 // Writes value v of channel ch at absolute time t (local time lt within this

@@ -25,12 +25,18 @@ constexpr float kLeakySlope = 0.2f;
 enum : int32_t { kDtF32 = 0, kDtBF16 = 1, kDtF16 = 2 };
 
 // Where one stream's frames of one view of one node live.  rows == 0: absent.
+// Frame t sits at ring row t mod R.  A low-precision view also keeps a copy
+// of its last `pre` ring rows just before row 0 (rows -pre .. -1 mirror rows
+// R-pre .. R-1, written together with them), so that a window of the cached
+// history plus the frames of one call that starts in the ring's tail can be
+// read as one run of consecutive rows.
 struct Ring {
-  int64_t off;    // byte offset inside a slot
+  int64_t off;    // byte offset inside a slot of ring row 0
   int32_t rows;   // R
   int32_t chans;  // C
   int32_t u;      // frames per model step at this node
   int32_t dtype;  // kDt*
+  int32_t pre;    // mirrored rows before row 0 (low-precision views), else 0
 };
 
 // Every destination of a layer's output.
@@ -84,8 +90,12 @@ struct TcArgs {
   Ring in;
   int32_t in_rows_per_slot;  // the input view seen as rows of the whole arena:
   int32_t in_row_off;        //   row = slot*in_rows_per_slot + in_row_off + ring row
+  int32_t box_ok;            // stride 1 and ncols divides 128 or is a multiple of it:
+                             //   tiles of consecutive slots at one step may load their
+                             //   window rows as 3D boxes (tmap_t) instead of gathers
   OutViews out;
   int32_t has_skip, skip_A;
+  int32_t skip_early;  // the residual's producer launched two or more launches back
   Ring skip;
   Batch batch;
   int32_t* err;  // device error word: set when a bounded wait gives up
@@ -141,10 +151,11 @@ cudaError_t launch_add(const AddArgs& a, cudaStream_t st);
 cudaError_t launch_input(const InputArgs& a, cudaStream_t st);
 cudaError_t launch_advance(const Batch& b, int64_t steps, cudaStream_t st);
 
-// Tensor-core kernels (cc_kernels_tc.cu).  tmap_a: weights [Mpad][Kt] in
-// 128 x 64 boxes; tmap_b: the input view as arena rows of C elements, one-row
-// boxes of 64 (gathered four rows at a time).  Both CUtensorMap (128 B).
-cudaError_t launch_conv_tc(const void* tmap_a, const void* tmap_b, const TcArgs& a, int bn,
+// Tensor-core kernels (cc_kernels_tc.cu).  tmap_t: the input view as
+// [slot][pre + R rows][C], boxes of 64 channels x min(ncols, 128) rows x
+// 128 / that many slots; tmap_b: the input view as arena rows of C elements,
+// one-row boxes of 64 (gathered four rows at a time).  Both CUtensorMap (128 B).
+cudaError_t launch_conv_tc(const void* tmap_t, const void* tmap_b, const TcArgs& a, int bn,
                            cudaStream_t st);
 int tc_tile_n(int64_t n_cols, int m_tiles);
 

@@ -8,16 +8,32 @@
 // One CTA computes a 128 x BN tile with three roles:
 //   warp 0     TMA producer: per 64-wide K slice, the weight tile (stored
 //              pre-tiled and pre-swizzled, so one 16 KB bulk copy) and the BN
-//              window rows, gathered four at a time (tile::gather4) from the
-//              stream rings into the 128-byte-swizzled operand layout; one
-//              expect-tx per stage, no thread waits on its own copies, so
-//              every stage can be in flight
+//              window rows in the 128-byte-swizzled operand layout.  When the
+//              tile's streams occupy consecutive slots at the same step, the
+//              rows of 128 columns are one 3D box (frames x slots) of the
+//              input view; otherwise they are gathered four at a time
+//              (tile::gather4), which costs about four times as much per
+//              slice.  One expect-tx per stage, no thread waits on its own
+//              copies, so every stage can be in flight
 //   warp 1     TMEM allocation; lane 0 issues tcgen05.mma (128 x BN x 16,
 //              BF16 or FP16 operands, FP32 accumulation in TMEM)
-//   warps 2-5  epilogue: TMEM -> registers -> transposed shared memory ->
-//              scale, bias, aligned residual, 16/32-byte stores of every view
+//   warps 2-5  epilogue: warp w owns accumulator rows 32*(w%4) .. +31 (its
+//              TMEM lane quarter); per 32-column chunk it loads the rows
+//              (tcgen05.ld), applies scale, bias and the aligned residual and
+//              stores every view column by column, each store covering 32
+//              consecutive channels (coalesced), with ring addresses from a
+//              per-column table built before the kernel waits on its
+//              predecessor
 // Every mbarrier wait is bounded in time and records an error in the model's
 // device error word instead of hanging.
+//
+// Reads before griddepcontrol.wait: the weights, scales and biases (written at
+// model creation), the batch's slot list and step counters, and (skip_early)
+// the residual rows.  Every kernel of a launch chain issues
+// griddepcontrol.launch_dependents only after its own wait, so when a grid
+// starts, every launch before its predecessor has completed: the slot list
+// (uploaded before the chain), the counters (advanced by the previous chain's
+// last kernel) and a residual produced two or more launches back are final.
 #include <cuda.h>
 
 #include "cc_device.cuh"
@@ -33,22 +49,27 @@ constexpr int kBM = 128;
 constexpr int kThreads = 192;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
-// Pipeline depth: 128-column tiles run with 2 stages (three CTAs per SM, so
-// the CTAs' epilogues overlap each other's main loops; deeper pipelines with
-// fewer CTAs measured no faster); 256-column tiles use 4 stages, one CTA per SM.
+// Pipeline depth: 128-column tiles run 6 stages when the grid fits in one wave
+// (one CTA per SM: few CTAs with long K loops need deep prefetch), else 2
+// stages (three CTAs per SM, whose epilogues overlap each other's main
+// loops); 256-column tiles use 4 stages.
 template <int BN, int STAGES>
 struct TcLayout {
   static constexpr int kStages = STAGES;
   static constexpr int kA = kBM * 128;  // one 128 x 64 low-precision tile
   static constexpr int kB = BN * 128;
   static constexpr int kBars = (2 * kStages + 1) * 8 + 8;
-  static constexpr int kCols = BN * (8 + 8 + 4 * 4);
+  // column table per view (f32, lp0, lp1, skip): arena offset in 16-byte
+  // units of the ring row holding the column's first frame, that ring row,
+  // the mirror row's offset (low-precision views); the caller-buffer offset
+  static constexpr int kCols = BN * (4 * 4 + 4 * 4 + 2 * 4 + 8);
   static constexpr int kBytes = 1024 + kStages * (kA + kB) + kBars + kCols + 64;
+  static constexpr int kMinBlocks = STAGES == 2 ? 3 : 1;
 };
 
 template <int BN, int STAGES>
-__global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
-    k_conv_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+__global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
+    k_conv_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmB,
               const TcArgs a) {
   using L = TcLayout<BN, STAGES>;
   constexpr int kStages = L::kStages;
@@ -61,9 +82,10 @@ __global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
   uint64_t* empty = full + kStages;
   uint64_t* tfull = empty + kStages;
   uint32_t* tbase = reinterpret_cast<uint32_t*>(tfull + 1);
-  int64_t* col_slot = reinterpret_cast<int64_t*>(tbase + 2);
-  int64_t* col_ext = col_slot + BN;
-  int32_t* col_row = reinterpret_cast<int32_t*>(col_ext + BN);  // [4][BN]
+  int64_t* col_ext = reinterpret_cast<int64_t*>(tbase + 2);   // [BN]
+  uint32_t* col_off = reinterpret_cast<uint32_t*>(col_ext + BN);  // [4][BN], 16-byte units
+  int32_t* col_row = reinterpret_cast<int32_t*>(col_off + 4 * BN);  // [4][BN]
+  uint32_t* col_mir = reinterpret_cast<uint32_t*>(col_row + 4 * BN);  // [2][BN], ~0u: none
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t m0 = blockIdx.y * kBM;
@@ -79,7 +101,7 @@ __global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
     }
     mbar_init(tfull, 1);
     fence_mbar_init();
-    prefetch_tmap(&tmB);
+    prefetch_tmap(a.box_ok ? &tmT : &tmB);
   }
   if (warp == 1) {
     tmem_alloc(tbase, BN);
@@ -92,8 +114,7 @@ __global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
-    // The weight tiles of the first stages do not depend on earlier kernels:
-    // they are requested before waiting for the previous layer.
+    // The weight tiles of the first stages are requested before anything else.
     const int pre = nk < kStages ? nk : kStages;
     const uint8_t* atile = static_cast<const uint8_t*>(a.A_tiled) + (size_t)blockIdx.y * nk * L::kA;
     if (lane == 0)
@@ -101,10 +122,33 @@ __global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
         mbar_arrive_expect_tx(full + kc, L::kA + L::kB);
         bulk_load(sA + kc * L::kA, atile + (size_t)kc * L::kA, L::kA, full + kc);
       }
-    pdl_wait();
-    pdl_release();
-    // lane l gathers tile rows 4*(l + 32*g) .. +3 for g < BN/128
     constexpr int G = BN / 128;
+    // Box form: the streams of the tile sit in consecutive slots at one step p,
+    // and the call's frames do not cross the ring's end; then tap k's rows of
+    // the 128 columns of half g start at view row pre + p - hist + j_g + k*dil
+    // of slot bz[g] (the mirrored tail holds the rows before ring row 0).
+    bool boxes = false;
+    int32_t by[G], bz[G];
+    if (a.box_ok) {
+      const int64_t s_first = n0 / a.ncols;
+      const int64_t s_end = min((n0 + BN - 1) / a.ncols + 1, (int64_t)a.batch.count);
+      const int32_t slot0 = a.batch.slots[s_first];
+      const int64_t step0 = steps_of(a.batch, (int32_t)s_first);
+      bool reg = true;
+      for (int64_t s = s_first + lane; s < s_end; s += 32)
+        reg = reg && a.batch.slots[s] == slot0 + (int32_t)(s - s_first) &&
+              steps_of(a.batch, (int32_t)s) == step0;
+      const int32_t p = (int32_t)ring_row(step0 * a.in.u, a.in.rows);
+      boxes = __all_sync(0xffffffffu, reg) && p + a.ncols <= a.in.rows;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int64_t ng = n0 + 128 * g;
+        const int64_t sg = ng / a.ncols;
+        by[g] = a.in.pre + p - a.hist + (int32_t)(ng - sg * a.ncols);
+        bz[g] = slot0 + (int32_t)(sg - s_first);
+      }
+    }
+    // gather form: lane l gathers tile rows 4*(l + 32*g) .. +3 for g < G
     int32_t ybase[G][4], r0[G][4];
 #pragma unroll
     for (int g = 0; g < G; ++g)
@@ -113,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
         const int64_t n = n0 + 4 * (lane + 32 * g) + i;
         ybase[g][i] = 0;
         r0[g][i] = -1;  // column past the batch: read arena row 0, result discarded
-        if (n < N) {
+        if (!boxes && n < N) {
           const int32_t s = (int32_t)(n / a.ncols);
           const int32_t j = (int32_t)(n - (int64_t)s * a.ncols);
           ybase[g][i] = a.batch.slots[s] * a.in_rows_per_slot + a.in_row_off;
@@ -121,6 +165,8 @@ __global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
                                        a.in.rows);
         }
       }
+    pdl_wait();  // the input view is the previous launch's output
+    pdl_release();
     bool ok = true;
     int issued = 0;
     for (int kc = 0; kc < nk; ++kc) {
@@ -138,13 +184,19 @@ __global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
       }
       __syncwarp();
       uint8_t* dst = sB + st * L::kB;
+      if (boxes) {
+        if (lane == 0)
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        int32_t y[4];
+          for (int g = 0; g < G; ++g) tma_load_3d(dst + g * 16384, &tmT, full + st, c0, by[g] + tap * a.dil, bz[g]);
+      } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          y[i] = r0[g][i] < 0 ? 0 : ybase[g][i] + wrap_row(r0[g][i] + tap * a.dil, a.in.rows);
-        tma_gather4(dst + (lane + 32 * g) * 512, &tmB, full + st, c0, y[0], y[1], y[2], y[3]);
+        for (int g = 0; g < G; ++g) {
+          int32_t y[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            y[i] = r0[g][i] < 0 ? 0 : ybase[g][i] + wrap_row(r0[g][i] + tap * a.dil, a.in.rows);
+          tma_gather4(dst + (lane + 32 * g) * 512, &tmB, full + st, c0, y[0], y[1], y[2], y[3]);
+        }
       }
       issued = kc + 1;
     }
@@ -183,47 +235,94 @@ __global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
     // ---------------------------------------------------------------- epilogue
     const int t = threadIdx.x - 64;  // 0..127
     const int sub = warp & 3;        // TMEM lane quarter this warp may access
-    pdl_wait();
-    pdl_release();
+    const int32_t m = m0 + sub * 32 + lane;  // accumulator row of this thread
+    const bool mok = m < a.M;
+    const int32_t ph = (mok && a.phases > 1) ? m / a.cout : 0;  // transposed conv: phase
+    const int32_t ch = mok ? m - ph * a.cout : 0;                // output channel
+    const float sc = mok ? a.scale[m] : 0.f;
+    const float bi = (mok && a.bias) ? a.bias[ch] : 0.f;
+    // Column table (pre-wait): per view, the 16-byte-unit arena offset of the
+    // ring row holding the column's first frame and that row; for a
+    // low-precision view also the offset of its mirror row (~0u if the row is
+    // not in the mirrored tail; used when phases == 1).  The arena is below
+    // 64 GiB, so offsets fit 32 bits.
     for (int c = t; c < BN; c += 128) {
       const int64_t n = n0 + c;
-      if (n < N) {
-        const int32_t s = (int32_t)(n / a.ncols);
-        const int32_t j = (int32_t)(n - (int64_t)s * a.ncols);
-        col_slot[c] = (int64_t)a.batch.slots[s] * a.batch.slot_bytes;
-        col_ext[c] = (int64_t)s * a.out.ext_stride + (int64_t)j * a.phases * a.cout;
-        const int64_t tb = steps_of(a.batch, s) * a.out_u + (int64_t)j * a.phases;
-        col_row[0 * BN + c] = a.out.f32.rows ? (int32_t)ring_row(tb, a.out.f32.rows) : 0;
-        col_row[1 * BN + c] = a.out.lp[0].rows ? (int32_t)ring_row(tb, a.out.lp[0].rows) : 0;
-        col_row[2 * BN + c] = a.out.lp[1].rows ? (int32_t)ring_row(tb, a.out.lp[1].rows) : 0;
-        col_row[3 * BN + c] = a.has_skip ? (int32_t)ring_row(tb - a.skip_A, a.skip.rows) : 0;
-      }
+      if (n >= N) break;
+      const int32_t s = (int32_t)(n / a.ncols);
+      const int32_t j = (int32_t)(n - (int64_t)s * a.ncols);
+      const int64_t sb = (int64_t)a.batch.slots[s] * a.batch.slot_bytes;
+      const int64_t tb = steps_of(a.batch, s) * a.out_u + (int64_t)j * a.phases;
+      col_ext[c] = (int64_t)s * a.out.ext_stride + (int64_t)j * a.phases * a.cout;
+      auto put = [&](int v, int64_t off, int32_t rows, int32_t chans, int32_t pre, int64_t time, int elem) {
+        const int32_t row = rows ? (int32_t)ring_row(time, rows) : 0;
+        const int64_t pitch = (int64_t)chans * elem;
+        col_row[v * BN + c] = row;
+        col_off[v * BN + c] = (uint32_t)((sb + off + row * pitch) >> 4);
+        if (v == 1 || v == 2)
+          col_mir[(v - 1) * BN + c] = (rows && row >= rows - pre) ? (uint32_t)((sb + off + (row - rows) * pitch) >> 4) : ~0u;
+      };
+      put(0, a.out.f32.off, a.out.f32.rows, a.out.f32.chans, 0, tb, 4);
+      put(1, a.out.lp[0].off, a.out.lp[0].rows, a.out.lp[0].chans, a.out.lp[0].pre, tb, 2);
+      put(2, a.out.lp[1].off, a.out.lp[1].rows, a.out.lp[1].chans, a.out.lp[1].pre, tb, 2);
+      put(3, a.skip.off, a.skip.rows, a.skip.chans, 0, tb - a.skip_A, 4);
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");  // column table complete
-    // Residual values of pass 2 (below), software-pipelined one 32-column
-    // chunk ahead: chunk 0's are requested before the accumulator is ready.
-    float4 skip_next[4][2];
-    auto fetch_skip = [&](int cb, float4 (&dst)[4][2]) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int p = t + q * 128;
-        const int c = p >> 4, g = p & 15;
-        const int32_t mb = m0 + g * 8;
-        dst[q][0] = dst[q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (!a.has_skip || cb >= BN || n0 + cb + c >= N || mb >= a.M) continue;
-        const int32_t ph = a.phases > 1 ? mb / a.cout : 0;
-        const int32_t cg = mb - ph * a.cout;
-        const int col = cb + c;
-        const int32_t row = wrap_row(col_row[3 * BN + col] + ph, a.skip.rows);
-        const float4* sp = reinterpret_cast<const float4*>(a.batch.arena + col_slot[col] + a.skip.off +
-                                                           ((int64_t)row * a.skip.chans + cg) * 4);
-        dst[q][0] = __ldg(sp);
-        dst[q][1] = __ldg(sp + 1);
+    char* const arena = a.batch.arena;
+    const bool phased = a.phases > 1;
+    // Offset (16-byte units) of this thread's row of a column for a phased
+    // (transposed) layer: the column's first row + ph, wrapped at the ring end.
+    auto phase_off = [&](uint32_t o16, int32_t row, int32_t rows, int32_t pitch16) -> uint32_t {
+      return o16 + (uint32_t)((row + ph >= rows ? ph - rows : ph) * pitch16);
+    };
+    const int32_t s_rows = a.skip.rows, s_p16 = a.skip.chans / 4;
+    char* const sk_base = arena + (int64_t)ch * 4;
+    // residual rows of the tile: every 128-byte line into L2 ahead of use
+    auto prefetch_skip = [&]() {
+      for (int c = t; c < BN; c += 128) {
+        if (n0 + c >= N) break;
+        for (int k = 0; k < kBM; k += 32) {
+          const int32_t mm = m0 + k;
+          if (mm >= a.M) break;
+          const int32_t p2 = a.phases > 1 ? mm / a.cout : 0;
+          const int32_t row = col_row[3 * BN + c];
+          const int32_t d = row + p2 >= s_rows ? p2 - s_rows : p2;
+          prefetch_l2(arena + (uint64_t)col_off[3 * BN + c] * 16 + ((int64_t)d * a.skip.chans + (mm - p2 * a.cout)) * 4);
+        }
       }
     };
-    fetch_skip(0, skip_next);
+    // Columns go in groups of 8 (one tcgen05.ld each) inside chunks of 32:
+    // per chunk each lane holds the table entries of column cb + lane and the
+    // store loop broadcasts them (no shared-memory reads between stores).
+    // The group body is the only unrolled code, so the loop stays small in
+    // the instruction cache.
+    float sk[8];
+    auto load_skip = [&](int cb, int g, uint32_t so, int32_t sr) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        uint32_t o = __shfl_sync(0xffffffffu, so, 8 * g + k);
+        if (phased) o = phase_off(o, __shfl_sync(0xffffffffu, sr, 8 * g + k), s_rows, s_p16);
+        sk[k] = (mok && n0 + cb + 8 * g + k < N) ? ld_global_nc_f32(sk_base + (uint64_t)o * 16) : 0.f;
+      }
+    };
+    uint32_t so_next = 0;
+    int32_t sr_next = 0;
+    if (a.has_skip) {
+      so_next = col_off[3 * BN + lane];
+      sr_next = col_row[3 * BN + lane];
+    }
+    if (a.has_skip && a.skip_early) {
+      prefetch_skip();
+      load_skip(0, 0, so_next, sr_next);
+    }
+    pdl_wait();
+    pdl_release();
+    if (a.has_skip && !a.skip_early) {
+      prefetch_skip();
+      load_skip(0, 0, so_next, sr_next);
+    }
     // one verdict for all 128 epilogue threads (a reduction barrier), so the
-    // named barriers below always match
+    // named barriers stay matched
     const bool waited = mbar_wait(tfull, 0, kWaitNs);
     uint32_t all_ok;
     asm volatile(
@@ -238,87 +337,109 @@ __global__ void __launch_bounds__(kThreads, STAGES == 2 ? 3 : 1)
     if (!all_ok) {
       if (t == 0) atomicOr(a.err, 2);
     } else {
-      // Two passes per 32-column TMEM chunk.  Pass 1: thread = output row,
-      // scaled + biased values go transposed into shared memory (the free
-      // pipeline buffers).  Pass 2: thread = (column, 8 consecutive rows):
-      // 16/32-byte residual loads and view stores, coalesced along channels.
-      const int32_t rloc = sub * 32 + lane;
-      const int32_t m = m0 + rloc;
-      const bool mok = m < a.M;
-      int32_t ch = m;
-      if (a.phases > 1) ch = m - (m / a.cout) * a.cout;
-      const float sc = mok ? a.scale[m] : 0.f;
-      const float bi = (mok && a.bias) ? a.bias[ch] : 0.f;
-      float* stage = reinterpret_cast<float*>(sA);  // 2 x 32 x 128 floats
-      for (int cb = 0, it = 0; cb < BN; cb += 32, ++it) {
-        if (n0 + cb >= N) break;  // uniform over the 128 epilogue threads
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)cb, r);
-        tmem_ld_wait();
-        float* stg = stage + (it & 1) * 32 * kBM;
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) stg[jj * kBM + rloc] = __uint_as_float(r[jj]) * sc + bi;
-        float4 skip_cur[4][2];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          skip_cur[q][0] = skip_next[q][0];
-          skip_cur[q][1] = skip_next[q][1];
+      // view geometry in registers (the loop reads no kernel parameters)
+      float* const ext = a.out.ext;
+      const int32_t ext_ch = ph * a.cout + ch;
+      const int32_t f_rows = a.out.f32.rows, f_p16 = a.out.f32.chans / 4;
+      const int32_t l_rows0 = a.out.lp[0].rows, l_rows1 = a.out.lp[1].rows;
+      const int32_t l_p16_0 = a.out.lp[0].chans / 8, l_p16_1 = a.out.lp[1].chans / 8;
+      const int32_t l_mir0 = a.out.lp[0].rows - a.out.lp[0].pre, l_mir1 = a.out.lp[1].rows - a.out.lp[1].pre;
+      const bool l_bf16 = (l_rows0 ? a.out.lp[0].dtype : a.out.lp[1].dtype) == kDtBF16;
+      const bool has_skip = a.has_skip != 0;
+      char* const f_base = arena + (int64_t)ch * 4;
+      char* const l_base = arena + (int64_t)ch * 2;
+#pragma unroll 1
+      for (int cb = 0; cb < BN; cb += 32) {
+        if (n0 + cb >= N) break;  // uniform over the CTA
+        const int cl = cb + lane;
+        const int64_t eb = col_ext[cl];
+        const uint32_t fo = col_off[cl], lo0 = col_off[BN + cl], lo1 = col_off[2 * BN + cl];
+        const uint32_t lm0 = col_mir[cl], lm1 = col_mir[BN + cl];
+        const int32_t fr = col_row[cl], lr0 = col_row[BN + cl], lr1 = col_row[2 * BN + cl];
+        const uint32_t so_cur = so_next;
+        const int32_t sr_cur = sr_next;
+        if (has_skip && cb + 32 < BN) {
+          so_next = col_off[3 * BN + cl + 32];
+          sr_next = col_row[3 * BN + cl + 32];
         }
-        fetch_skip(cb + 32, skip_next);
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int p = t + q * 128;
-          const int c = p >> 4, g = p & 15;
-          const int32_t mb = m0 + g * 8;
-          if (n0 + cb + c >= N || mb >= a.M) continue;
+#pragma unroll 1
+        for (int g = 0; g < 4; ++g) {
+          if (n0 + cb + 8 * g >= N) break;  // uniform
+          uint32_t r[8];
+          tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(cb + 8 * g), r);
+          tmem_ld_wait();
           float x[8];
-          const float4 x0 = *reinterpret_cast<const float4*>(stg + c * kBM + g * 8);
-          const float4 x1 = *reinterpret_cast<const float4*>(stg + c * kBM + g * 8 + 4);
-          x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
-          x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
-          const int32_t ph = a.phases > 1 ? mb / a.cout : 0;
-          const int32_t cg = mb - ph * a.cout;  // first channel of the group
-          const int col = cb + c;
-          char* base = a.batch.arena + col_slot[col];
-          if (a.has_skip) {
-            const float4 s0 = skip_cur[q][0], s1 = skip_cur[q][1];
-            x[0] += s0.x; x[1] += s0.y; x[2] += s0.z; x[3] += s0.w;
-            x[4] += s1.x; x[5] += s1.y; x[6] += s1.z; x[7] += s1.w;
-          }
-          if (a.out.ext) {
-            float* e = a.out.ext + col_ext[col] + (int64_t)ph * a.cout + cg;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) e[k] = x[k];
+          for (int k = 0; k < 8; ++k) x[k] = fmaf(__uint_as_float(r[k]), sc, bi) + (has_skip ? sk[k] : 0.f);
+          // the next group's residual loads overlap this group's stores
+          if (has_skip) {
+            if (g < 3)
+              load_skip(cb, g + 1, so_cur, sr_cur);
+            else if (cb + 32 < BN && n0 + cb + 32 < N)
+              load_skip(cb + 32, 0, so_next, sr_next);
           }
-          if (a.out.f32.rows) {
-            const int32_t row = wrap_row(col_row[col] + ph, a.out.f32.rows);
-            float4* d = reinterpret_cast<float4*>(base + a.out.f32.off +
-                                                  ((int64_t)row * a.out.f32.chans + cg) * 4);
-            d[0] = make_float4(x[0], x[1], x[2], x[3]);
-            d[1] = make_float4(x[4], x[5], x[6], x[7]);
-          }
+          // One pass per view (a uniform branch per group and view), each a
+          // branch-free 8-column body of broadcast + predicated store.
+          bool ok[8];
 #pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            const Ring& lr = a.out.lp[v];
-            if (!lr.rows) continue;
-            const int32_t row = wrap_row(col_row[(1 + v) * BN + col] + ph, lr.rows);
-            float y[8];
+          for (int k = 0; k < 8; ++k) ok[k] = mok && n0 + cb + 8 * g + k < N;
+          if (ext) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) y[k] = v ? leaky(x[k]) : x[k];
-            uint4 pk;
-            if (lr.dtype == kDtBF16) {
-              __nv_bfloat162 h0 = __floats2bfloat162_rn(y[0], y[1]), h1 = __floats2bfloat162_rn(y[2], y[3]);
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(y[4], y[5]), h3 = __floats2bfloat162_rn(y[6], y[7]);
-              pk.x = *reinterpret_cast<uint32_t*>(&h0); pk.y = *reinterpret_cast<uint32_t*>(&h1);
-              pk.z = *reinterpret_cast<uint32_t*>(&h2); pk.w = *reinterpret_cast<uint32_t*>(&h3);
-            } else {
-              __half2 h0 = __floats2half2_rn(y[0], y[1]), h1 = __floats2half2_rn(y[2], y[3]);
-              __half2 h2 = __floats2half2_rn(y[4], y[5]), h3 = __floats2half2_rn(y[6], y[7]);
-              pk.x = *reinterpret_cast<uint32_t*>(&h0); pk.y = *reinterpret_cast<uint32_t*>(&h1);
-              pk.z = *reinterpret_cast<uint32_t*>(&h2); pk.w = *reinterpret_cast<uint32_t*>(&h3);
+            for (int k = 0; k < 8; ++k) {
+              const int64_t e = shfl64(eb, 8 * g + k);
+              if (ok[k]) st_global_f32(ext + e + ext_ch, x[k]);
             }
-            *reinterpret_cast<uint4*>(base + lr.off + ((int64_t)row * lr.chans + cg) * 2) = pk;
+          }
+          if (f_rows) {
+            if (!phased) {
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                const uint32_t o = __shfl_sync(0xffffffffu, fo, 8 * g + k);
+                if (ok[k]) st_global_f32(f_base + (uint64_t)o * 16, x[k]);
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                const uint32_t o = phase_off(__shfl_sync(0xffffffffu, fo, 8 * g + k),
+                                             __shfl_sync(0xffffffffu, fr, 8 * g + k), f_rows, f_p16);
+                if (ok[k]) st_global_f32(f_base + (uint64_t)o * 16, x[k]);
+              }
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int32_t rows = q ? l_rows1 : l_rows0;
+            if (!rows) continue;
+            uint16_t h[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const float y = q ? leaky(x[k]) : x[k];
+              h[k] = l_bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(y)) : __half_as_ushort(__float2half_rn(y));
+            }
+            const uint32_t lo = q ? lo1 : lo0;
+            if (!phased) {
+              const uint32_t lm = q ? lm1 : lm0;
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                const uint32_t o = __shfl_sync(0xffffffffu, lo, 8 * g + k);
+                const uint32_t om = __shfl_sync(0xffffffffu, lm, 8 * g + k);
+                if (ok[k]) st_global_b16(l_base + (uint64_t)o * 16, h[k]);
+                if (ok[k] && om != ~0u) st_global_b16(l_base + (uint64_t)om * 16, h[k]);  // mirrored tail
+              }
+            } else {
+              const int32_t lr = q ? lr1 : lr0;
+              const int32_t p16 = q ? l_p16_1 : l_p16_0;
+              const int32_t mir = q ? l_mir1 : l_mir0;
+#pragma unroll
+              for (int k = 0; k < 8; ++k) {
+                const int32_t rw = __shfl_sync(0xffffffffu, lr, 8 * g + k);
+                const int32_t d = rw + ph >= rows ? ph - rows : ph;
+                const uint32_t o = __shfl_sync(0xffffffffu, lo, 8 * g + k) + (uint32_t)(d * p16);
+                if (ok[k]) st_global_b16(l_base + (uint64_t)o * 16, h[k]);
+                if (ok[k] && rw + d >= mir)  // mirrored tail
+                  st_global_b16(l_base + (uint64_t)(o - (uint32_t)(rows * p16)) * 16, h[k]);
+              }
+            }
           }
         }
       }
@@ -352,13 +473,15 @@ int tc_tile_n(int64_t n_cols, int m_tiles) {
   return ((n_cols + 255) / 256) * m_tiles >= 152 ? 256 : 128;
 }
 
-cudaError_t launch_conv_tc(const void* tmap_a, const void* tmap_b, const TcArgs& a, int bn,
+cudaError_t launch_conv_tc(const void* tmap_t, const void* tmap_b, const TcArgs& a, int bn,
                            cudaStream_t st) {
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   if (N <= 0) return cudaSuccess;
-  const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(tmap_a);
+  const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(tmap_t);
   const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(tmap_b);
   if (bn == 256) return launch_bn<256, 4>(ta, tb, a, st);
+  const int64_t ctas = (N + 127) / 128 * ((a.M + kBM - 1) / kBM);
+  if (ctas <= 148) return launch_bn<128, 6>(ta, tb, a, st);
   return launch_bn<128, 2>(ta, tb, a, st);
 }
 

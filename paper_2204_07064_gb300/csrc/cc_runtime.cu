@@ -199,7 +199,10 @@ static size_t lcm_size(size_t a, size_t b) {
 
 // Low-precision views are aligned to their row pitch (and the slot size to
 // every such pitch) so that a single 2D tensor map over the arena addresses
-// the rows of that view in every stream's slot.
+// the rows of that view in every stream's slot.  Their rings hold whole
+// steps (R a multiple of u, so a one-step call never crosses the ring's end)
+// and at least four times the kept history, whose mirror sits before row 0:
+// the mirrored tail costs at most a quarter of the view's stores.
 static cc_status plan_arena(Model& m) {
   size_t off = 0, state = 0, slot_align = 256;
   const int n = (int)m.nodes.size();
@@ -211,16 +214,24 @@ static cc_status plan_arena(Model& m) {
     for (int v = 0; v < 3; ++v) {
       if (!p.used_view[v]) continue;
       Ring& r = p.view[v];
-      r.rows = p.keep_view[v] + p.u * m.max_steps;
+      const int64_t keep = p.keep_view[v];
+      int64_t rows = keep + (int64_t)p.u * m.max_steps;
       r.chans = p.d.c_out;
       r.u = p.u;
       r.dtype = v == 0 ? kDtF32 : m.lp_dtype;
+      r.pre = 0;
       const size_t elem = v == 0 ? 4 : 2;
       if (v > 0) {
         const size_t pitch = (size_t)r.chans * elem;
+        rows = std::max(rows, 4 * keep);
+        rows = (rows + p.u - 1) / p.u * p.u;
+        r.pre = (int32_t)keep;
         off = align_up(off, lcm_size(256, pitch));
+        off += (size_t)r.pre * pitch;
         slot_align = lcm_size(slot_align, pitch);
       }
+      if (rows >= (1ll << 30)) return fail(CC_ERR_NO_MEMORY, "ring of node %d too long", i);
+      r.rows = (int32_t)rows;
       r.off = (int64_t)off;
       off = align_up(off + (size_t)r.rows * r.chans * elem, 256);
       state += (size_t)p.keep_view[v] * p.d.c_out * elem;
@@ -336,6 +347,23 @@ static cc_status encode_gather_maps(Model& m) {
                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(CC_ERR_CUDA, "gather tensor map encoding failed (%d)", (int)r);
+    // box maps: the view of every slot as [slot][pre + R rows][C]; box i covers
+    // 2^i consecutive rows of 2^(7-i) consecutive slots (128 rows in all).  A
+    // shape the driver rejects (a box larger than the view) stays unused.
+    const cuuint64_t d3[3] = {(cuuint64_t)in.chans, (cuuint64_t)(in.pre + in.rows), (cuuint64_t)m.max_streams};
+    const cuuint64_t s3[2] = {(cuuint64_t)pitch, (cuuint64_t)m.slot_bytes};
+    const cuuint32_t e3[3] = {1, 1, 1};
+    for (int li = 0; li < 8; ++li) {
+      const cuuint32_t b3[3] = {64, 1u << li, 1u << (7 - li)};
+      p.tmapT_ok[li] = false;
+      if (b3[1] > d3[1] || b3[2] > d3[2]) continue;
+      const CUresult r3 = enc(reinterpret_cast<CUtensorMap*>(p.tmapT[li]),
+                              m.lp_dtype == kDtBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                              3, m.arena + in.off - (int64_t)in.pre * (int64_t)pitch, d3, s3, b3, e3,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      p.tmapT_ok[li] = r3 == CUDA_SUCCESS;
+    }
   }
   return CC_OK;
 }
@@ -426,10 +454,16 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
     o.ext_stride = out_stride;
     return o;
   };
+  // launch index at which each node's values were written (a fused add's by
+  // its producer's launch): a residual written two or more launches before
+  // its reader is final when the reader starts (see k_conv_tc)
+  std::vector<int> made_at(n, -1);
+  int launches = 0;
   for (int i = 0; i < n; ++i) {
     NodePlan& p = nodes[i];
     const cc_node_desc& d = p.d;
     if (d.op == CC_OP_INPUT) {
+      made_at[i] = launches++;
       InputArgs a{};
       a.src = in;
       a.src_stride = in_stride;
@@ -450,6 +484,8 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
     const NodePlan& w = nodes[wi];
     if (wi != last && !w.has_ring) continue;  // dead branch
     const OutViews ov = views_of(wi);
+    const int this_launch = launches++;
+    made_at[i] = made_at[wi] = this_launch;
     cc_status s = begin(i);
     if (s) return s;
     if (d.op == CC_OP_CONV || d.op == CC_OP_CONVT) {
@@ -481,11 +517,22 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
           a.has_skip = 1;
           a.skip = nodes[p.fused_skip].view[0];
           a.skip_A = p.fused_skip_A;
+          const int sm = made_at[p.fused_skip];
+          a.skip_early = sm >= 0 && sm <= this_launch - 2;
         }
         a.batch = batch;
         a.err = err;
+        // 3D window boxes: stride 1 and a box of min(ncols, 128) frames that
+        // tiles the 128-column halves of a tile exactly
+        int li = -1;
+        if (stride == 1 && (128 % ncols == 0 || ncols % 128 == 0)) {
+          li = 0;
+          while ((1 << li) < std::min(ncols, 128)) ++li;
+          if (!p.tmapT_ok[li]) li = -1;
+        }
+        a.box_ok = li >= 0;
         const int bn = tile_n_for(p, (int64_t)batch.count * ncols);
-        CC_CUDA(launch_conv_tc(p.tmap, p.tmapB, a, bn, st));
+        CC_CUDA(launch_conv_tc(li >= 0 ? p.tmapT[li] : p.tmapB, p.tmapB, a, bn, st));
       } else {
         ConvArgs a{};
         a.A = p.dA;
@@ -778,7 +825,9 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
   if (!s) s = cc::pack_and_upload(*m, weights, biases);
   if (!s) {
     const size_t arena_bytes = m->slot_bytes * (size_t)m->max_streams;
-    cudaError_t e = cudaMalloc(&m->arena, arena_bytes);
+    // the tensor-core epilogue addresses the arena in 32-bit 16-byte units
+    cudaError_t e = arena_bytes >= (size_t(1) << 36) ? cudaErrorMemoryAllocation
+                                                     : cudaMalloc(&m->arena, arena_bytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       m->arena = nullptr;

@@ -46,6 +46,9 @@ struct NodePlan {
   float* dscale = nullptr;
   alignas(64) unsigned char tmap[128] = {};   // weights
   alignas(64) unsigned char tmapB[128] = {};  // input view as arena rows
+  // input view as [slot][pre + R][C], boxes of 64 x 2^i rows x 2^(7-i) slots
+  alignas(64) unsigned char tmapT[8][128] = {};
+  bool tmapT_ok[8] = {};
   int32_t in_rows_per_slot = 0, in_row_off = 0;
   std::map<int64_t, int32_t> tile_n;  // autotuned N tile by launch width (columns), 0: heuristic
 };

@@ -285,3 +285,35 @@ def test_decoder_bf16_noise_off_vs_original(cclib, cuda):
     yo = M.run_original(dec, p, z, seed=1, noise_on=False)
     d, w = model.total_delay, M.warmup_frames(dec)
     _assert_lowp(y[d + w:], yo[w:len(yo) - d], "bf16 vs original delayed")
+
+
+def test_lowp_window_boxes_match_gathers(cclib, cuda):
+    """The tensor-core producer loads a tile's window rows as one 3D box when
+    its streams sit in consecutive slots at one step, and gathers them row by
+    row otherwise.  Both forms feed the same operands to the same MMAs, so a
+    batch in slot order (boxes, a partial last tile whose box reaches past the
+    last slot) and the same streams in reverse order (gathers) agree exactly,
+    over enough steps for every ring to wrap through its mirrored tail; one
+    stream is checked against the oracle."""
+    import torch
+
+    dec, p = _decoder(11)
+    count, steps = 50, 40
+    seeds = W.stream_seeds(77, count)
+    z = np.random.default_rng(5).standard_normal((steps, count, 1, 128))
+    outs = []
+    for order in (np.arange(count), np.arange(count)[::-1]):
+        model = api.Model(dec, p, dtype="bf16", max_streams=count, max_steps_per_call=1)
+        streams = [model.stream(seed=s) for s in seeds]
+        batch = [streams[i] for i in order]
+        y = torch.empty((count, 2048, 1), dtype=torch.float32, device=cuda)
+        o = np.zeros((count, steps * 2048))
+        for t in range(steps):
+            model.process_batch(batch, torch.tensor(z[t][order], dtype=torch.float32, device=cuda), y)
+            o[order, t * 2048:(t + 1) * 2048] = y[:, :, 0].cpu().numpy()
+        assert model.device_status() == 0
+        outs.append(o)
+        model.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    ref = M.run_causal(dec, p, z[:, 31, 0, :], seed=seeds[31])[:, 0]
+    _assert_lowp(outs[0][31], ref, "bf16 stream 31 of 50, 40 steps")

@@ -17,8 +17,9 @@
 //              copies, so every stage can be in flight
 //   warp 1     TMEM allocation; lane 0 issues tcgen05.mma (128 x BN x 16,
 //              BF16 or FP16 operands, FP32 accumulation in TMEM)
-//   warps 2-5  epilogue: warp w owns accumulator rows 32*(w%4) .. +31 (its
-//              TMEM lane quarter); per 32-column chunk it loads the rows
+//   warps 2-9  epilogue: warp w owns accumulator rows 32*(w%4) .. +31 (its
+//              TMEM lane quarter) and every other group of 8 columns (the two
+//              warps of a quarter alternate); per group it loads the rows
 //              (tcgen05.ld), applies scale, bias and the aligned residual and
 //              stores every view column by column, each store covering 32
 //              consecutive channels (coalesced), with ring addresses from a
@@ -46,13 +47,14 @@ namespace {
 using namespace sm100;
 
 constexpr int kBM = 128;
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;  // producer, MMA issuer, 8 epilogue warps
+constexpr int kEpi = 256;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
 // Pipeline depth: 128-column tiles run 6 stages when the grid fits in one wave
-// (one CTA per SM: few CTAs with long K loops need deep prefetch), else 2
-// stages (three CTAs per SM, whose epilogues overlap each other's main
-// loops); 256-column tiles use 4 stages.
+// (one CTA per SM: few CTAs with long K loops need deep prefetch), else 3
+// stages (two CTAs per SM, whose epilogues overlap each other's main loops);
+// 256-column tiles use 4 stages.
 template <int BN, int STAGES>
 struct TcLayout {
   static constexpr int kStages = STAGES;
@@ -64,7 +66,7 @@ struct TcLayout {
   // the mirror row's offset (low-precision views); the caller-buffer offset
   static constexpr int kCols = BN * (4 * 4 + 4 * 4 + 2 * 4 + 8);
   static constexpr int kBytes = 1024 + kStages * (kA + kB) + kBars + kCols + 64;
-  static constexpr int kMinBlocks = STAGES == 2 ? 3 : 1;
+  static constexpr int kMinBlocks = STAGES == 3 ? 2 : 1;
 };
 
 template <int BN, int STAGES>
@@ -233,8 +235,9 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     }
   } else {
     // ---------------------------------------------------------------- epilogue
-    const int t = threadIdx.x - 64;  // 0..127
+    const int t = threadIdx.x - 64;  // 0..255
     const int sub = warp & 3;        // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;  // which groups of 8 columns: half, half + 2
     const int32_t m = m0 + sub * 32 + lane;  // accumulator row of this thread
     const bool mok = m < a.M;
     const int32_t ph = (mok && a.phases > 1) ? m / a.cout : 0;  // transposed conv: phase
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     // low-precision view also the offset of its mirror row (~0u if the row is
     // not in the mirrored tail; used when phases == 1).  The arena is below
     // 64 GiB, so offsets fit 32 bits.
-    for (int c = t; c < BN; c += 128) {
+    for (int c = t; c < BN; c += kEpi) {
       const int64_t n = n0 + c;
       if (n >= N) break;
       const int32_t s = (int32_t)(n / a.ncols);
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
       put(2, a.out.lp[1].off, a.out.lp[1].rows, a.out.lp[1].chans, a.out.lp[1].pre, tb, 2);
       put(3, a.skip.off, a.skip.rows, a.skip.chans, 0, tb - a.skip_A, 4);
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");  // column table complete
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // column table complete
     char* const arena = a.batch.arena;
     const bool phased = a.phases > 1;
     // Offset (16-byte units) of this thread's row of a column for a phased
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     char* const sk_base = arena + (int64_t)ch * 4;
     // residual rows of the tile: every 128-byte line into L2 ahead of use
     auto prefetch_skip = [&]() {
-      for (int c = t; c < BN; c += 128) {
+      for (int c = t; c < BN; c += kEpi) {
         if (n0 + c >= N) break;
         for (int k = 0; k < kBM; k += 32) {
           const int32_t mm = m0 + k;
@@ -313,22 +316,22 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     }
     if (a.has_skip && a.skip_early) {
       prefetch_skip();
-      load_skip(0, 0, so_next, sr_next);
+      load_skip(0, half, so_next, sr_next);
     }
     pdl_wait();
     pdl_release();
     if (a.has_skip && !a.skip_early) {
       prefetch_skip();
-      load_skip(0, 0, so_next, sr_next);
+      load_skip(0, half, so_next, sr_next);
     }
-    // one verdict for all 128 epilogue threads (a reduction barrier), so the
+    // one verdict for all epilogue threads (a reduction barrier), so the
     // named barriers stay matched
     const bool waited = mbar_wait(tfull, 0, kWaitNs);
     uint32_t all_ok;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, 1, 128, q;\n\t"
+        "bar.red.and.pred p, 1, 256, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(all_ok)
         : "r"((uint32_t)waited)
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
           sr_next = col_row[3 * BN + cl + 32];
         }
 #pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
+        for (int g = half; g < 4; g += 2) {
           if (n0 + cb + 8 * g >= N) break;  // uniform
           uint32_t r[8];
           tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(cb + 8 * g), r);
@@ -373,10 +376,10 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
           for (int k = 0; k < 8; ++k) x[k] = fmaf(__uint_as_float(r[k]), sc, bi) + (has_skip ? sk[k] : 0.f);
           // the next group's residual loads overlap this group's stores
           if (has_skip) {
-            if (g < 3)
-              load_skip(cb, g + 1, so_cur, sr_cur);
+            if (g + 2 < 4)
+              load_skip(cb, g + 2, so_cur, sr_cur);
             else if (cb + 32 < BN && n0 + cb + 32 < N)
-              load_skip(cb + 32, 0, so_next, sr_next);
+              load_skip(cb + 32, half, so_next, sr_next);
           }
           // One pass per view (a uniform branch per group and view), each a
           // branch-free 8-column body of broadcast + predicated store.
@@ -482,7 +485,7 @@ cudaError_t launch_conv_tc(const void* tmap_t, const void* tmap_b, const TcArgs&
   if (bn == 256) return launch_bn<256, 4>(ta, tb, a, st);
   const int64_t ctas = (N + 127) / 128 * ((a.M + kBM - 1) / kBM);
   if (ctas <= 148) return launch_bn<128, 6>(ta, tb, a, st);
-  return launch_bn<128, 2>(ta, tb, a, st);
+  return launch_bn<128, 3>(ta, tb, a, st);
 }
 
 }  // namespace cc

@@ -20,11 +20,12 @@
 //   warps 2-9  epilogue: warp w owns accumulator rows 32*(w%4) .. +31 (its
 //              TMEM lane quarter) and every other group of 8 columns (the two
 //              warps of a quarter alternate); per group it loads the rows
-//              (tcgen05.ld), applies scale, bias and the aligned residual and
-//              stores every view column by column, each store covering 32
-//              consecutive channels (coalesced), with ring addresses from a
-//              per-column table built before the kernel waits on its
-//              predecessor
+//              (tcgen05.ld), applies scale and bias, turns the 32 x 8 block
+//              around in 1 KB of shared memory so that each lane holds 8
+//              consecutive channels of one column, adds the aligned residual
+//              (16-byte loads) and stores every view with 16-byte stores, at
+//              ring addresses from a per-column table built before the
+//              kernel waits on its predecessor
 // Every mbarrier wait is bounded in time and records an error in the model's
 // device error word instead of hanging.
 //
@@ -65,7 +66,8 @@ struct TcLayout {
   // units of the ring row holding the column's first frame, that ring row,
   // the mirror row's offset (low-precision views); the caller-buffer offset
   static constexpr int kCols = BN * (4 * 4 + 4 * 4 + 2 * 4 + 8);
-  static constexpr int kBytes = 1024 + kStages * (kA + kB) + kBars + kCols + 64;
+  static constexpr int kTurn = 8 * 32 * 8 * 4;  // per epilogue warp: 32 rows x 8 columns of FP32
+  static constexpr int kBytes = 1024 + kStages * (kA + kB) + kBars + kCols + kTurn + 64;
   static constexpr int kMinBlocks = STAGES == 3 ? 2 : 1;
 };
 
@@ -88,6 +90,8 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
   uint32_t* col_off = reinterpret_cast<uint32_t*>(col_ext + BN);  // [4][BN], 16-byte units
   int32_t* col_row = reinterpret_cast<int32_t*>(col_off + 4 * BN);  // [4][BN]
   uint32_t* col_mir = reinterpret_cast<uint32_t*>(col_row + 4 * BN);  // [2][BN], ~0u: none
+  float* turn = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(col_mir + 2 * BN) + 15) & ~static_cast<uintptr_t>(15));  // [8 warps][8][32]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t m0 = blockIdx.y * kBM;
@@ -273,13 +277,22 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     asm volatile("bar.sync 1, 256;" ::: "memory");  // column table complete
     char* const arena = a.batch.arena;
     const bool phased = a.phases > 1;
-    // Offset (16-byte units) of this thread's row of a column for a phased
-    // (transposed) layer: the column's first row + ph, wrapped at the ring end.
+    // After the turn, lane l holds column kk = l / 4 of its group and the 8
+    // consecutive rows 8*(l % 4) .. +7 of its warp's 32: channels ch_l .. +7
+    // of phase ph_l (cout is a multiple of 8, so they share a phase).
+    const int kk = lane >> 2;
+    const int32_t mrow = m0 + sub * 32 + 8 * (lane & 3);
+    const bool vok = mrow < a.M;
+    const int32_t ph_l = (vok && phased) ? mrow / a.cout : 0;
+    const int32_t ch_l = vok ? mrow - ph_l * a.cout : 0;
+    float* const tw = turn + (warp - 2) * 256;
+    // Offset (16-byte units) of this lane's row of a column for a phased
+    // (transposed) layer: the column's first row + ph_l, wrapped at the ring end.
     auto phase_off = [&](uint32_t o16, int32_t row, int32_t rows, int32_t pitch16) -> uint32_t {
-      return o16 + (uint32_t)((row + ph >= rows ? ph - rows : ph) * pitch16);
+      return o16 + (uint32_t)((row + ph_l >= rows ? ph_l - rows : ph_l) * pitch16);
     };
     const int32_t s_rows = a.skip.rows, s_p16 = a.skip.chans / 4;
-    char* const sk_base = arena + (int64_t)ch * 4;
+    char* const sk_base = arena + (int64_t)ch_l * 4;
     // residual rows of the tile: every 128-byte line into L2 ahead of use
     auto prefetch_skip = [&]() {
       for (int c = t; c < BN; c += kEpi) {
@@ -294,19 +307,19 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
         }
       }
     };
-    // Columns go in groups of 8 (one tcgen05.ld each) inside chunks of 32:
-    // per chunk each lane holds the table entries of column cb + lane and the
-    // store loop broadcasts them (no shared-memory reads between stores).
-    // The group body is the only unrolled code, so the loop stays small in
-    // the instruction cache.
-    float sk[8];
+    // Columns go in groups of 8 inside chunks of 32: per chunk lane l holds
+    // the table entries of column cb + l; a group's lanes fetch those of their
+    // column by one shuffle per view.  Residual values of the next group are
+    // requested before the current group's stores.
+    float4 sk0 = make_float4(0.f, 0.f, 0.f, 0.f), sk1 = sk0;
     auto load_skip = [&](int cb, int g, uint32_t so, int32_t sr) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        uint32_t o = __shfl_sync(0xffffffffu, so, 8 * g + k);
-        if (phased) o = phase_off(o, __shfl_sync(0xffffffffu, sr, 8 * g + k), s_rows, s_p16);
-        sk[k] = (mok && n0 + cb + 8 * g + k < N) ? ld_global_nc_f32(sk_base + (uint64_t)o * 16) : 0.f;
-      }
+      uint32_t o = __shfl_sync(0xffffffffu, so, 8 * g + kk);
+      const int32_t rw = __shfl_sync(0xffffffffu, sr, 8 * g + kk);
+      if (phased) o = phase_off(o, rw, s_rows, s_p16);
+      const bool ok = vok && n0 + cb + 8 * g + kk < N;
+      const char* pa = sk_base + (uint64_t)o * 16;
+      sk0 = ok ? ld_global_nc_v4(pa) : make_float4(0.f, 0.f, 0.f, 0.f);
+      sk1 = ok ? ld_global_nc_v4(pa + 16) : make_float4(0.f, 0.f, 0.f, 0.f);
     };
     uint32_t so_next = 0;
     int32_t sr_next = 0;
@@ -342,15 +355,23 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     } else {
       // view geometry in registers (the loop reads no kernel parameters)
       float* const ext = a.out.ext;
-      const int32_t ext_ch = ph * a.cout + ch;
+      const int64_t ext_ch = (int64_t)ph_l * a.cout + ch_l;
       const int32_t f_rows = a.out.f32.rows, f_p16 = a.out.f32.chans / 4;
       const int32_t l_rows0 = a.out.lp[0].rows, l_rows1 = a.out.lp[1].rows;
       const int32_t l_p16_0 = a.out.lp[0].chans / 8, l_p16_1 = a.out.lp[1].chans / 8;
       const int32_t l_mir0 = a.out.lp[0].rows - a.out.lp[0].pre, l_mir1 = a.out.lp[1].rows - a.out.lp[1].pre;
       const bool l_bf16 = (l_rows0 ? a.out.lp[0].dtype : a.out.lp[1].dtype) == kDtBF16;
       const bool has_skip = a.has_skip != 0;
-      char* const f_base = arena + (int64_t)ch * 4;
-      char* const l_base = arena + (int64_t)ch * 2;
+      char* const f_base = arena + (int64_t)ch_l * 4;
+      char* const l_base = arena + (int64_t)ch_l * 2;
+      auto pack = [&](float lo, float hi) -> uint32_t {
+        if (l_bf16) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+          return *reinterpret_cast<const uint32_t*>(&h);
+        }
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t*>(&h);
+      };
 #pragma unroll 1
       for (int cb = 0; cb < BN; cb += 32) {
         if (n0 + cb >= N) break;  // uniform over the CTA
@@ -371,78 +392,62 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
           uint32_t r[8];
           tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(cb + 8 * g), r);
           tmem_ld_wait();
-          float x[8];
+          // turn: row-per-lane values in, 8-channel column slices out
+          __syncwarp();
 #pragma unroll
-          for (int k = 0; k < 8; ++k) x[k] = fmaf(__uint_as_float(r[k]), sc, bi) + (has_skip ? sk[k] : 0.f);
-          // the next group's residual loads overlap this group's stores
+          for (int k = 0; k < 8; ++k) tw[k * 32 + lane] = fmaf(__uint_as_float(r[k]), sc, bi);
+          __syncwarp();
+          const float4 v0 = *reinterpret_cast<const float4*>(tw + kk * 32 + 8 * (lane & 3));
+          const float4 v1 = *reinterpret_cast<const float4*>(tw + kk * 32 + 8 * (lane & 3) + 4);
+          float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
           if (has_skip) {
+            x[0] += sk0.x; x[1] += sk0.y; x[2] += sk0.z; x[3] += sk0.w;
+            x[4] += sk1.x; x[5] += sk1.y; x[6] += sk1.z; x[7] += sk1.w;
+            // the next group's residual loads overlap this group's stores
             if (g + 2 < 4)
               load_skip(cb, g + 2, so_cur, sr_cur);
             else if (cb + 32 < BN && n0 + cb + 32 < N)
               load_skip(cb + 32, half, so_next, sr_next);
           }
-          // One pass per view (a uniform branch per group and view), each a
-          // branch-free 8-column body of broadcast + predicated store.
-          bool ok[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) ok[k] = mok && n0 + cb + 8 * g + k < N;
+          const int src = 8 * g + kk;  // table lane of this lane's column
+          const bool ok = vok && n0 + cb + src < N;
           if (ext) {
+            const int64_t e = shfl64(eb, src) + ext_ch;
+            if (ok)
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const int64_t e = shfl64(eb, 8 * g + k);
-              if (ok[k]) st_global_f32(ext + e + ext_ch, x[k]);
-            }
+              for (int i = 0; i < 8; ++i) st_global_f32(ext + e + i, x[i]);
           }
           if (f_rows) {
-            if (!phased) {
-#pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                const uint32_t o = __shfl_sync(0xffffffffu, fo, 8 * g + k);
-                if (ok[k]) st_global_f32(f_base + (uint64_t)o * 16, x[k]);
-              }
-            } else {
-#pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                const uint32_t o = phase_off(__shfl_sync(0xffffffffu, fo, 8 * g + k),
-                                             __shfl_sync(0xffffffffu, fr, 8 * g + k), f_rows, f_p16);
-                if (ok[k]) st_global_f32(f_base + (uint64_t)o * 16, x[k]);
-              }
+            uint32_t o = __shfl_sync(0xffffffffu, fo, src);
+            const int32_t rw = __shfl_sync(0xffffffffu, fr, src);
+            if (phased) o = phase_off(o, rw, f_rows, f_p16);
+            char* pa = f_base + (uint64_t)o * 16;
+            if (ok) {
+              st_global_v4(pa, make_uint4(__float_as_uint(x[0]), __float_as_uint(x[1]), __float_as_uint(x[2]),
+                                          __float_as_uint(x[3])));
+              st_global_v4(pa + 16, make_uint4(__float_as_uint(x[4]), __float_as_uint(x[5]),
+                                               __float_as_uint(x[6]), __float_as_uint(x[7])));
             }
           }
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             const int32_t rows = q ? l_rows1 : l_rows0;
             if (!rows) continue;
-            uint16_t h[8];
+            float y[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const float y = q ? leaky(x[k]) : x[k];
-              h[k] = l_bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(y)) : __half_as_ushort(__float2half_rn(y));
-            }
-            const uint32_t lo = q ? lo1 : lo0;
-            if (!phased) {
-              const uint32_t lm = q ? lm1 : lm0;
-#pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                const uint32_t o = __shfl_sync(0xffffffffu, lo, 8 * g + k);
-                const uint32_t om = __shfl_sync(0xffffffffu, lm, 8 * g + k);
-                if (ok[k]) st_global_b16(l_base + (uint64_t)o * 16, h[k]);
-                if (ok[k] && om != ~0u) st_global_b16(l_base + (uint64_t)om * 16, h[k]);  // mirrored tail
-              }
-            } else {
-              const int32_t lr = q ? lr1 : lr0;
+            for (int i = 0; i < 8; ++i) y[i] = q ? leaky(x[i]) : x[i];
+            const uint4 pk = make_uint4(pack(y[0], y[1]), pack(y[2], y[3]), pack(y[4], y[5]), pack(y[6], y[7]));
+            uint32_t o = __shfl_sync(0xffffffffu, q ? lo1 : lo0, src);
+            uint32_t om = __shfl_sync(0xffffffffu, q ? lm1 : lm0, src);
+            if (phased) {
+              const int32_t rw = __shfl_sync(0xffffffffu, q ? lr1 : lr0, src);
               const int32_t p16 = q ? l_p16_1 : l_p16_0;
-              const int32_t mir = q ? l_mir1 : l_mir0;
-#pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                const int32_t rw = __shfl_sync(0xffffffffu, lr, 8 * g + k);
-                const int32_t d = rw + ph >= rows ? ph - rows : ph;
-                const uint32_t o = __shfl_sync(0xffffffffu, lo, 8 * g + k) + (uint32_t)(d * p16);
-                if (ok[k]) st_global_b16(l_base + (uint64_t)o * 16, h[k]);
-                if (ok[k] && rw + d >= mir)  // mirrored tail
-                  st_global_b16(l_base + (uint64_t)(o - (uint32_t)(rows * p16)) * 16, h[k]);
-              }
+              const int32_t d = rw + ph_l >= rows ? ph_l - rows : ph_l;
+              o += (uint32_t)(d * p16);
+              om = rw + d >= (q ? l_mir1 : l_mir0) ? o - (uint32_t)(rows * p16) : ~0u;
             }
+            if (ok) st_global_v4(l_base + (uint64_t)o * 16, pk);
+            if (ok && om != ~0u) st_global_v4(l_base + (uint64_t)om * 16, pk);  // mirrored tail
           }
         }
       }

@@ -31,7 +31,10 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
-SUB_BATCHES = {"f32": 1, "bf16": 4, "f16": 4}  # concurrent launch chains per step (default)
+# Concurrent launch chains per step (default): one per 256 streams in the
+# low-precision modes (measured best at 256, 1024 and 2048 streams), one in FP32.
+def default_sub_batches(dtype, streams):
+    return 1 if dtype == "f32" else max(1, streams // 256)
 
 WORKLOADS = {
     # name: (dtype, streams, buffer latent frames)
@@ -390,7 +393,7 @@ def main():
     # one step = every stream advances one buffer; the streams are split into
     # sub-batches launched on separate CUDA streams so that the launch chains
     # overlap (each chain is latency-bound at this batch size)
-    nsub = args.sub_batches or SUB_BATCHES[dtype]
+    nsub = args.sub_batches or default_sub_batches(dtype, streams)
     nsub = max(1, min(nsub, streams))
     bounds = [round(k * streams / nsub) for k in range(nsub + 1)]
     side = [torch.cuda.Stream() for _ in range(nsub)]

@@ -96,6 +96,7 @@ struct TcArgs {
   OutViews out;
   int32_t has_skip, skip_A;
   int32_t skip_early;  // the residual's producer launched two or more launches back
+  int32_t ksplit;      // split-K factor (1, 2 or 4): CTAs per cluster sharing a tile
   Ring skip;
   Batch batch;
   int32_t* err;  // device error word: set when a bounded wait gives up

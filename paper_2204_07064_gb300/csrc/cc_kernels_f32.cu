@@ -353,6 +353,66 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Narrow contraction (M <= 32 rows, Kt <= 64, cin % 4 == 0): one thread per
+// GEMM column with the weights in shared memory (every thread reads the same
+// weight: a broadcast) and its window read once, 16 bytes at a time.  Used by
+// the tail of the decoder (the noise branch's second conv, the inverse PQMF).
+// ---------------------------------------------------------------------------
+template <int TM>
+__global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
+  __shared__ float As[TM * 64];
+  // weights are written once at model creation: staged before the wait
+  for (int i = threadIdx.x; i < a.M * a.Kt; i += 128) As[i] = a.A[i];
+  __syncthreads();
+  pdl_wait();
+  pdl_release();
+  const int32_t n = blockIdx.x * 128 + threadIdx.x;
+  const int32_t N = a.batch.count * a.ncols;
+  if (n >= N) return;
+  const int32_t s = n / a.ncols, j = n - s * a.ncols;
+  const float* col = ring_ptr<const float>(a.batch, s, a.in);
+  const int32_t r0 =
+      (int32_t)ring_row(steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist, a.in.rows);
+  float acc[TM];
+#pragma unroll
+  for (int m = 0; m < TM; ++m) acc[m] = 0.f;
+  for (int32_t tap = 0; tap < a.taps; ++tap) {
+    const float* x = col + (int64_t)wrap_row(r0 + tap * a.dil, a.in.rows) * a.cin;
+    const float* w = As + tap * a.cin;
+    for (int32_t c = 0; c < a.cin; c += 4) {
+      const float4 v4 = *reinterpret_cast<const float4*>(x + c);
+      const float v[4] = {activate(v4.x, a.act), activate(v4.y, a.act), activate(v4.z, a.act),
+                          activate(v4.w, a.act)};
+#pragma unroll
+      for (int m = 0; m < TM; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[m] = fmaf(w[m * a.Kt + c + q], v[q], acc[m]);
+    }
+  }
+  // an output that is only the caller's buffer with the TM rows contiguous
+  // there (one phase per row of one channel, or channels of one phase):
+  // 16-byte stores
+  const bool ext_only = a.out.ext && !a.out.f32.rows && !a.out.lp[0].rows && !a.out.lp[1].rows && !a.has_skip;
+  if (ext_only && a.M == TM && (a.cout == 1 || a.phases == 1)) {
+    float* e = a.out.ext + (int64_t)s * a.out.ext_stride + (int64_t)j * TM;
+    if ((reinterpret_cast<uintptr_t>(e) & 15) == 0) {
+#pragma unroll
+      for (int m = 0; m < TM; m += 4) {
+        float b4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b4[q] = acc[m + q] + (a.bias ? a.bias[a.cout == 1 ? 0 : m + q] : 0.f);
+        *reinterpret_cast<float4*>(e + m) = make_float4(b4[0], b4[1], b4[2], b4[3]);
+      }
+      return;
+    }
+  }
+  int32_t ms[TM];
+#pragma unroll
+  for (int m = 0; m < TM; ++m) ms[m] = m;
+  store_column<TM>(a, n, ms, acc, (a.cout % 4 == 0) && (a.M % 4 == 0));
+}
+
+// ---------------------------------------------------------------------------
 // Element-wise kernels
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
@@ -371,29 +431,39 @@ __device__ __forceinline__ float noise_uniform(uint64_t seed, int64_t frame, int
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 
+// One thread per (stream, frame): the ring rows of the three branches and of
+// every output view are computed once, then all bands (4 at a time when the
+// band count allows).
 __global__ void k_heads(const HeadsArgs a) {
   pdl_wait();
   pdl_release();
-  const int64_t total = (int64_t)a.batch.count * a.ncols * a.bands;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t b = (int32_t)(i % a.bands);
-    const int64_t nj = i / a.bands;
-    const int32_t j = (int32_t)(nj % a.ncols);
+  const int64_t total = (int64_t)a.batch.count * a.ncols;
+  for (int64_t nj = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; nj < total;
+       nj += (int64_t)gridDim.x * blockDim.x) {
     const int32_t s = (int32_t)(nj / a.ncols);
+    const int32_t j = (int32_t)(nj - (int64_t)s * a.ncols);
     const int64_t t = steps_of(a.batch, s) * a.out_u + j;
-    float v[3];
+    char* base = slot_base(a.batch, s);
+    const float* in[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float* p = ring_ptr<const float>(a.batch, s, a.in[q]);
-      v[q] = p[ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + b];
+    for (int q = 0; q < 3; ++q)
+      in[q] = reinterpret_cast<const float*>(base + a.in[q].off) +
+              ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans;
+    const uint64_t seed = a.batch.seeds[a.batch.slots[s]];
+    const int32_t rf = a.out.f32.rows ? (int32_t)ring_row(t, a.out.f32.rows) : 0;
+    const int32_t r0 = a.out.lp[0].rows ? (int32_t)ring_row(t, a.out.lp[0].rows) : 0;
+    const int32_t r1 = a.out.lp[1].rows ? (int32_t)ring_row(t, a.out.lp[1].rows) : 0;
+    float* fo = a.out.f32.rows ? reinterpret_cast<float*>(base + a.out.f32.off) + (int64_t)rf * a.out.f32.chans
+                               : nullptr;
+    float* eo = a.out.ext ? a.out.ext + (int64_t)s * a.out.ext_stride + (int64_t)j * a.bands : nullptr;
+    for (int32_t b = 0; b < a.bands; ++b) {
+      float y = tanhf(in[0][b]) * sigmoidf_(in[1][b]);
+      if (a.noise) y += sigmoidf_(in[2][b]) * noise_uniform(seed, t - a.delay, b, a.bands);
+      if (fo) fo[b] = y;
+      if (eo) eo[b] = y;
+      if (a.out.lp[0].rows) store_lp(base, a.out.lp[0], r0, b, y);
+      if (a.out.lp[1].rows) store_lp(base, a.out.lp[1], r1, b, leaky(y));
     }
-    float y = tanhf(v[0]) * sigmoidf_(v[1]);
-    if (a.noise) {
-      const uint64_t seed = a.batch.seeds[a.batch.slots[s]];
-      y += sigmoidf_(v[2]) * noise_uniform(seed, t - a.delay, b, a.bands);
-    }
-    store_views(a.batch, s, a.out, t, j, b, a.bands, y);
   }
 }
 
@@ -454,6 +524,11 @@ cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   if (N <= 0) return cudaSuccess;
   auto tiles = [&](int bm, int bn) { return ((a.M + bm - 1) / bm) * ((N + bn - 1) / bn); };
+  if (a.M <= 32 && a.Kt <= 64 && a.cin % 4 == 0) {
+    dim3 grid((unsigned)((N + 127) / 128));
+    if (a.M <= 16) return launch_pdl(k_conv_small_f32<16>, grid, dim3(128), 0, st, a);
+    return launch_pdl(k_conv_small_f32<32>, grid, dim3(128), 0, st, a);
+  }
   if (a.cin % 8 == 0 && a.M >= 128 && tiles(128, 128) >= 2 * 152) {
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((a.M + 127) / 128));
     return launch_pdl(k_conv_tile_f32<128, 128, 8>, grid, dim3(256), 0, st, a);
@@ -472,7 +547,7 @@ cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_heads(const HeadsArgs& a, cudaStream_t st) {
-  const int64_t total = (int64_t)a.batch.count * a.ncols * a.bands;
+  const int64_t total = (int64_t)a.batch.count * a.ncols;
   if (total <= 0) return cudaSuccess;
   return launch_pdl(k_heads, dim3(elementwise_grid(total)), dim3(256), 0, st, a);
 }

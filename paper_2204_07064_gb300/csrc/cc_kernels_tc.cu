@@ -26,6 +26,13 @@
 //              (16-byte loads) and stores every view with 16-byte stores, at
 //              ring addresses from a per-column table built before the
 //              kernel waits on its predecessor
+// Split-K (layers with few tiles and long K): the ksplit CTAs of a cluster
+// along z share one tile; CTA z accumulates an equal share of the K slices,
+// writes its partial accumulator to its own shared memory, and after a
+// cluster barrier finishes columns [z, z+1) * BN/ksplit by summing the
+// partials of all CTAs of the cluster (distributed shared memory, fixed order
+// z = 0, 1, ...).  The split is a property of the layer, so a stream's result
+// does not depend on the batch it runs in.
 // Every mbarrier wait is bounded in time and records an error in the model's
 // device error word instead of hanging.
 //
@@ -99,6 +106,9 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   const int nk = a.Kt / 64;
   const int cchunks = a.cin / 64;
+  const int KS = (int)gridDim.z, zr = (int)blockIdx.z;  // split-K (cluster along z)
+  const int kb = zr * nk / KS, ke = (zr + 1) * nk / KS;  // this CTA's K slices
+  const int c_n = BN / KS, c_lo = zr * c_n;              // columns this CTA finishes
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -121,12 +131,13 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
     // The weight tiles of the first stages are requested before anything else.
-    const int pre = nk < kStages ? nk : kStages;
-    const uint8_t* atile = static_cast<const uint8_t*>(a.A_tiled) + (size_t)blockIdx.y * nk * L::kA;
+    const int nks = ke - kb;
+    const int pre = nks < kStages ? nks : kStages;
+    const uint8_t* atile = static_cast<const uint8_t*>(a.A_tiled) + ((size_t)blockIdx.y * nk + kb) * L::kA;
     if (lane == 0)
-      for (int kc = 0; kc < pre; ++kc) {
-        mbar_arrive_expect_tx(full + kc, L::kA + L::kB);
-        bulk_load(sA + kc * L::kA, atile + (size_t)kc * L::kA, L::kA, full + kc);
+      for (int i = 0; i < pre; ++i) {
+        mbar_arrive_expect_tx(full + i, L::kA + L::kB);
+        bulk_load(sA + i * L::kA, atile + (size_t)i * L::kA, L::kA, full + i);
       }
     constexpr int G = BN / 128;
     // Box form: the streams of the tile sit in consecutive slots at one step p,
@@ -175,18 +186,19 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     pdl_release();
     bool ok = true;
     int issued = 0;
-    for (int kc = 0; kc < nk; ++kc) {
-      const int st = kc % kStages;
-      const uint32_t ph = (kc / kStages) & 1;
+    for (int i = 0; i < nks; ++i) {
+      const int kc = kb + i;
+      const int st = i % kStages;
+      const uint32_t ph = (i / kStages) & 1;
       if (!mbar_wait(empty + st, ph ^ 1, kWaitNs)) {
         ok = false;
         break;
       }
       const int tap = kc / cchunks;
       const int c0 = (kc - tap * cchunks) * 64;
-      if (lane == 0 && kc >= pre) {
+      if (lane == 0 && i >= pre) {
         mbar_arrive_expect_tx(full + st, L::kA + L::kB);
-        bulk_load(sA + st * L::kA, atile + (size_t)kc * L::kA, L::kA, full + st);
+        bulk_load(sA + st * L::kA, atile + (size_t)i * L::kA, L::kA, full + st);
       }
       __syncwarp();
       uint8_t* dst = sB + st * L::kB;
@@ -204,13 +216,17 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
           tma_gather4(dst + (lane + 32 * g) * 512, &tmB, full + st, c0, y[0], y[1], y[2], y[3]);
         }
       }
-      issued = kc + 1;
+      issued = i + 1;
     }
     if (!ok) {
       if (lane == 0) atomicOr(a.err, 1);
       // let the copies already issued land before the CTA's shared memory goes away
-      for (int kc = issued - kStages < 0 ? 0 : issued - kStages; kc < issued; ++kc)
-        mbar_wait(full + kc % kStages, (kc / kStages) & 1, kWaitNs);
+      for (int i = issued - kStages < 0 ? 0 : issued - kStages; i < issued; ++i)
+        mbar_wait(full + i % kStages, (i / kStages) & 1, kWaitNs);
+    }
+    if (KS > 1) {  // the epilogue's two cluster barriers
+      cluster_sync();
+      cluster_sync();
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
@@ -219,9 +235,9 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     if (lane == 0) {
       const uint32_t idesc = idesc_f16(kBM, BN, a.in.dtype == kDtBF16);
       bool ok = true;
-      for (int kc = 0; kc < nk; ++kc) {
-        const int st = kc % kStages;
-        const uint32_t ph = (kc / kStages) & 1;
+      for (int i = 0; i < ke - kb; ++i) {
+        const int st = i % kStages;
+        const uint32_t ph = (i / kStages) & 1;
         if (!mbar_wait(full + st, ph, kWaitNs)) {
           ok = false;
           break;
@@ -231,11 +247,16 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
 #pragma unroll
         for (int k = 0; k < 4; ++k)
           mma_f16(tmem, sw128_kmajor_desc(sa + k * 32), sw128_kmajor_desc(sb + k * 32), idesc,
-                  (kc | k) != 0);
+                  (i | k) != 0);
         mma_commit(empty + st);
       }
       mma_commit(tfull);
       if (!ok) atomicOr(a.err, 4);
+    }
+    __syncwarp();
+    if (KS > 1) {  // the epilogue's two cluster barriers
+      cluster_sync();
+      cluster_sync();
     }
   } else {
     // ---------------------------------------------------------------- epilogue
@@ -295,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     char* const sk_base = arena + (int64_t)ch_l * 4;
     // residual rows of the tile: every 128-byte line into L2 ahead of use
     auto prefetch_skip = [&]() {
-      for (int c = t; c < BN; c += kEpi) {
+      for (int c = c_lo + t; c < c_lo + c_n; c += kEpi) {
         if (n0 + c >= N) break;
         for (int k = 0; k < kBM; k += 32) {
           const int32_t mm = m0 + k;
@@ -324,18 +345,18 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     uint32_t so_next = 0;
     int32_t sr_next = 0;
     if (a.has_skip) {
-      so_next = col_off[3 * BN + lane];
-      sr_next = col_row[3 * BN + lane];
+      so_next = col_off[3 * BN + c_lo + lane];
+      sr_next = col_row[3 * BN + c_lo + lane];
     }
     if (a.has_skip && a.skip_early) {
       prefetch_skip();
-      load_skip(0, half, so_next, sr_next);
+      load_skip(c_lo, half, so_next, sr_next);
     }
     pdl_wait();
     pdl_release();
     if (a.has_skip && !a.skip_early) {
       prefetch_skip();
-      load_skip(0, half, so_next, sr_next);
+      load_skip(c_lo, half, so_next, sr_next);
     }
     // one verdict for all epilogue threads (a reduction barrier), so the
     // named barriers stay matched
@@ -350,6 +371,24 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
         : "r"((uint32_t)waited)
         : "memory");
     tc_fence_after();
+    // split-K: partial accumulator [BN columns][128 rows] FP32 into the free
+    // pipeline buffers, then the cluster's partials are complete
+    float* const part = reinterpret_cast<float*>(sA);
+    uint32_t part_at[4] = {0, 0, 0, 0};  // the partial buffers of the cluster's CTAs
+    if (KS > 1) {
+      if (all_ok)
+#pragma unroll 1
+        for (int g = half; g < BN / 8; g += 2) {
+          uint32_t r[8];
+          tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(8 * g), r);
+          tmem_ld_wait();
+#pragma unroll
+          for (int k = 0; k < 8; ++k) part[(8 * g + k) * kBM + sub * 32 + lane] = __uint_as_float(r[k]);
+        }
+#pragma unroll
+      for (int z = 0; z < 4; ++z) part_at[z] = z < KS ? dsmem_map(smem_u32(part), z) : 0u;
+      cluster_sync();
+    }
     if (!all_ok) {
       if (t == 0) atomicOr(a.err, 2);
     } else {
@@ -373,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
         return *reinterpret_cast<const uint32_t*>(&h);
       };
 #pragma unroll 1
-      for (int cb = 0; cb < BN; cb += 32) {
+      for (int cb = c_lo; cb < c_lo + c_n; cb += 32) {
         if (n0 + cb >= N) break;  // uniform over the CTA
         const int cl = cb + lane;
         const int64_t eb = col_ext[cl];
@@ -382,7 +421,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
         const int32_t fr = col_row[cl], lr0 = col_row[BN + cl], lr1 = col_row[2 * BN + cl];
         const uint32_t so_cur = so_next;
         const int32_t sr_cur = sr_next;
-        if (has_skip && cb + 32 < BN) {
+        if (has_skip && cb + 32 < c_lo + c_n) {
           so_next = col_off[3 * BN + cl + 32];
           sr_next = col_row[3 * BN + cl + 32];
         }
@@ -390,8 +429,20 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
         for (int g = half; g < 4; g += 2) {
           if (n0 + cb + 8 * g >= N) break;  // uniform
           uint32_t r[8];
-          tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(cb + 8 * g), r);
-          tmem_ld_wait();
+          if (KS == 1) {
+            tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(cb + 8 * g), r);
+            tmem_ld_wait();
+          } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const uint32_t off = (uint32_t)(((cb + 8 * g + k) * kBM + sub * 32 + lane) * 4);
+              float acc = 0.f;
+#pragma unroll
+              for (int z = 0; z < 4; ++z)
+                if (z < KS) acc += dsmem_ld_f32(part_at[z] + off);
+              r[k] = __float_as_uint(acc);
+            }
+          }
           // turn: row-per-lane values in, 8-channel column slices out
           __syncwarp();
 #pragma unroll
@@ -406,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
             // the next group's residual loads overlap this group's stores
             if (g + 2 < 4)
               load_skip(cb, g + 2, so_cur, sr_cur);
-            else if (cb + 32 < BN && n0 + cb + 32 < N)
+            else if (cb + 32 < c_lo + c_n && n0 + cb + 32 < N)
               load_skip(cb + 32, half, so_next, sr_next);
           }
           const int src = 8 * g + kk;  // table lane of this lane's column
@@ -452,6 +503,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
         }
       }
     }
+    if (KS > 1) cluster_sync();  // the cluster's partials are read: buffers may go
   }
   tc_fence_before();
   __syncthreads();
@@ -460,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
 }
 
 template <int BN, int STAGES>
-cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, cudaStream_t st) {
+cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int ks, cudaStream_t st) {
   static bool configured = false;
   constexpr int bytes = TcLayout<BN, STAGES>::kBytes;
   if (!configured) {
@@ -471,8 +523,22 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs
   }
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   const int mtiles = (a.M + kBM - 1) / kBM;
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)mtiles);
-  return launch_pdl(k_conv_tc<BN, STAGES>, grid, dim3(kThreads), (size_t)bytes, st, ta, tb, a);
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)mtiles, (unsigned)ks);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = (size_t)bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = 1;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = (unsigned)ks;
+  cfg.attrs = attr;
+  cfg.numAttrs = ks > 1 ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, k_conv_tc<BN, STAGES>, ta, tb, a);
 }
 
 }  // namespace
@@ -487,10 +553,11 @@ cudaError_t launch_conv_tc(const void* tmap_t, const void* tmap_b, const TcArgs&
   if (N <= 0) return cudaSuccess;
   const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(tmap_t);
   const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(tmap_b);
-  if (bn == 256) return launch_bn<256, 4>(ta, tb, a, st);
-  const int64_t ctas = (N + 127) / 128 * ((a.M + kBM - 1) / kBM);
-  if (ctas <= 148) return launch_bn<128, 6>(ta, tb, a, st);
-  return launch_bn<128, 3>(ta, tb, a, st);
+  const int ks = a.ksplit > 1 ? a.ksplit : 1;
+  if (bn == 256 && ks == 1) return launch_bn<256, 4>(ta, tb, a, 1, st);
+  const int64_t ctas = (N + 127) / 128 * ((a.M + kBM - 1) / kBM) * ks;
+  if (ctas <= 148) return launch_bn<128, 6>(ta, tb, a, ks, st);
+  return launch_bn<128, 3>(ta, tb, a, ks, st);
 }
 
 }  // namespace cc

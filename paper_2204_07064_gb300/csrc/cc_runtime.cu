@@ -409,6 +409,14 @@ static cc_status pack_and_upload(Model& m, const float* const* weights, const fl
     if (p.engine == 1) {
       cc_status s = upload_tc_operand(m, p, A);
       if (s) return s;
+      // Split-K for layers whose tiles at full capacity (max_streams, one
+      // step) fill few SMs and whose K is long: clusters of 4 or 2 CTAs share
+      // a tile.  Chosen from the layer and the capacity only, so that every
+      // batch runs the same arithmetic.
+      const int nk = p.Kt / 64, mt = p.Mpad / 128;
+      const int64_t cols = (int64_t)m.max_streams * (d.op == CC_OP_CONVT ? m.nodes[d.inputs[0]].u : p.u);
+      const int64_t ctas = (cols + 127) / 128 * mt;
+      p.ksplit = (ctas * 4 <= 148 && nk >= 8) ? 4 : (ctas * 2 <= 148 && nk >= 4) ? 2 : 1;
     } else {
       CC_CUDA(cudaMalloc(&p.dA, A.size() * sizeof(float)));
       CC_CUDA(cudaMemcpy(p.dA, A.data(), A.size() * sizeof(float), cudaMemcpyHostToDevice));
@@ -531,6 +539,7 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
           if (!p.tmapT_ok[li]) li = -1;
         }
         a.box_ok = li >= 0;
+        a.ksplit = p.ksplit;
         const int bn = tile_n_for(p, (int64_t)batch.count * ncols);
         CC_CUDA(launch_conv_tc(li >= 0 ? p.tmapT[li] : p.tmapB, p.tmapB, a, bn, st));
       } else {

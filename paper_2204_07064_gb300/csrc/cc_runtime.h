@@ -50,6 +50,7 @@ struct NodePlan {
   alignas(64) unsigned char tmapT[8][128] = {};
   bool tmapT_ok[8] = {};
   int32_t in_rows_per_slot = 0, in_row_off = 0;
+  int32_t ksplit = 1;  // tensor-core split-K factor, fixed per layer (batch-independent numerics)
   std::map<int64_t, int32_t> tile_n;  // autotuned N tile by launch width (columns), 0: heuristic
 };
 

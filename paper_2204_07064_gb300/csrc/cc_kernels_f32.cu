@@ -373,21 +373,29 @@ __global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
   const float* col = ring_ptr<const float>(a.batch, s, a.in);
   const int32_t r0 =
       (int32_t)ring_row(steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist, a.in.rows);
+  // the whole window (taps x cin <= 64 values) is requested before any use
+  float xw[64];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int32_t k = 4 * q;
+    float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < a.Kt) {
+      const int32_t tap = k / a.cin, c = k - tap * a.cin;
+      v4 = *reinterpret_cast<const float4*>(col + (int64_t)wrap_row(r0 + tap * a.dil, a.in.rows) * a.cin + c);
+    }
+    xw[k] = activate(v4.x, a.act);
+    xw[k + 1] = activate(v4.y, a.act);
+    xw[k + 2] = activate(v4.z, a.act);
+    xw[k + 3] = activate(v4.w, a.act);
+  }
   float acc[TM];
 #pragma unroll
   for (int m = 0; m < TM; ++m) acc[m] = 0.f;
-  for (int32_t tap = 0; tap < a.taps; ++tap) {
-    const float* x = col + (int64_t)wrap_row(r0 + tap * a.dil, a.in.rows) * a.cin;
-    const float* w = As + tap * a.cin;
-    for (int32_t c = 0; c < a.cin; c += 4) {
-      const float4 v4 = *reinterpret_cast<const float4*>(x + c);
-      const float v[4] = {activate(v4.x, a.act), activate(v4.y, a.act), activate(v4.z, a.act),
-                          activate(v4.w, a.act)};
 #pragma unroll
-      for (int m = 0; m < TM; ++m)
+  for (int k = 0; k < 64; ++k) {
+    if (k >= a.Kt) break;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[m] = fmaf(w[m * a.Kt + c + q], v[q], acc[m]);
-    }
+    for (int m = 0; m < TM; ++m) acc[m] = fmaf(As[m * a.Kt + k], xw[k], acc[m]);
   }
   // an output that is only the caller's buffer with the TM rows contiguous
   // there (one phase per row of one channel, or channels of one phase):
@@ -432,8 +440,8 @@ __device__ __forceinline__ float noise_uniform(uint64_t seed, int64_t frame, int
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 // One thread per (stream, frame): the ring rows of the three branches and of
-// every output view are computed once, then all bands (4 at a time when the
-// band count allows).
+// every output view are computed once; bands go 16 at a time, the 48 branch
+// values of a block of 16 requested before any use.
 __global__ void k_heads(const HeadsArgs a) {
   pdl_wait();
   pdl_release();
@@ -456,13 +464,23 @@ __global__ void k_heads(const HeadsArgs a) {
     float* fo = a.out.f32.rows ? reinterpret_cast<float*>(base + a.out.f32.off) + (int64_t)rf * a.out.f32.chans
                                : nullptr;
     float* eo = a.out.ext ? a.out.ext + (int64_t)s * a.out.ext_stride + (int64_t)j * a.bands : nullptr;
-    for (int32_t b = 0; b < a.bands; ++b) {
-      float y = tanhf(in[0][b]) * sigmoidf_(in[1][b]);
-      if (a.noise) y += sigmoidf_(in[2][b]) * noise_uniform(seed, t - a.delay, b, a.bands);
-      if (fo) fo[b] = y;
-      if (eo) eo[b] = y;
-      if (a.out.lp[0].rows) store_lp(base, a.out.lp[0], r0, b, y);
-      if (a.out.lp[1].rows) store_lp(base, a.out.lp[1], r1, b, leaky(y));
+    for (int32_t b0 = 0; b0 < a.bands; b0 += 16) {
+      float v[3][16];
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[q][k] = b0 + k < a.bands ? in[q][b0 + k] : 0.f;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int32_t b = b0 + k;
+        if (b >= a.bands) break;
+        float y = tanhf(v[0][k]) * sigmoidf_(v[1][k]);
+        if (a.noise) y += sigmoidf_(v[2][k]) * noise_uniform(seed, t - a.delay, b, a.bands);
+        if (fo) fo[b] = y;
+        if (eo) eo[b] = y;
+        if (a.out.lp[0].rows) store_lp(base, a.out.lp[0], r0, b, y);
+        if (a.out.lp[1].rows) store_lp(base, a.out.lp[1], r1, b, leaky(y));
+      }
     }
   }
 }

@@ -36,6 +36,11 @@ FP32_LANES_PER_SM = 128
 def default_sub_batches(dtype, streams):
     return 1 if dtype == "f32" else max(1, streams // 256)
 
+# DRAM bytes (read + write) per tensor-core launch, from one ncu capture of
+# the 32 contractions of a step of this exact workload and kernel version
+# (profiles/k_conv_tc_decoder_bf16_b256.md); null for any other workload.
+TC_TRAFFIC_PER_LAUNCH = {"decoder-bf16-b256": 6.04e6}
+
 WORKLOADS = {
     # name: (dtype, streams, buffer latent frames)
     "decoder-bf16-b256": ("bf16", 256, 1),
@@ -77,6 +82,74 @@ def build_decoder(dtype, streams, seed=1):
     params[W.pqmf_node_index(nodes)] = (api.inverse_pqmf_weights(g), None)
     model = api.Model(nodes, params, dtype=dtype, max_streams=streams, max_steps_per_call=1)
     return nodes, params, model
+
+
+def run_differentiate(args):
+    """Differentiation form: the encoder + decoder (audio -> audio, FP32),
+    --diff-streams streams of --diff-chunks 2048-sample chunks of N(0, 0.1^2)
+    audio, streamed through torch.autograd with one device checkpoint per chunk,
+    then the hand-written chunked backward (loss = sum(r * y), r seeded).
+    Reports audio seconds differentiated per second (forward + backward, CUDA
+    events) and the checkpoint memory."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2204_07064_gb300 import api
+    from paper_2204_07064_gb300 import autograd as AG
+    from paper_2204_07064_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    enc = W.rave_encoder()
+    dec = W.rave_decoder()
+    nodes = W.chain(enc, dec)
+    params = W.init_params(nodes, 4)
+    _, g, _ = api.pqmf_design(16, 64, 5.0)
+    for i, nd in enumerate(nodes):
+        if nd["name"] == "pqmf":
+            params[i] = (api.pqmf_analysis_weights(g), None)
+        if nd["name"] == "ipqmf":
+            params[i] = (api.inverse_pqmf_weights(g), None)
+    count, chunks = args.diff_streams, args.diff_chunks
+    model = api.Model(nodes, params, dtype="f32", max_streams=count, max_steps_per_call=1)
+    streams = [model.stream(seed=s) for s in W.stream_seeds(4, count)]
+    runner = AG.StreamedRunner(model, params, streams, 1)
+    n = chunks * 2048
+    rng = np.random.default_rng(4)
+    x = torch.tensor(rng.standard_normal((count, n, 1)) * 0.1, dtype=torch.float32, device=dev, requires_grad=True)
+    r = torch.tensor(rng.standard_normal((count, n, 1)), dtype=torch.float32, device=dev)
+
+    def once():
+        x.grad = None
+        runner.grads.zero()
+        y = AG.streamed(x, runner)
+        (y * r).sum().backward()
+
+    for _ in range(max(1, args.warmup // 3)):
+        once()
+    torch.cuda.synchronize()
+    model.device_status()
+    reps = max(1, args.steps // 10)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    model.device_status()
+    ms = e0.elapsed_time(e1) / reps
+    audio_s = count * n / SR
+    ckpt_bytes = (chunks + 1) * count * api.snapshot_bytes(model)
+    print(json.dumps({
+        "metric": "streamed forward + backward, audio seconds per second", "value": audio_s / (ms / 1000.0),
+        "unit": "audio s / s", "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "ms_per_pass": ms, "repeats": reps,
+        "config": {"workload": f"autoencoder-f32-diff-{count}x{chunks}", "streams": count, "chunks": chunks,
+                   "chunk_samples": 2048, "checkpoint_bytes": ckpt_bytes,
+                   "loss": "sum(r * y), r ~ N(0,1) seeded"}}))
+    model.close()
 
 
 class ClockSampler:
@@ -353,6 +426,10 @@ def main():
     ap.add_argument("--serve-warmup", type=float, default=10.0)
     ap.add_argument("--serve-cap", type=int, default=2048)
     ap.add_argument("--serve-fixed", type=int, default=0, help="N fixed streams of 2048-sample buffers")
+    ap.add_argument("--differentiate", action="store_true",
+                    help="time the streamed forward + hand-written backward of the encoder + decoder")
+    ap.add_argument("--diff-streams", type=int, default=32)
+    ap.add_argument("--diff-chunks", type=int, default=32)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -360,6 +437,8 @@ def main():
         return run_reference(args)
     if args.serving:
         return run_serving(args)
+    if args.differentiate:
+        return run_differentiate(args)
 
     import torch
 
@@ -513,7 +592,7 @@ def main():
     else:
         peak = pk.get("bf16_tflops", 1900.0)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": TC_TRAFFIC_PER_LAUNCH.get(args.workload),
                 "kernel": "tcgen05 implicit-GEMM contractions", "peak_source": f"bf16 burst, {pk_kind}"}
     roof["share_of_step"] = conv_ms / sum(node_ms) if sum(node_ms) else None
     roof["launches"] = conv_launches

@@ -92,7 +92,14 @@ typedef struct {
   int32_t max_steps_per_call; /* model steps one launch chain covers (longer buffers are
                                  split); sizes the per-slot scratch rows              */
   int32_t noise;              /* 1: heads add sigmoid(in2)*u; 0: u = 0 (section 4.2)  */
+  int32_t flags;              /* CC_FLAG_* bits (0: defaults)                          */
 } cc_model_config;
+
+/* cc_model_config.flags: launch each convolution of a residual unit on its own
+ * (the tensor-core path otherwise runs a k-wide conv and the 1x1 conv that
+ * consumes only it as one launch, the intermediate kept on chip; the results
+ * are identical). */
+#define CC_FLAG_NO_UNIT_FUSION 1
 
 typedef struct cc_model cc_model;
 typedef struct cc_stream cc_stream;

@@ -40,7 +40,7 @@ class NodeDesc(C.Structure):
 
 class ModelConfig(C.Structure):
     _fields_ = [("compute", C.c_int32), ("max_streams", C.c_int32),
-                ("max_steps_per_call", C.c_int32), ("noise", C.c_int32)]
+                ("max_steps_per_call", C.c_int32), ("noise", C.c_int32), ("flags", C.c_int32)]
 
 
 _LIB = None
@@ -151,7 +151,8 @@ def _desc(node):
 class Model:
     """A reconfigured model on the GPU: packed weights + stream-state arena."""
 
-    def __init__(self, nodes, params, dtype="f32", max_streams=1, max_steps_per_call=1, noise=True):
+    def __init__(self, nodes, params, dtype="f32", max_streams=1, max_steps_per_call=1, noise=True,
+                 fuse_units=True):
         L = lib()
         n = len(nodes)
         descs = (NodeDesc * n)(*[_desc(nd) for nd in nodes])
@@ -168,7 +169,8 @@ class Model:
                     b32 = np.ascontiguousarray(b, dtype=np.float32)
                     self._keep.append(b32)
                     bp[i] = b32.ctypes.data
-        cfg = ModelConfig(DTYPES[dtype], max_streams, max_steps_per_call, int(bool(noise)))
+        cfg = ModelConfig(DTYPES[dtype], max_streams, max_steps_per_call, int(bool(noise)),
+                          0 if fuse_units else 1)
         h = _P()
         _check(L.cc_model_create(descs, n, wp, bp, C.byref(cfg), C.byref(h)))
         self._keep = None

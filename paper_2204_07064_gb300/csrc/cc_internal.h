@@ -97,6 +97,14 @@ struct TcArgs {
   int32_t has_skip, skip_A;
   int32_t skip_early;  // the residual's producer launched two or more launches back
   int32_t ksplit;      // split-K factor (1, 2 or 4): CTAs per cluster sharing a tile
+  // Residual-unit fusion (k2 > 0): the tile's result, scaled, biased and
+  // activated (act2) in BF16/FP16, is the B operand of a second, 1x1
+  // contraction A2 [M][k2*64] (pre-tiled like A) whose result, with scale2,
+  // bias2, the residual and the views above, is the launch's output.
+  const void* A2_tiled;
+  const float* scale2;
+  const float* bias2;
+  int32_t k2, act2;
   Ring skip;
   Batch batch;
   int32_t* err;  // device error word: set when a bounded wait gives up

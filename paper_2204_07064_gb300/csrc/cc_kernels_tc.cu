@@ -26,6 +26,14 @@
 //              (16-byte loads) and stores every view with 16-byte stores, at
 //              ring addresses from a per-column table built before the
 //              kernel waits on its predecessor
+// Residual-unit fusion (FUSE): a k-wide conv and the 1x1 conv that consumes
+// only it run as one launch.  The first epilogue writes the scaled, biased,
+// activated first result in BF16/FP16 straight into shared memory in the
+// swizzled K-major operand layout; the MMA warp then runs the 1x1 contraction
+// (its weights streamed through the same pipeline) into a second TMEM
+// accumulator, and the second epilogue is the ordinary one.  The rounding of
+// the intermediate is the one the unfused path applies when it stores it, so
+// the results are identical.
 // Split-K (layers with few tiles and long K): the ksplit CTAs of a cluster
 // along z share one tile; CTA z accumulates an equal share of the K slices,
 // writes its partial accumulator to its own shared memory, and after a
@@ -63,7 +71,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 // (one CTA per SM: few CTAs with long K loops need deep prefetch), else 3
 // stages (two CTAs per SM, whose epilogues overlap each other's main loops);
 // 256-column tiles use 4 stages.
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool FUSE>
 struct TcLayout {
   static constexpr int kStages = STAGES;
   static constexpr int kA = kBM * 128;  // one 128 x 64 low-precision tile
@@ -74,25 +82,40 @@ struct TcLayout {
   // the mirror row's offset (low-precision views); the caller-buffer offset
   static constexpr int kCols = BN * (4 * 4 + 4 * 4 + 2 * 4 + 8);
   static constexpr int kTurn = 8 * 32 * 8 * 4;  // per epilogue warp: 32 rows x 8 columns of FP32
-  static constexpr int kBytes = 1024 + kStages * (kA + kB) + kBars + kCols + kTurn + 64;
-  static constexpr int kMinBlocks = STAGES == 3 ? 2 : 1;
+  static constexpr int kB2 = FUSE ? 2 * BN * 128 : 0;  // fused unit: BN x 128 channels, 2 K slices
+  static constexpr int kBars2 = FUSE ? 16 : 0;          // b2ready, tfull2
+  static constexpr int kBytes = 1024 + kStages * (kA + kB) + kB2 + kBars + kBars2 + kCols + kTurn + 64;
+  static constexpr int kMinBlocks = (STAGES == 3 || FUSE) ? 2 : 1;
+  static constexpr int kTmemCols = FUSE ? 2 * BN : BN;
 };
 
-template <int BN, int STAGES>
-__global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
+__device__ __forceinline__ uint32_t pack2(float lo, float hi, bool bf16) {
+  if (bf16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+template <int BN, int STAGES, bool FUSE>
+__global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBlocks)
     k_conv_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmB,
               const TcArgs a) {
-  using L = TcLayout<BN, STAGES>;
+  using L = TcLayout<BN, STAGES, FUSE>;
   constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + kStages * L::kA;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * L::kB);
+  uint8_t* sB2 = sB + kStages * L::kB;  // fused unit: second operand (1024-aligned)
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB2 + L::kB2);
   uint64_t* empty = full + kStages;
   uint64_t* tfull = empty + kStages;
-  uint32_t* tbase = reinterpret_cast<uint32_t*>(tfull + 1);
+  uint64_t* b2ready = tfull + 1;  // fused unit (FUSE only)
+  uint64_t* tfull2 = tfull + 2;
+  uint32_t* tbase = reinterpret_cast<uint32_t*>(tfull + 1 + (FUSE ? 2 : 0));
   int64_t* col_ext = reinterpret_cast<int64_t*>(tbase + 2);   // [BN]
   uint32_t* col_off = reinterpret_cast<uint32_t*>(col_ext + BN);  // [4][BN], 16-byte units
   int32_t* col_row = reinterpret_cast<int32_t*>(col_off + 4 * BN);  // [4][BN]
@@ -116,11 +139,15 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
       mbar_init(empty + s, 1);
     }
     mbar_init(tfull, 1);
+    if (FUSE) {
+      mbar_init(b2ready, 1);
+      mbar_init(tfull2, 1);
+    }
     fence_mbar_init();
     prefetch_tmap(a.box_ok ? &tmT : &tmB);
   }
   if (warp == 1) {
-    tmem_alloc(tbase, BN);
+    tmem_alloc(tbase, L::kTmemCols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -218,6 +245,25 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
       }
       issued = i + 1;
     }
+    if (FUSE && ok) {
+      // fused unit: the 1x1 conv's weight slices through the same stages
+      const uint8_t* a2tile = static_cast<const uint8_t*>(a.A2_tiled);
+      for (int j = 0; j < a.k2; ++j) {
+        const int i = nks + j;
+        const int st = i % kStages;
+        const uint32_t ph = (i / kStages) & 1;
+        if (!mbar_wait(empty + st, ph ^ 1, kWaitNs)) {
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          mbar_arrive_expect_tx(full + st, L::kA);
+          bulk_load(sA + st * L::kA, a2tile + (size_t)j * L::kA, L::kA, full + st);
+        }
+        __syncwarp();
+        issued = i + 1;
+      }
+    }
     if (!ok) {
       if (lane == 0) atomicOr(a.err, 1);
       // let the copies already issued land before the CTA's shared memory goes away
@@ -251,6 +297,30 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
         mma_commit(empty + st);
       }
       mma_commit(tfull);
+      if (FUSE) {
+        // fused unit: wait for the first epilogue's operand, then the 1x1 conv
+        // into the second accumulator (TMEM columns BN .. 2*BN-1)
+        ok = ok && mbar_wait(b2ready, 0, kWaitNs);
+        tc_fence_after();
+        const int nks = ke - kb;
+        for (int j = 0; ok && j < a.k2; ++j) {
+          const int i = nks + j;
+          const int st = i % kStages;
+          const uint32_t ph = (i / kStages) & 1;
+          if (!mbar_wait(full + st, ph, kWaitNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(sA + st * L::kA), sb = smem_u32(sB2 + j * BN * 128);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            mma_f16(tmem + BN, sw128_kmajor_desc(sa + k * 32), sw128_kmajor_desc(sb + k * 32), idesc,
+                    (j | k) != 0);
+          mma_commit(empty + st);
+        }
+        mma_commit(tfull2);
+      }
       if (!ok) atomicOr(a.err, 4);
     }
     __syncwarp();
@@ -267,8 +337,11 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
     const bool mok = m < a.M;
     const int32_t ph = (mok && a.phases > 1) ? m / a.cout : 0;  // transposed conv: phase
     const int32_t ch = mok ? m - ph * a.cout : 0;                // output channel
-    const float sc = mok ? a.scale[m] : 0.f;
-    const float bi = (mok && a.bias) ? a.bias[ch] : 0.f;
+    const float sc1 = mok ? a.scale[m] : 0.f;
+    const float bi1 = (mok && a.bias) ? a.bias[ch] : 0.f;
+    // the stored result's scale and bias (the fused unit's second conv)
+    const float sc = !FUSE ? sc1 : mok ? a.scale2[m] : 0.f;
+    const float bi = !FUSE ? bi1 : (mok && a.bias2) ? a.bias2[ch] : 0.f;
     // Column table (pre-wait): per view, the 16-byte-unit arena offset of the
     // ring row holding the column's first frame and that row; for a
     // low-precision view also the offset of its mirror row (~0u if the row is
@@ -371,6 +444,53 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
         : "r"((uint32_t)waited)
         : "memory");
     tc_fence_after();
+    uint32_t acc_col = 0;  // TMEM column of the stored result's accumulator
+    if (FUSE) {
+      // fused unit, first epilogue: the k-wide conv's result, scaled, biased,
+      // activated and rounded, into the 1x1 conv's K-major operand (row =
+      // column of the tile, 128-byte-swizzled rows, 64 channels per K slice)
+      const bool lp_bf16 = a.in.dtype == kDtBF16;
+      if (all_ok)
+#pragma unroll 1
+        for (int g = half; g < BN / 8; g += 2) {
+          uint32_t r[8];
+          tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(8 * g), r);
+          tmem_ld_wait();
+          __syncwarp();
+#pragma unroll
+          for (int k = 0; k < 8; ++k) tw[k * 32 + lane] = fmaf(__uint_as_float(r[k]), sc1, bi1);
+          __syncwarp();
+          const float4 v0 = *reinterpret_cast<const float4*>(tw + kk * 32 + 8 * (lane & 3));
+          const float4 v1 = *reinterpret_cast<const float4*>(tw + kk * 32 + 8 * (lane & 3) + 4);
+          float y[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+          if (a.act2)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) y[i] = leaky(y[i]);
+          const uint4 pk = make_uint4(pack2(y[0], y[1], lp_bf16), pack2(y[2], y[3], lp_bf16),
+                                      pack2(y[4], y[5], lp_bf16), pack2(y[6], y[7], lp_bf16));
+          if (vok) {
+            const int c = 8 * g + kk;
+            const int chunk = (ch_l & 63) >> 3;
+            *reinterpret_cast<uint4*>(sB2 + (ch_l >> 6) * (BN * 128) + c * 128 + ((chunk ^ (c & 7)) << 4)) = pk;
+          }
+        }
+      fence_proxy_async_smem();  // the operand is read by the tensor cores (async proxy)
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (t == 0) mbar_arrive(b2ready);
+      const bool waited2 = mbar_wait(tfull2, 0, kWaitNs);
+      uint32_t ok2;
+      asm volatile(
+          "{\n\t.reg .pred p, q;\n\t"
+          "setp.ne.u32 q, %1, 0;\n\t"
+          "bar.red.and.pred p, 1, 256, q;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(ok2)
+          : "r"((uint32_t)waited2)
+          : "memory");
+      tc_fence_after();
+      all_ok = all_ok && ok2;
+      acc_col = BN;
+    }
     // split-K: partial accumulator [BN columns][128 rows] FP32 into the free
     // pipeline buffers, then the cluster's partials are complete
     float* const part = reinterpret_cast<float*>(sA);
@@ -430,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
           if (n0 + cb + 8 * g >= N) break;  // uniform
           uint32_t r[8];
           if (KS == 1) {
-            tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(cb + 8 * g), r);
+            tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + acc_col + (uint32_t)(cb + 8 * g), r);
             tmem_ld_wait();
           } else {
 #pragma unroll
@@ -508,16 +628,16 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES>::kMinBlocks)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1) tmem_dealloc(tmem, BN);
+  if (warp == 1) tmem_dealloc(tmem, L::kTmemCols);
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool FUSE = false>
 cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int ks, cudaStream_t st) {
   static bool configured = false;
-  constexpr int bytes = TcLayout<BN, STAGES>::kBytes;
+  constexpr int bytes = TcLayout<BN, STAGES, FUSE>::kBytes;
   if (!configured) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_conv_tc<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k_conv_tc<BN, STAGES, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -538,7 +658,7 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs
   attr[1].val.clusterDim.z = (unsigned)ks;
   cfg.attrs = attr;
   cfg.numAttrs = ks > 1 ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, k_conv_tc<BN, STAGES>, ta, tb, a);
+  return cudaLaunchKernelEx(&cfg, k_conv_tc<BN, STAGES, FUSE>, ta, tb, a);
 }
 
 }  // namespace
@@ -554,6 +674,11 @@ cudaError_t launch_conv_tc(const void* tmap_t, const void* tmap_b, const TcArgs&
   const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(tmap_t);
   const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(tmap_b);
   const int ks = a.ksplit > 1 ? a.ksplit : 1;
+  if (a.k2 > 0) {
+    // fused residual unit: 128-column tiles, no split, one M tile (M <= 128)
+    if (ks != 1 || a.M > kBM || a.k2 > 2) return cudaErrorInvalidValue;
+    return launch_bn<128, 2, true>(ta, tb, a, 1, st);
+  }
   if (bn == 256 && ks == 1) return launch_bn<256, 4>(ta, tb, a, 1, st);
   const int64_t ctas = (N + 127) / 128 * ((a.M + kBM - 1) / kBM) * ks;
   if (ctas <= 148) return launch_bn<128, 6>(ta, tb, a, ks, st);

@@ -187,6 +187,44 @@ static void plan_fusion(Model& m) {
   }
 }
 
+// Residual units on tensor cores: a stride-1 conv whose only consumer is a
+// 1x1 conv with a fused residual (and no history) run as one launch; the
+// intermediate never leaves the chip.  Both must fit one 128-row tile.
+static void plan_units(Model& m) {
+  if (!m.fuse_units) return;
+  const int n = (int)m.nodes.size();
+  for (int i = 0; i < n; ++i) {
+    NodePlan& p = m.nodes[i];
+    if (p.d.op != CC_OP_CONV || p.engine != 1 || p.d.stride != 1 || p.fused_add >= 0 ||
+        p.consumers.size() != 1)
+      continue;
+    const int qi = p.consumers[0];
+    NodePlan& q = m.nodes[qi];
+    if (q.d.op != CC_OP_CONV || q.engine != 1 || q.d.kernel != 1 || q.d.stride != 1 || q.hist_need != 0 ||
+        q.fused_add < 0 || q.unit_fused)
+      continue;
+    if (p.M > 128 || q.M > 128 || q.d.c_in != p.d.c_out || q.d.c_out != p.d.c_out || q.Kt > 128) continue;
+    p.unit_next = qi;
+    q.unit_fused = true;
+  }
+}
+
+// Split-K for tensor-core layers whose tiles at full capacity (max_streams,
+// one step) fill few SMs and whose K is long: clusters of 4 or 2 CTAs share a
+// tile.  Chosen from the layer and the capacity only, so that every batch
+// runs the same arithmetic; fused residual units run unsplit.
+static void plan_ksplit(Model& m) {
+  for (auto& p : m.nodes) {
+    p.ksplit = 1;
+    if (p.engine != 1 || p.unit_next >= 0 || p.unit_fused) continue;
+    const int nk = p.Kt / 64, mt = p.Mpad / 128;
+    const int64_t cols =
+        (int64_t)m.max_streams * (p.d.op == CC_OP_CONVT ? m.nodes[p.d.inputs[0]].u : p.u);
+    const int64_t ctas = (cols + 127) / 128 * mt;
+    p.ksplit = (ctas * 4 <= 148 && nk >= 8) ? 4 : (ctas * 2 <= 148 && nk >= 4) ? 2 : 1;
+  }
+}
+
 static size_t lcm_size(size_t a, size_t b) {
   size_t x = a, y = b;
   while (y) {
@@ -409,14 +447,6 @@ static cc_status pack_and_upload(Model& m, const float* const* weights, const fl
     if (p.engine == 1) {
       cc_status s = upload_tc_operand(m, p, A);
       if (s) return s;
-      // Split-K for layers whose tiles at full capacity (max_streams, one
-      // step) fill few SMs and whose K is long: clusters of 4 or 2 CTAs share
-      // a tile.  Chosen from the layer and the capacity only, so that every
-      // batch runs the same arithmetic.
-      const int nk = p.Kt / 64, mt = p.Mpad / 128;
-      const int64_t cols = (int64_t)m.max_streams * (d.op == CC_OP_CONVT ? m.nodes[d.inputs[0]].u : p.u);
-      const int64_t ctas = (cols + 127) / 128 * mt;
-      p.ksplit = (ctas * 4 <= 148 && nk >= 8) ? 4 : (ctas * 2 <= 148 && nk >= 4) ? 2 : 1;
     } else {
       CC_CUDA(cudaMalloc(&p.dA, A.size() * sizeof(float)));
       CC_CUDA(cudaMemcpy(p.dA, A.data(), A.size() * sizeof(float), cudaMemcpyHostToDevice));
@@ -487,13 +517,19 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
       continue;
     }
     if (d.op == CC_OP_ADD && p.fused) continue;
+    if (p.unit_fused) continue;  // computed by its producer's fused launch
+    // a fused residual unit writes the 1x1 conv's (and its fused add's) output
+    const int qi = p.unit_next;
+    const NodePlan* q = qi >= 0 ? &nodes[qi] : nullptr;
+    const NodePlan& r = q ? *q : p;  // the conv whose output this launch stores
     // the node whose output this launch writes (a fused add writes for its conv)
-    const int wi = (d.op == CC_OP_CONV || d.op == CC_OP_CONVT) && p.fused_add >= 0 ? p.fused_add : i;
+    const int wi = (r.d.op == CC_OP_CONV || r.d.op == CC_OP_CONVT) && r.fused_add >= 0 ? r.fused_add : (q ? qi : i);
     const NodePlan& w = nodes[wi];
     if (wi != last && !w.has_ring) continue;  // dead branch
     const OutViews ov = views_of(wi);
     const int this_launch = launches++;
     made_at[i] = made_at[wi] = this_launch;
+    if (q) made_at[qi] = this_launch;
     cc_status s = begin(i);
     if (s) return s;
     if (d.op == CC_OP_CONV || d.op == CC_OP_CONVT) {
@@ -521,12 +557,19 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
         a.in_rows_per_slot = p.in_rows_per_slot;
         a.in_row_off = p.in_row_off;
         a.out = ov;
-        if (p.fused_add >= 0) {
+        if (r.fused_add >= 0) {
           a.has_skip = 1;
-          a.skip = nodes[p.fused_skip].view[0];
-          a.skip_A = p.fused_skip_A;
-          const int sm = made_at[p.fused_skip];
+          a.skip = nodes[r.fused_skip].view[0];
+          a.skip_A = r.fused_skip_A;
+          const int sm = made_at[r.fused_skip];
           a.skip_early = sm >= 0 && sm <= this_launch - 2;
+        }
+        if (q) {
+          a.A2_tiled = q->dA_tiled;
+          a.scale2 = q->dscale;
+          a.bias2 = q->dbias;
+          a.k2 = q->Kt / 64;
+          a.act2 = q->d.act_in;
         }
         a.batch = batch;
         a.err = err;
@@ -820,6 +863,7 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
   m->max_streams = config->max_streams;
   m->max_steps = config->max_steps_per_call;
   m->noise = config->noise ? 1 : 0;
+  m->fuse_units = (config->flags & CC_FLAG_NO_UNIT_FUSION) ? 0 : 1;
   m->nodes.resize(n_nodes);
   for (int i = 0; i < n_nodes; ++i) m->nodes[i].d = nodes[i];
   cc_status s = cc::validate_and_analyze(*m);
@@ -832,6 +876,10 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
     return CC_OK;
   }
   if (!s) s = cc::pack_and_upload(*m, weights, biases);
+  if (!s) {
+    cc::plan_units(*m);
+    cc::plan_ksplit(*m);
+  }
   if (!s) {
     const size_t arena_bytes = m->slot_bytes * (size_t)m->max_streams;
     // the tensor-core epilogue addresses the arena in 32-bit 16-byte units

@@ -51,6 +51,8 @@ struct NodePlan {
   bool tmapT_ok[8] = {};
   int32_t in_rows_per_slot = 0, in_row_off = 0;
   int32_t ksplit = 1;  // tensor-core split-K factor, fixed per layer (batch-independent numerics)
+  int32_t unit_next = -1;  // this conv and the 1x1 conv (node unit_next) run as one launch
+  bool unit_fused = false;  // (1x1 conv) computed by its producer's fused launch
   std::map<int64_t, int32_t> tile_n;  // autotuned N tile by launch width (columns), 0: heuristic
 };
 
@@ -63,6 +65,7 @@ struct Model {
   int32_t dtype = CC_F32;
   int32_t lp_dtype = kDtBF16;  // element type of low-precision views
   int32_t max_streams = 0, max_steps = 1, noise = 1;
+  int32_t fuse_units = 1;  // residual units (k-wide conv -> 1x1 conv) as one tensor-core launch
   int32_t in_per_step = 1;
   std::vector<NodePlan> nodes;
   size_t slot_bytes = 0, state_bytes = 0, weight_bytes = 0;

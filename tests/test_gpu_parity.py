@@ -317,3 +317,33 @@ def test_lowp_window_boxes_match_gathers(cclib, cuda):
     np.testing.assert_array_equal(outs[0], outs[1])
     ref = M.run_causal(dec, p, z[:, 31, 0, :], seed=seeds[31])[:, 0]
     _assert_lowp(outs[0][31], ref, "bf16 stream 31 of 50, 40 steps")
+
+
+@pytest.mark.parametrize("count", [256, 250])
+def test_fused_residual_units_equal_unfused(cclib, cuda, count):
+    """A residual unit (k=3 conv -> 1x1 conv + skip) with at most 128 channels
+    runs as one tensor-core launch, its intermediate rounded to BF16 in
+    shared memory exactly as the unfused path rounds it into its ring: the two
+    give identical outputs.  One stream is also checked against the oracle."""
+    import torch
+
+    dec, p = _decoder(12)
+    steps = 4
+    seeds = W.stream_seeds(21, count)
+    z = np.random.default_rng(6).standard_normal((steps, count, 1, 128))
+    outs = []
+    for fuse in (True, False):
+        model = api.Model(dec, p, dtype="bf16", max_streams=count, max_steps_per_call=1, fuse_units=fuse)
+        streams = [model.stream(seed=s) for s in seeds]
+        y = torch.empty((count, 2048, 1), dtype=torch.float32, device=cuda)
+        o = np.zeros((count, steps * 2048))
+        for t in range(steps):
+            model.process_batch(streams, torch.tensor(z[t], dtype=torch.float32, device=cuda), y)
+            o[:, t * 2048:(t + 1) * 2048] = y[:, :, 0].cpu().numpy()
+        assert model.device_status() == 0
+        outs.append(o)
+        model.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    k = count // 3
+    ref = M.run_causal(dec, p, z[:, k, 0, :], seed=seeds[k])[:, 0]
+    _assert_lowp(outs[0][k], ref, f"bf16 fused units, stream {k} of {count}")

@@ -97,6 +97,8 @@ struct TcArgs {
   int32_t has_skip, skip_A;
   int32_t skip_early;  // the residual's producer launched two or more launches back
   int32_t ksplit;      // split-K factor (1, 2 or 4): CTAs per cluster sharing a tile
+  int32_t deep_ok;     // one-wave grids may take the deep one-CTA-per-SM pipelines (models
+                       //   sized for at most 256 streams: no concurrent chains expected)
   // Residual-unit fusion (k2 > 0): the tile's result, scaled, biased and
   // activated (act2) in BF16/FP16, is the B operand of a second, 1x1
   // contraction A2 [M][k2*64] (pre-tiled like A) whose result, with scale2,

@@ -68,9 +68,10 @@ constexpr int kEpi = 256;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
 // Pipeline depth: 128-column tiles run 6 stages when the grid fits in one wave
-// (one CTA per SM: few CTAs with long K loops need deep prefetch), else 3
-// stages (two CTAs per SM, whose epilogues overlap each other's main loops);
-// 256-column tiles use 4 stages.
+// and the model expects no concurrent launch chains (one CTA per SM: few CTAs
+// with long K loops need deep prefetch) or the layer is split; else 3 stages
+// (two CTAs per SM, whose epilogues overlap each other's main loops and other
+// chains' kernels); 256-column tiles use 4 stages.
 template <int BN, int STAGES, bool FUSE>
 struct TcLayout {
   static constexpr int kStages = STAGES;
@@ -85,7 +86,7 @@ struct TcLayout {
   static constexpr int kB2 = FUSE ? 2 * BN * 128 : 0;  // fused unit: BN x 128 channels, 2 K slices
   static constexpr int kBars2 = FUSE ? 16 : 0;          // b2ready, tfull2
   static constexpr int kBytes = 1024 + kStages * (kA + kB) + kB2 + kBars + kBars2 + kCols + kTurn + 64;
-  static constexpr int kMinBlocks = (STAGES == 3 || FUSE) ? 2 : 1;
+  static constexpr int kMinBlocks = (STAGES == 3 || (FUSE && STAGES == 2)) ? 2 : 1;
   static constexpr int kTmemCols = FUSE ? 2 * BN : BN;
 };
 
@@ -449,30 +450,29 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBloc
       // fused unit, first epilogue: the k-wide conv's result, scaled, biased,
       // activated and rounded, into the 1x1 conv's K-major operand (row =
       // column of the tile, 128-byte-swizzled rows, 64 channels per K slice)
+      // Each lane holds one channel (its accumulator row) of 8 columns: it
+      // stores 2 bytes per column; a warp's 32 channels of a column are four
+      // 16-byte chunks of that column's swizzled row.
       const bool lp_bf16 = a.in.dtype == kDtBF16;
+      const int32_t cm = m;  // channel = accumulator row (phases == 1)
+      uint8_t* const b2row = sB2 + (cm >> 6) * (BN * 128) + (cm & 7) * 2;
+      const int chunk1 = (cm & 63) >> 3;
       if (all_ok)
 #pragma unroll 1
         for (int g = half; g < BN / 8; g += 2) {
           uint32_t r[8];
           tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(8 * g), r);
           tmem_ld_wait();
-          __syncwarp();
+          if (mok)
 #pragma unroll
-          for (int k = 0; k < 8; ++k) tw[k * 32 + lane] = fmaf(__uint_as_float(r[k]), sc1, bi1);
-          __syncwarp();
-          const float4 v0 = *reinterpret_cast<const float4*>(tw + kk * 32 + 8 * (lane & 3));
-          const float4 v1 = *reinterpret_cast<const float4*>(tw + kk * 32 + 8 * (lane & 3) + 4);
-          float y[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-          if (a.act2)
-#pragma unroll
-            for (int i = 0; i < 8; ++i) y[i] = leaky(y[i]);
-          const uint4 pk = make_uint4(pack2(y[0], y[1], lp_bf16), pack2(y[2], y[3], lp_bf16),
-                                      pack2(y[4], y[5], lp_bf16), pack2(y[6], y[7], lp_bf16));
-          if (vok) {
-            const int c = 8 * g + kk;
-            const int chunk = (ch_l & 63) >> 3;
-            *reinterpret_cast<uint4*>(sB2 + (ch_l >> 6) * (BN * 128) + c * 128 + ((chunk ^ (c & 7)) << 4)) = pk;
-          }
+            for (int k = 0; k < 8; ++k) {
+              float y = fmaf(__uint_as_float(r[k]), sc1, bi1);
+              if (a.act2) y = leaky(y);
+              const uint16_t h = lp_bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(y))
+                                         : __half_as_ushort(__float2half_rn(y));
+              const int c = 8 * g + k;
+              *reinterpret_cast<uint16_t*>(b2row + c * 128 + ((chunk1 ^ (c & 7)) << 4)) = h;
+            }
         }
       fence_proxy_async_smem();  // the operand is read by the tensor cores (async proxy)
       asm volatile("bar.sync 1, 256;" ::: "memory");
@@ -677,11 +677,12 @@ cudaError_t launch_conv_tc(const void* tmap_t, const void* tmap_b, const TcArgs&
   if (a.k2 > 0) {
     // fused residual unit: 128-column tiles, no split, one M tile (M <= 128)
     if (ks != 1 || a.M > kBM || a.k2 > 2) return cudaErrorInvalidValue;
+    if (a.deep_ok && (N + 127) / 128 <= 148) return launch_bn<128, 4, true>(ta, tb, a, 1, st);
     return launch_bn<128, 2, true>(ta, tb, a, 1, st);
   }
   if (bn == 256 && ks == 1) return launch_bn<256, 4>(ta, tb, a, 1, st);
   const int64_t ctas = (N + 127) / 128 * ((a.M + kBM - 1) / kBM) * ks;
-  if (ctas <= 148) return launch_bn<128, 6>(ta, tb, a, ks, st);
+  if (ctas <= 148 && (a.deep_ok || ks > 1)) return launch_bn<128, 6>(ta, tb, a, ks, st);
   return launch_bn<128, 3>(ta, tb, a, ks, st);
 }
 

@@ -583,6 +583,7 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
         }
         a.box_ok = li >= 0;
         a.ksplit = p.ksplit;
+        a.deep_ok = max_streams <= 256;
         const int bn = tile_n_for(p, (int64_t)batch.count * ncols);
         CC_CUDA(launch_conv_tc(li >= 0 ? p.tmapT[li] : p.tmapB, p.tmapB, a, bn, st));
       } else {

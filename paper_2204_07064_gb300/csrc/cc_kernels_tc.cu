@@ -17,9 +17,10 @@
 //              copies, so every stage can be in flight
 //   warp 1     TMEM allocation; lane 0 issues tcgen05.mma (128 x BN x 16,
 //              BF16 or FP16 operands, FP32 accumulation in TMEM)
-//   warps 2-9  epilogue: warp w owns accumulator rows 32*(w%4) .. +31 (its
-//              TMEM lane quarter) and every other group of 8 columns (the two
-//              warps of a quarter alternate); per group it loads the rows
+//   warps 2-   epilogue (8 or 16 warps): warp w owns accumulator rows
+//              32*(w%4) .. +31 (its TMEM lane quarter) and every EW/4-th
+//              group of 8 columns (the warps of a quarter alternate); per
+//              group it loads the rows
 //              (tcgen05.ld), applies scale and bias, turns the 32 x 8 block
 //              around in 1 KB of shared memory so that each lane holds 8
 //              consecutive channels of one column, adds the aligned residual
@@ -63,8 +64,8 @@ namespace {
 using namespace sm100;
 
 constexpr int kBM = 128;
-constexpr int kThreads = 320;  // producer, MMA issuer, 8 epilogue warps
-constexpr int kEpi = 256;
+// producer warp, MMA warp, EW epilogue warps (8, or 16 for the one-CTA-per-SM
+// variants, whose epilogue has the SM to itself)
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
 // Pipeline depth: 128-column tiles run 6 stages when the grid fits in one wave
@@ -72,8 +73,9 @@ constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 // with long K loops need deep prefetch) or the layer is split; else 3 stages
 // (two CTAs per SM, whose epilogues overlap each other's main loops and other
 // chains' kernels); 256-column tiles use 4 stages.
-template <int BN, int STAGES, bool FUSE>
+template <int BN, int STAGES, bool FUSE, int EW>
 struct TcLayout {
+  static constexpr int kThreads = 64 + 32 * EW;
   static constexpr int kStages = STAGES;
   static constexpr int kA = kBM * 128;  // one 128 x 64 low-precision tile
   static constexpr int kB = BN * 128;
@@ -82,7 +84,7 @@ struct TcLayout {
   // units of the ring row holding the column's first frame, that ring row,
   // the mirror row's offset (low-precision views); the caller-buffer offset
   static constexpr int kCols = BN * (4 * 4 + 4 * 4 + 2 * 4 + 8);
-  static constexpr int kTurn = 8 * 32 * 8 * 4;  // per epilogue warp: 32 rows x 8 columns of FP32
+  static constexpr int kTurn = EW * 32 * 8 * 4;  // per epilogue warp: 32 rows x 8 columns of FP32
   static constexpr int kB2 = FUSE ? 2 * BN * 128 : 0;  // fused unit: BN x 128 channels, 2 K slices
   static constexpr int kBars2 = FUSE ? 16 : 0;          // b2ready, tfull2
   static constexpr int kBytes = 1024 + kStages * (kA + kB) + kB2 + kBars + kBars2 + kCols + kTurn + 64;
@@ -99,11 +101,13 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi, bool bf16) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-template <int BN, int STAGES, bool FUSE>
-__global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBlocks)
+template <int BN, int STAGES, bool FUSE, int EW>
+__global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW>::kThreads, TcLayout<BN, STAGES, FUSE, EW>::kMinBlocks)
     k_conv_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmB,
               const TcArgs a) {
-  using L = TcLayout<BN, STAGES, FUSE>;
+  using L = TcLayout<BN, STAGES, FUSE, EW>;
+  constexpr int kEpi = 32 * EW;  // epilogue threads
+  constexpr int kParts = EW / 4;  // epilogue warps per TMEM lane quarter
   constexpr int kStages = L::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBloc
     // ---------------------------------------------------------------- epilogue
     const int t = threadIdx.x - 64;  // 0..255
     const int sub = warp & 3;        // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;  // which groups of 8 columns: half, half + 2
+    const int half = (warp - 2) >> 2;  // which groups of 8 columns: half, half + kParts, ...
     const int32_t m = m0 + sub * 32 + lane;  // accumulator row of this thread
     const bool mok = m < a.M;
     const int32_t ph = (mok && a.phases > 1) ? m / a.cout : 0;  // transposed conv: phase
@@ -369,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBloc
       put(2, a.out.lp[1].off, a.out.lp[1].rows, a.out.lp[1].chans, a.out.lp[1].pre, tb, 2);
       put(3, a.skip.off, a.skip.rows, a.skip.chans, 0, tb - a.skip_A, 4);
     }
-    asm volatile("bar.sync 1, 256;" ::: "memory");  // column table complete
+    asm volatile("bar.sync 1, %0;" ::"n"(kEpi) : "memory");  // column table complete
     char* const arena = a.batch.arena;
     const bool phased = a.phases > 1;
     // After the turn, lane l holds column kk = l / 4 of its group and the 8
@@ -439,10 +443,10 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBloc
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.and.pred p, 1, 256, q;\n\t"
+        "bar.red.and.pred p, 1, %2, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(all_ok)
-        : "r"((uint32_t)waited)
+        : "r"((uint32_t)waited), "n"(kEpi)
         : "memory");
     tc_fence_after();
     uint32_t acc_col = 0;  // TMEM column of the stored result's accumulator
@@ -459,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBloc
       const int chunk1 = (cm & 63) >> 3;
       if (all_ok)
 #pragma unroll 1
-        for (int g = half; g < BN / 8; g += 2) {
+        for (int g = half; g < BN / 8; g += kParts) {
           uint32_t r[8];
           tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(8 * g), r);
           tmem_ld_wait();
@@ -475,17 +479,17 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBloc
             }
         }
       fence_proxy_async_smem();  // the operand is read by the tensor cores (async proxy)
-      asm volatile("bar.sync 1, 256;" ::: "memory");
+      asm volatile("bar.sync 1, %0;" ::"n"(kEpi) : "memory");
       if (t == 0) mbar_arrive(b2ready);
       const bool waited2 = mbar_wait(tfull2, 0, kWaitNs);
       uint32_t ok2;
       asm volatile(
           "{\n\t.reg .pred p, q;\n\t"
           "setp.ne.u32 q, %1, 0;\n\t"
-          "bar.red.and.pred p, 1, 256, q;\n\t"
+          "bar.red.and.pred p, 1, %2, q;\n\t"
           "selp.u32 %0, 1, 0, p;\n\t}"
           : "=r"(ok2)
-          : "r"((uint32_t)waited2)
+          : "r"((uint32_t)waited2), "n"(kEpi)
           : "memory");
       tc_fence_after();
       all_ok = all_ok && ok2;
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBloc
     if (KS > 1) {
       if (all_ok)
 #pragma unroll 1
-        for (int g = half; g < BN / 8; g += 2) {
+        for (int g = half; g < BN / 8; g += kParts) {
           uint32_t r[8];
           tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(8 * g), r);
           tmem_ld_wait();
@@ -546,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBloc
           sr_next = col_row[3 * BN + cl + 32];
         }
 #pragma unroll 1
-        for (int g = half; g < 4; g += 2) {
+        for (int g = half; g < 4; g += kParts) {
           if (n0 + cb + 8 * g >= N) break;  // uniform
           uint32_t r[8];
           if (KS == 1) {
@@ -575,8 +579,8 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBloc
             x[0] += sk0.x; x[1] += sk0.y; x[2] += sk0.z; x[3] += sk0.w;
             x[4] += sk1.x; x[5] += sk1.y; x[6] += sk1.z; x[7] += sk1.w;
             // the next group's residual loads overlap this group's stores
-            if (g + 2 < 4)
-              load_skip(cb, g + 2, so_cur, sr_cur);
+            if (g + kParts < 4)
+              load_skip(cb, g + kParts, so_cur, sr_cur);
             else if (cb + 32 < c_lo + c_n && n0 + cb + 32 < N)
               load_skip(cb + 32, half, so_next, sr_next);
           }
@@ -631,13 +635,14 @@ __global__ void __launch_bounds__(kThreads, TcLayout<BN, STAGES, FUSE>::kMinBloc
   if (warp == 1) tmem_dealloc(tmem, L::kTmemCols);
 }
 
-template <int BN, int STAGES, bool FUSE = false>
+template <int BN, int STAGES, bool FUSE, int EW>
 cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int ks, cudaStream_t st) {
   static bool configured = false;
-  constexpr int bytes = TcLayout<BN, STAGES, FUSE>::kBytes;
+  using L = TcLayout<BN, STAGES, FUSE, EW>;
+  constexpr int bytes = L::kBytes;
   if (!configured) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_conv_tc<BN, STAGES, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        cudaFuncSetAttribute(k_conv_tc<BN, STAGES, FUSE, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -646,7 +651,7 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)mtiles, (unsigned)ks);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(L::kThreads);
   cfg.dynamicSmemBytes = (size_t)bytes;
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
@@ -658,7 +663,7 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs
   attr[1].val.clusterDim.z = (unsigned)ks;
   cfg.attrs = attr;
   cfg.numAttrs = ks > 1 ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, k_conv_tc<BN, STAGES, FUSE>, ta, tb, a);
+  return cudaLaunchKernelEx(&cfg, k_conv_tc<BN, STAGES, FUSE, EW>, ta, tb, a);
 }
 
 }  // namespace
@@ -677,13 +682,13 @@ cudaError_t launch_conv_tc(const void* tmap_t, const void* tmap_b, const TcArgs&
   if (a.k2 > 0) {
     // fused residual unit: 128-column tiles, no split, one M tile (M <= 128)
     if (ks != 1 || a.M > kBM || a.k2 > 2) return cudaErrorInvalidValue;
-    if (a.deep_ok && (N + 127) / 128 <= 148) return launch_bn<128, 4, true>(ta, tb, a, 1, st);
-    return launch_bn<128, 2, true>(ta, tb, a, 1, st);
+    if (a.deep_ok && (N + 127) / 128 <= 148) return launch_bn<128, 4, true, 16>(ta, tb, a, 1, st);
+    return launch_bn<128, 2, true, 8>(ta, tb, a, 1, st);
   }
-  if (bn == 256 && ks == 1) return launch_bn<256, 4>(ta, tb, a, 1, st);
+  if (bn == 256 && ks == 1) return launch_bn<256, 4, false, 8>(ta, tb, a, 1, st);
   const int64_t ctas = (N + 127) / 128 * ((a.M + kBM - 1) / kBM) * ks;
-  if (ctas <= 148 && (a.deep_ok || ks > 1)) return launch_bn<128, 6>(ta, tb, a, ks, st);
-  return launch_bn<128, 3>(ta, tb, a, ks, st);
+  if (ctas <= 148 && (a.deep_ok || ks > 1)) return launch_bn<128, 6, false, 16>(ta, tb, a, ks, st);
+  return launch_bn<128, 3, false, 8>(ta, tb, a, ks, st);
 }
 
 }  // namespace cc

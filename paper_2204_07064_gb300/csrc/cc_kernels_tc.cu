@@ -36,11 +36,11 @@
 // the intermediate is the one the unfused path applies when it stores it, so
 // the results are identical.
 // Split-K (layers with few tiles and long K): the ksplit CTAs of a cluster
-// along z share one tile; CTA z accumulates an equal share of the K slices,
-// writes its partial accumulator to its own shared memory, and after a
-// cluster barrier finishes columns [z, z+1) * BN/ksplit by summing the
-// partials of all CTAs of the cluster (distributed shared memory, fixed order
-// z = 0, 1, ...).  The split is a property of the layer, so a stream's result
+// along z share one tile; CTA z accumulates an equal share of the K slices and
+// finishes columns [z, z+1) * BN/ksplit.  Each CTA pushes its partial sums of
+// the other CTAs' columns into their shared memory (distributed shared-memory
+// stores); after one cluster barrier, each CTA adds its own partial (TMEM) and
+// the received ones in the fixed order z = 0, 1, ...  The split is a property of the layer, so a stream's result
 // does not depend on the batch it runs in.
 // Every mbarrier wait is bounded in time and records an error in the model's
 // device error word instead of hanging.
@@ -73,7 +73,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 // with long K loops need deep prefetch) or the layer is split; else 3 stages
 // (two CTAs per SM, whose epilogues overlap each other's main loops and other
 // chains' kernels); 256-column tiles use 4 stages.
-template <int BN, int STAGES, bool FUSE, int EW>
+template <int BN, int STAGES, bool FUSE, int EW, bool SPLIT = false>
 struct TcLayout {
   static constexpr int kThreads = 64 + 32 * EW;
   static constexpr int kStages = STAGES;
@@ -87,7 +87,10 @@ struct TcLayout {
   static constexpr int kTurn = EW * 32 * 8 * 4;  // per epilogue warp: 32 rows x 8 columns of FP32
   static constexpr int kB2 = FUSE ? 2 * BN * 128 : 0;  // fused unit: BN x 128 channels, 2 K slices
   static constexpr int kBars2 = FUSE ? 16 : 0;          // b2ready, tfull2
-  static constexpr int kBytes = 1024 + kStages * (kA + kB) + kB2 + kBars + kBars2 + kCols + kTurn + 64;
+  // split-K receive buffer: the other CTAs' partials of this CTA's columns
+  // ([ksplit-1][BN/ksplit][128] FP32: at most 3 x 32 or 1 x 64 columns)
+  static constexpr int kRecv = SPLIT ? 3 * (BN / 4) * kBM * 4 : 0;
+  static constexpr int kBytes = 1024 + kStages * (kA + kB) + kB2 + kRecv + kBars + kBars2 + kCols + kTurn + 64;
   static constexpr int kMinBlocks = (STAGES == 3 || (FUSE && STAGES == 2)) ? 2 : 1;
   static constexpr int kTmemCols = FUSE ? 2 * BN : BN;
 };
@@ -101,11 +104,12 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi, bool bf16) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-template <int BN, int STAGES, bool FUSE, int EW>
-__global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW>::kThreads, TcLayout<BN, STAGES, FUSE, EW>::kMinBlocks)
+template <int BN, int STAGES, bool FUSE, int EW, bool SPLIT>
+__global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThreads,
+                                  TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kMinBlocks)
     k_conv_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmB,
               const TcArgs a) {
-  using L = TcLayout<BN, STAGES, FUSE, EW>;
+  using L = TcLayout<BN, STAGES, FUSE, EW, SPLIT>;
   constexpr int kEpi = 32 * EW;  // epilogue threads
   constexpr int kParts = EW / 4;  // epilogue warps per TMEM lane quarter
   constexpr int kStages = L::kStages;
@@ -115,7 +119,8 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW>::kThreads, TcLa
   uint8_t* sA = smem;
   uint8_t* sB = smem + kStages * L::kA;
   uint8_t* sB2 = sB + kStages * L::kB;  // fused unit: second operand (1024-aligned)
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB2 + L::kB2);
+  float* const recv = reinterpret_cast<float*>(sB2 + L::kB2);  // split-K receive buffer
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB2 + L::kB2 + L::kRecv);
   uint64_t* empty = full + kStages;
   uint64_t* tfull = empty + kStages;
   uint64_t* b2ready = tfull + 1;  // fused unit (FUSE only)
@@ -134,7 +139,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW>::kThreads, TcLa
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   const int nk = a.Kt / 64;
   const int cchunks = a.cin / 64;
-  const int KS = (int)gridDim.z, zr = (int)blockIdx.z;  // split-K (cluster along z)
+  const int KS = SPLIT ? (int)gridDim.z : 1, zr = SPLIT ? (int)blockIdx.z : 0;  // split-K (cluster along z)
   const int kb = zr * nk / KS, ke = (zr + 1) * nk / KS;  // this CTA's K slices
   const int c_n = BN / KS, c_lo = zr * c_n;              // columns this CTA finishes
 
@@ -275,10 +280,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW>::kThreads, TcLa
       for (int i = issued - kStages < 0 ? 0 : issued - kStages; i < issued; ++i)
         mbar_wait(full + i % kStages, (i / kStages) & 1, kWaitNs);
     }
-    if (KS > 1) {  // the epilogue's two cluster barriers
-      cluster_sync();
-      cluster_sync();
-    }
+    if (KS > 1) cluster_sync();  // the epilogue's partial exchange
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     pdl_wait();
@@ -329,10 +331,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW>::kThreads, TcLa
       if (!ok) atomicOr(a.err, 4);
     }
     __syncwarp();
-    if (KS > 1) {  // the epilogue's two cluster barriers
-      cluster_sync();
-      cluster_sync();
-    }
+    if (KS > 1) cluster_sync();  // the epilogue's partial exchange
   } else {
     // ---------------------------------------------------------------- epilogue
     const int t = threadIdx.x - 64;  // 0..255
@@ -495,22 +494,25 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW>::kThreads, TcLa
       all_ok = all_ok && ok2;
       acc_col = BN;
     }
-    // split-K: partial accumulator [BN columns][128 rows] FP32 into the free
-    // pipeline buffers, then the cluster's partials are complete
-    float* const part = reinterpret_cast<float*>(sA);
-    uint32_t part_at[4] = {0, 0, 0, 0};  // the partial buffers of the cluster's CTAs
-    if (KS > 1) {
+    // split-K: receive buffer [KS-1 senders][c_n columns][128 rows] FP32 of
+    // its own (never touched by the main loop, so a CTA may push into a
+    // slower one's); sender z's slot in owner o's buffer is z (z < o) or z - 1
+    if (SPLIT && KS > 1) {
       if (all_ok)
+        for (int o = 0; o < KS; ++o) {
+          if (o == zr) continue;
+          const uint32_t rbase =
+              dsmem_map(smem_u32(recv), (uint32_t)o) + (uint32_t)((zr < o ? zr : zr - 1) * c_n * kBM * 4);
 #pragma unroll 1
-        for (int g = half; g < BN / 8; g += kParts) {
-          uint32_t r[8];
-          tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(8 * g), r);
-          tmem_ld_wait();
+          for (int g = half; g < c_n / 8; g += kParts) {
+            uint32_t r[8];
+            tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(o * c_n + 8 * g), r);
+            tmem_ld_wait();
 #pragma unroll
-          for (int k = 0; k < 8; ++k) part[(8 * g + k) * kBM + sub * 32 + lane] = __uint_as_float(r[k]);
+            for (int k = 0; k < 8; ++k)
+              dsmem_st_f32(rbase + (uint32_t)(((8 * g + k) * kBM + sub * 32 + lane) * 4), __uint_as_float(r[k]));
+          }
         }
-#pragma unroll
-      for (int z = 0; z < 4; ++z) part_at[z] = z < KS ? dsmem_map(smem_u32(part), z) : 0u;
       cluster_sync();
     }
     if (!all_ok) {
@@ -553,17 +555,18 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW>::kThreads, TcLa
         for (int g = half; g < 4; g += kParts) {
           if (n0 + cb + 8 * g >= N) break;  // uniform
           uint32_t r[8];
-          if (KS == 1) {
-            tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + acc_col + (uint32_t)(cb + 8 * g), r);
-            tmem_ld_wait();
-          } else {
+          tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + acc_col + (uint32_t)(cb + 8 * g), r);
+          tmem_ld_wait();
+          if (KS > 1) {
+            // own partial (TMEM) and the received ones, summed in the order z = 0, 1, ...
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-              const uint32_t off = (uint32_t)(((cb + 8 * g + k) * kBM + sub * 32 + lane) * 4);
+              const float* rc = recv + (cb - c_lo + 8 * g + k) * kBM + sub * 32 + lane;
+              const float own = __uint_as_float(r[k]);
               float acc = 0.f;
 #pragma unroll
               for (int z = 0; z < 4; ++z)
-                if (z < KS) acc += dsmem_ld_f32(part_at[z] + off);
+                if (z < KS) acc += z == zr ? own : rc[(z < zr ? z : z - 1) * c_n * kBM];
               r[k] = __float_as_uint(acc);
             }
           }
@@ -627,7 +630,6 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW>::kThreads, TcLa
         }
       }
     }
-    if (KS > 1) cluster_sync();  // the cluster's partials are read: buffers may go
   }
   tc_fence_before();
   __syncthreads();
@@ -635,14 +637,14 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW>::kThreads, TcLa
   if (warp == 1) tmem_dealloc(tmem, L::kTmemCols);
 }
 
-template <int BN, int STAGES, bool FUSE, int EW>
+template <int BN, int STAGES, bool FUSE, int EW, bool SPLIT = false>
 cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int ks, cudaStream_t st) {
   static bool configured = false;
-  using L = TcLayout<BN, STAGES, FUSE, EW>;
+  using L = TcLayout<BN, STAGES, FUSE, EW, SPLIT>;
   constexpr int bytes = L::kBytes;
   if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_conv_tc<BN, STAGES, FUSE, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<BN, STAGES, FUSE, EW, SPLIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -663,7 +665,7 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs
   attr[1].val.clusterDim.z = (unsigned)ks;
   cfg.attrs = attr;
   cfg.numAttrs = ks > 1 ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, k_conv_tc<BN, STAGES, FUSE, EW>, ta, tb, a);
+  return cudaLaunchKernelEx(&cfg, k_conv_tc<BN, STAGES, FUSE, EW, SPLIT>, ta, tb, a);
 }
 
 }  // namespace
@@ -687,8 +689,12 @@ cudaError_t launch_conv_tc(const void* tmap_t, const void* tmap_b, const TcArgs&
   }
   if (bn == 256 && ks == 1) return launch_bn<256, 4, false, 8>(ta, tb, a, 1, st);
   const int64_t ctas = (N + 127) / 128 * ((a.M + kBM - 1) / kBM) * ks;
-  if (ctas <= 148 && (a.deep_ok || ks > 1)) return launch_bn<128, 6, false, 16>(ta, tb, a, ks, st);
-  return launch_bn<128, 3, false, 8>(ta, tb, a, ks, st);
+  if (ks > 1) {
+    if (ks > 4) return cudaErrorInvalidValue;
+    return launch_bn<128, 4, false, 16, true>(ta, tb, a, ks, st);
+  }
+  if (ctas <= 148 && a.deep_ok) return launch_bn<128, 6, false, 16>(ta, tb, a, 1, st);
+  return launch_bn<128, 3, false, 8>(ta, tb, a, 1, st);
 }
 
 }  // namespace cc

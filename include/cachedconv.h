@@ -100,6 +100,12 @@ typedef struct {
  * consumes only it as one launch, the intermediate kept on chip; the results
  * are identical). */
 #define CC_FLAG_NO_UNIT_FUSION 1
+/* cc_model_config.flags: launch sibling tensor-core convolutions on their own
+ * (the path otherwise runs stride-1 convs that share their input, whose
+ * outputs are read in FP32 only, as one contraction with their windows
+ * right-aligned and their outputs side by side in one ring; the results are
+ * identical). */
+#define CC_FLAG_NO_SIBLING_MERGE 2
 
 typedef struct cc_model cc_model;
 typedef struct cc_stream cc_stream;

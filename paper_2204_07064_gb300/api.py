@@ -152,7 +152,7 @@ class Model:
     """A reconfigured model on the GPU: packed weights + stream-state arena."""
 
     def __init__(self, nodes, params, dtype="f32", max_streams=1, max_steps_per_call=1, noise=True,
-                 fuse_units=True):
+                 fuse_units=True, merge_siblings=True):
         L = lib()
         n = len(nodes)
         descs = (NodeDesc * n)(*[_desc(nd) for nd in nodes])
@@ -170,7 +170,7 @@ class Model:
                     self._keep.append(b32)
                     bp[i] = b32.ctypes.data
         cfg = ModelConfig(DTYPES[dtype], max_streams, max_steps_per_call, int(bool(noise)),
-                          0 if fuse_units else 1)
+                          (0 if fuse_units else 1) | (0 if merge_siblings else 2))
         h = _P()
         _check(L.cc_model_create(descs, n, wp, bp, C.byref(cfg), C.byref(h)))
         self._keep = None

@@ -37,6 +37,8 @@ struct Ring {
   int32_t u;      // frames per model step at this node
   int32_t dtype;  // kDt*
   int32_t pre;    // mirrored rows before row 0 (low-precision views), else 0
+  int32_t choff;  // first channel of this view inside the ring's rows (a sibling
+                  // group's members share one ring of `chans` channels per row)
 };
 
 // Every destination of a layer's output.

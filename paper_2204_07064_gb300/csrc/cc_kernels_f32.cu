@@ -27,7 +27,7 @@ __device__ __forceinline__ void store_conv(const ConvArgs& a, int32_t m, int32_t
   const int64_t t = steps_of(a.batch, s) * a.out_u + lt;
   if (a.has_skip) {
     const float* sk = ring_ptr<const float>(a.batch, s, a.skip);
-    v += sk[ring_row(t - a.skip_A, a.skip.rows) * a.skip.chans + ch];
+    v += sk[ring_row(t - a.skip_A, a.skip.rows) * a.skip.chans + a.skip.choff + ch];
   }
   store_views(a.batch, s, a.out, t, lt, ch, a.cout, v);
 }
@@ -64,7 +64,7 @@ __device__ __forceinline__ void store_column(const ConvArgs& a, int32_t n, const
         if (a.has_skip) {
           const float4 s4 = __ldg(reinterpret_cast<const float4*>(
               reinterpret_cast<const float*>(base + a.skip.off) +
-              (int64_t)wrap_row(rs + ph[g], a.skip.rows) * a.skip.chans + ch[g]));
+              (int64_t)wrap_row(rs + ph[g], a.skip.rows) * a.skip.chans + a.skip.choff + ch[g]));
           b4.x += s4.x; b4.y += s4.y; b4.z += s4.z; b4.w += s4.w;
         }
       }
@@ -103,7 +103,7 @@ __device__ __forceinline__ void store_column(const ConvArgs& a, int32_t n, const
       if (a.bias) add[i] = __ldg(a.bias + ch[i]);
       if (a.has_skip)
         add[i] += __ldg(reinterpret_cast<const float*>(base + a.skip.off) +
-                        (int64_t)wrap_row(rs + ph[i], a.skip.rows) * a.skip.chans + ch[i]);
+                        (int64_t)wrap_row(rs + ph[i], a.skip.rows) * a.skip.chans + a.skip.choff + ch[i]);
     }
   }
 #pragma unroll
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kGemvWarps * 32) k_conv_gemv_f32(const ConvArg
       const int32_t s = n / a.ncols, j = n - s * a.ncols;
       const int64_t t = steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist;
       r0[c] = (int32_t)ring_row(t, a.in.rows);
-      col[c] = ring_ptr<const float>(a.batch, s, a.in);
+      col[c] = ring_ptr<const float>(a.batch, s, a.in) + a.in.choff;
     }
   }
   float acc[kGemvCols];
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kGemvWarps * 32) k_conv_gemv_f32(const ConvArg
       int32_t rowoff[kGemvCols];
 #pragma unroll
       for (int c = 0; c < kGemvCols; ++c)
-        rowoff[c] = wrap_row(r0[c] + tap * a.dil, a.in.rows) * a.cin;
+        rowoff[c] = wrap_row(r0[c] + tap * a.dil, a.in.rows) * a.in.chans;
       const float* At = Arow + tap * a.cin;
       for (int32_t ch = lane * 4; ch < a.cin; ch += 128) {
         const float4 w = *reinterpret_cast<const float4*>(At + ch);
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kGemvWarps * 32) k_conv_gemv_f32(const ConvArg
       for (int c = 0; c < kGemvCols; ++c) {
         if (ok[c]) {
           const int32_t row = wrap_row(r0[c] + tap * a.dil, a.in.rows);
-          acc[c] = fmaf(w, activate(col[c][row * a.cin + ch], a.act), acc[c]);
+          acc[c] = fmaf(w, activate(col[c][row * a.in.chans + ch], a.act), acc[c]);
         }
       }
     }
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
       const int32_t s = n / a.ncols, j = n - s * a.ncols;
       const int64_t t = steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist;
       br0[q] = (int32_t)ring_row(t, a.in.rows);
-      bcol[q] = ring_ptr<const float>(a.batch, s, a.in);
+      bcol[q] = ring_ptr<const float>(a.batch, s, a.in) + a.in.choff;
     }
   }
   float4 ra[A4], rb[B4];
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
       if (b_ok[q]) {
         const int32_t row = wrap_row(br0[q] + tap * a.dil, a.in.rows);
         const float4 x =
-            *reinterpret_cast<const float4*>(bcol[q] + (int64_t)row * a.cin + chb + lkB[q]);
+            *reinterpret_cast<const float4*>(bcol[q] + (int64_t)row * a.in.chans + chb + lkB[q]);
         rb[q] = make_float4(activate(x.x, a.act), activate(x.y, a.act), activate(x.z, a.act),
                             activate(x.w, a.act));
       } else {
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
   const int32_t N = a.batch.count * a.ncols;
   if (n >= N) return;
   const int32_t s = n / a.ncols, j = n - s * a.ncols;
-  const float* col = ring_ptr<const float>(a.batch, s, a.in);
+  const float* col = ring_ptr<const float>(a.batch, s, a.in) + a.in.choff;
   const int32_t r0 =
       (int32_t)ring_row(steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist, a.in.rows);
   // the whole window (taps x cin <= 64 values) is requested before any use
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
     float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k < a.Kt) {
       const int32_t tap = k / a.cin, c = k - tap * a.cin;
-      v4 = *reinterpret_cast<const float4*>(col + (int64_t)wrap_row(r0 + tap * a.dil, a.in.rows) * a.cin + c);
+      v4 = *reinterpret_cast<const float4*>(col + (int64_t)wrap_row(r0 + tap * a.dil, a.in.rows) * a.in.chans + c);
     }
     xw[k] = activate(v4.x, a.act);
     xw[k + 1] = activate(v4.y, a.act);
@@ -456,7 +456,7 @@ __global__ void k_heads(const HeadsArgs a) {
 #pragma unroll
     for (int q = 0; q < 3; ++q)
       in[q] = reinterpret_cast<const float*>(base + a.in[q].off) +
-              ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans;
+              ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + a.in[q].choff;
     const uint64_t seed = a.batch.seeds[a.batch.slots[s]];
     const int32_t rf = a.out.f32.rows ? (int32_t)ring_row(t, a.out.f32.rows) : 0;
     const int32_t r0 = a.out.lp[0].rows ? (int32_t)ring_row(t, a.out.lp[0].rows) : 0;
@@ -501,7 +501,7 @@ __global__ void k_add(const AddArgs a) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const float* p = ring_ptr<const float>(a.batch, s, a.in[q]);
-      y += p[ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + c];
+      y += p[ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + a.in[q].choff + c];
     }
     store_views(a.batch, s, a.out, t, j, c, C, y);
   }

@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
       put(0, a.out.f32.off, a.out.f32.rows, a.out.f32.chans, 0, tb, 4);
       put(1, a.out.lp[0].off, a.out.lp[0].rows, a.out.lp[0].chans, a.out.lp[0].pre, tb, 2);
       put(2, a.out.lp[1].off, a.out.lp[1].rows, a.out.lp[1].chans, a.out.lp[1].pre, tb, 2);
-      put(3, a.skip.off, a.skip.rows, a.skip.chans, 0, tb - a.skip_A, 4);
+      put(3, a.skip.off + (int64_t)a.skip.choff * 4, a.skip.rows, a.skip.chans, 0, tb - a.skip_A, 4);
     }
     asm volatile("bar.sync 1, %0;" ::"n"(kEpi) : "memory");  // column table complete
     char* const arena = a.batch.arena;

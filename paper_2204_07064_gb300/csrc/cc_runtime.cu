@@ -187,6 +187,49 @@ static void plan_fusion(Model& m) {
   }
 }
 
+// Sibling tensor-core convolutions (stride 1, dilation 1) that read the same
+// input view and whose outputs are read in FP32 only run as one contraction:
+// M = the members' channels side by side (at most 128), the windows
+// right-aligned (a member with less history starts its taps later; the taps
+// in front of them are zero), one FP32 ring whose rows hold every member's
+// channels (each member's view points at its channels).
+static void plan_siblings(Model& m) {
+  if (!m.merge_siblings) return;
+  const int n = (int)m.nodes.size();
+  auto eligible = [&](const NodePlan& p) {
+    return p.d.op == CC_OP_CONV && p.engine == 1 && p.d.stride == 1 && p.d.dilation == 1 && p.fused_add < 0 &&
+           p.group_leader < 0 && !p.consumers.empty() && !p.used_view[1] && !p.used_view[2] &&
+           p.d.c_out % 8 == 0;
+  };
+  for (int i = 0; i < n; ++i) {
+    NodePlan& lead = m.nodes[i];
+    if (!eligible(lead)) continue;
+    std::vector<int> g{i};
+    int32_t ctot = lead.d.c_out;
+    for (int j = i + 1; j < n; ++j) {
+      const NodePlan& q = m.nodes[j];
+      if (!eligible(q) || q.d.inputs[0] != lead.d.inputs[0] || q.d.act_in != lead.d.act_in ||
+          q.d.c_in != lead.d.c_in || ctot + q.d.c_out > 128)
+        continue;
+      g.push_back(j);
+      ctot += q.d.c_out;
+    }
+    if (g.size() < 2) continue;
+    int32_t hist = 0, taps = 0;
+    for (int k : g) hist = std::max(hist, m.nodes[k].hist_need);
+    for (int k : g) taps = std::max(taps, hist - m.nodes[k].hist_need + m.nodes[k].d.kernel);
+    int32_t off = 0;
+    for (int k : g) {
+      m.nodes[k].group_leader = i;
+      m.nodes[k].choff = off;
+      off += m.nodes[k].d.c_out;
+    }
+    lead.group = g;
+    lead.group_taps = taps;
+    lead.group_hist = hist;
+  }
+}
+
 // Residual units on tensor cores: a stride-1 conv whose only consumer is a
 // 1x1 conv with a fused residual (and no history) run as one launch; the
 // intermediate never leaves the chip.  Both must fit one 128-row tile.
@@ -196,7 +239,7 @@ static void plan_units(Model& m) {
   for (int i = 0; i < n; ++i) {
     NodePlan& p = m.nodes[i];
     if (p.d.op != CC_OP_CONV || p.engine != 1 || p.d.stride != 1 || p.fused_add >= 0 ||
-        p.consumers.size() != 1)
+        p.consumers.size() != 1 || p.group_leader >= 0)
       continue;
     const int qi = p.consumers[0];
     NodePlan& q = m.nodes[qi];
@@ -217,6 +260,7 @@ static void plan_ksplit(Model& m) {
   for (auto& p : m.nodes) {
     p.ksplit = 1;
     if (p.engine != 1 || p.unit_next >= 0 || p.unit_fused) continue;
+    if (p.group_leader >= 0 && p.group_leader != (int)(&p - m.nodes.data())) continue;
     const int nk = p.Kt / 64, mt = p.Mpad / 128;
     const int64_t cols =
         (int64_t)m.max_streams * (p.d.op == CC_OP_CONVT ? m.nodes[p.d.inputs[0]].u : p.u);
@@ -249,6 +293,33 @@ static cc_status plan_arena(Model& m) {
     const bool needs_ring = !p.consumers.empty() && p.fused_add < 0;
     if (!needs_ring) continue;
     p.has_ring = true;
+    if (p.group_leader >= 0) {
+      // one FP32 ring for the sibling group, made when the leader comes by
+      NodePlan& lead = m.nodes[p.group_leader];
+      if (p.group_leader == i) {
+        int64_t rows = 0;
+        int32_t chans = 0;
+        for (int k : lead.group) {
+          const NodePlan& q = m.nodes[k];
+          rows = std::max(rows, (int64_t)q.keep_view[0] + (int64_t)q.u * m.max_steps);
+          chans += q.d.c_out;
+        }
+        if (rows >= (1ll << 30)) return fail(CC_ERR_NO_MEMORY, "ring of node %d too long", i);
+        Ring r{};
+        r.rows = (int32_t)rows;
+        r.chans = chans;
+        r.u = p.u;
+        r.dtype = kDtF32;
+        r.off = (int64_t)off;
+        off = align_up(off + (size_t)rows * chans * 4, 256);
+        lead.view[0] = r;
+      }
+      Ring r = lead.view[0];
+      r.choff = p.choff;
+      p.view[0] = r;
+      state += (size_t)p.keep_view[0] * p.d.c_out * 4;
+      continue;
+    }
     for (int v = 0; v < 3; ++v) {
       if (!p.used_view[v]) continue;
       Ring& r = p.view[v];
@@ -415,6 +486,42 @@ static cc_status pack_and_upload(Model& m, const float* const* weights, const fl
     if (d.has_bias && (!biases || !biases[i])) return fail(CC_ERR_INVALID_ARG, "node %d: missing bias", i);
     std::vector<float> A;
     const float* w = weights[i];
+    if (p.group_leader >= 0) {
+      if (p.group_leader != i) continue;  // computed by the leader
+      // [sum c_out][taps * c_in]: member k's tap j at merged tap j + (hist - hist_k)
+      int32_t M = 0;
+      for (int k : p.group) M += m.nodes[k].d.c_out;
+      p.taps = p.group_taps;
+      p.phases = 1;
+      p.M = M;
+      p.Kt = p.group_taps * d.c_in;
+      A.assign((size_t)p.M * p.Kt, 0.f);
+      std::vector<float> bias(M, 0.f);
+      bool any_bias = false;
+      for (int k : p.group) {
+        const NodePlan& q = m.nodes[k];
+        if (!weights[k]) return fail(CC_ERR_INVALID_ARG, "node %d: missing weights", k);
+        if (q.d.has_bias && (!biases || !biases[k])) return fail(CC_ERR_INVALID_ARG, "node %d: missing bias", k);
+        const int shift = p.group_hist - q.hist_need;
+        for (int o = 0; o < q.d.c_out; ++o) {
+          for (int c = 0; c < d.c_in; ++c)
+            for (int j = 0; j < q.d.kernel; ++j)
+              A[(size_t)(q.choff + o) * p.Kt + (size_t)(j + shift) * d.c_in + c] =
+                  weights[k][((size_t)o * d.c_in + c) * q.d.kernel + j];
+          if (q.d.has_bias) {
+            bias[q.choff + o] = biases[k][o];
+            any_bias = true;
+          }
+        }
+      }
+      cc_status s = upload_tc_operand(m, p, A);
+      if (s) return s;
+      if (any_bias) {
+        CC_CUDA(cudaMalloc(&p.dbias, M * sizeof(float)));
+        CC_CUDA(cudaMemcpy(p.dbias, bias.data(), M * sizeof(float), cudaMemcpyHostToDevice));
+      }
+      continue;
+    }
     if (d.op == CC_OP_CONV) {
       // trained [c_out][c_in][K] -> [c_out][K][c_in]: a K-slice is one tap
       p.taps = d.kernel;
@@ -518,6 +625,7 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
     }
     if (d.op == CC_OP_ADD && p.fused) continue;
     if (p.unit_fused) continue;  // computed by its producer's fused launch
+    if (p.group_leader >= 0 && p.group_leader != i) continue;  // computed by its group's leader
     // a fused residual unit writes the 1x1 conv's (and its fused add's) output
     const int qi = p.unit_next;
     const NodePlan* q = qi >= 0 ? &nodes[qi] : nullptr;
@@ -530,6 +638,7 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
     const int this_launch = launches++;
     made_at[i] = made_at[wi] = this_launch;
     if (q) made_at[qi] = this_launch;
+    for (int k : p.group) made_at[k] = this_launch;
     cc_status s = begin(i);
     if (s) return s;
     if (d.op == CC_OP_CONV || d.op == CC_OP_CONVT) {
@@ -548,9 +657,9 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
         a.cin = d.c_in;
         a.dil = dil;
         a.stride = stride;
-        a.hist = p.hist_need;
+        a.hist = p.group.empty() ? p.hist_need : p.group_hist;
         a.ncols = ncols;
-        a.cout = d.c_out;
+        a.cout = p.group.empty() ? d.c_out : p.M;
         a.phases = p.phases;
         a.out_u = w.u;
         a.in = src.view[1 + d.act_in];
@@ -865,11 +974,13 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
   m->max_steps = config->max_steps_per_call;
   m->noise = config->noise ? 1 : 0;
   m->fuse_units = (config->flags & CC_FLAG_NO_UNIT_FUSION) ? 0 : 1;
+  m->merge_siblings = (config->flags & CC_FLAG_NO_SIBLING_MERGE) ? 0 : 1;
   m->nodes.resize(n_nodes);
   for (int i = 0; i < n_nodes; ++i) m->nodes[i].d = nodes[i];
   cc_status s = cc::validate_and_analyze(*m);
   if (!s) {
     cc::plan_fusion(*m);
+    cc::plan_siblings(*m);
     s = cc::plan_arena(*m);
   }
   if (!s && m->max_streams == 0) {  // plan only: analysis queries, no device memory

@@ -52,6 +52,12 @@ struct NodePlan {
   int32_t in_rows_per_slot = 0, in_row_off = 0;
   int32_t ksplit = 1;  // tensor-core split-K factor, fixed per layer (batch-independent numerics)
   int32_t unit_next = -1;  // this conv and the 1x1 conv (node unit_next) run as one launch
+  // sibling group: stride-1 tensor-core convs sharing their input, computed by
+  // one contraction of the leader; members' FP32 views share one ring
+  int32_t group_leader = -1;
+  int32_t choff = 0;                 // (member) first channel in the group's ring
+  std::vector<int> group;            // (leader) members, leader first
+  int32_t group_taps = 0, group_hist = 0;  // (leader) merged window
   bool unit_fused = false;  // (1x1 conv) computed by its producer's fused launch
   std::map<int64_t, int32_t> tile_n;  // autotuned N tile by launch width (columns), 0: heuristic
 };
@@ -66,6 +72,7 @@ struct Model {
   int32_t lp_dtype = kDtBF16;  // element type of low-precision views
   int32_t max_streams = 0, max_steps = 1, noise = 1;
   int32_t fuse_units = 1;  // residual units (k-wide conv -> 1x1 conv) as one tensor-core launch
+  int32_t merge_siblings = 1;  // tensor-core convs sharing their input as one contraction
   int32_t in_per_step = 1;
   std::vector<NodePlan> nodes;
   size_t slot_bytes = 0, state_bytes = 0, weight_bytes = 0;

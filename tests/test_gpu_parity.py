@@ -347,3 +347,33 @@ def test_fused_residual_units_equal_unfused(cclib, cuda, count):
     k = count // 3
     ref = M.run_causal(dec, p, z[:, k, 0, :], seed=seeds[k])[:, 0]
     _assert_lowp(outs[0][k], ref, f"bf16 fused units, stream {k} of {count}")
+
+
+def test_merged_sibling_convs_equal_separate(cclib, cuda):
+    """The decoder's three head convolutions (k = 7, 3, 3, all reading
+    LeakyReLU(h)) run as one tensor-core contraction with right-aligned
+    windows (zero taps in front of the shorter kernels) and their FP32 outputs
+    side by side in one ring; adding exact zeros leaves every sum unchanged,
+    so the outputs equal those of three separate launches.  Checked with a
+    partial last tile (250 streams) and against the oracle for one stream."""
+    import torch
+
+    dec, p = _decoder(13)
+    count, steps = 250, 4
+    seeds = W.stream_seeds(31, count)
+    z = np.random.default_rng(7).standard_normal((steps, count, 1, 128))
+    outs = []
+    for merge in (True, False):
+        model = api.Model(dec, p, dtype="bf16", max_streams=count, max_steps_per_call=1, merge_siblings=merge)
+        streams = [model.stream(seed=s) for s in seeds]
+        y = torch.empty((count, 2048, 1), dtype=torch.float32, device=cuda)
+        o = np.zeros((count, steps * 2048))
+        for t in range(steps):
+            model.process_batch(streams, torch.tensor(z[t], dtype=torch.float32, device=cuda), y)
+            o[:, t * 2048:(t + 1) * 2048] = y[:, :, 0].cpu().numpy()
+        assert model.device_status() == 0
+        outs.append(o)
+        model.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+    ref = M.run_causal(dec, p, z[:, 99, 0, :], seed=seeds[99])[:, 0]
+    _assert_lowp(outs[0][99], ref, "bf16 merged heads, stream 99 of 250")

@@ -319,8 +319,8 @@ def test_lowp_window_boxes_match_gathers(cclib, cuda):
     _assert_lowp(outs[0][31], ref, "bf16 stream 31 of 50, 40 steps")
 
 
-@pytest.mark.parametrize("count", [256, 250])
-def test_fused_residual_units_equal_unfused(cclib, cuda, count):
+@pytest.mark.parametrize("count,dtype", [(256, "bf16"), (250, "bf16"), (250, "f16")])
+def test_fused_residual_units_equal_unfused(cclib, cuda, count, dtype):
     """A residual unit (k=3 conv -> 1x1 conv + skip) with at most 128 channels
     runs as one tensor-core launch, its intermediate rounded to BF16 in
     shared memory exactly as the unfused path rounds it into its ring: the two
@@ -333,7 +333,7 @@ def test_fused_residual_units_equal_unfused(cclib, cuda, count):
     z = np.random.default_rng(6).standard_normal((steps, count, 1, 128))
     outs = []
     for fuse in (True, False):
-        model = api.Model(dec, p, dtype="bf16", max_streams=count, max_steps_per_call=1, fuse_units=fuse)
+        model = api.Model(dec, p, dtype=dtype, max_streams=count, max_steps_per_call=1, fuse_units=fuse)
         streams = [model.stream(seed=s) for s in seeds]
         y = torch.empty((count, 2048, 1), dtype=torch.float32, device=cuda)
         o = np.zeros((count, steps * 2048))
@@ -346,7 +346,7 @@ def test_fused_residual_units_equal_unfused(cclib, cuda, count):
     np.testing.assert_array_equal(outs[0], outs[1])
     k = count // 3
     ref = M.run_causal(dec, p, z[:, k, 0, :], seed=seeds[k])[:, 0]
-    _assert_lowp(outs[0][k], ref, f"bf16 fused units, stream {k} of {count}")
+    _assert_lowp(outs[0][k], ref, f"{dtype} fused units, stream {k} of {count}")
 
 
 def test_merged_sibling_convs_equal_separate(cclib, cuda):

@@ -152,6 +152,60 @@ def run_differentiate(args):
     model.close()
 
 
+def throughput_at(batch, steps=10, warmup=3):
+    """Real-time streams at `batch` streams (BF16 decoder, one 2048-sample
+    buffer per step), the step captured as a CUDA graph of one launch chain
+    per 256 streams, timed with CUDA events over `steps` steps."""
+    import torch
+
+    from paper_2204_07064_gb300 import workloads as W
+
+    _, _, model = build_decoder("bf16", batch)
+    ss = [model.stream(seed=s) for s in W.stream_seeds(77, batch)]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    z = torch.randn((warmup + steps, batch, 1, 128), device=dev)
+    x_in = torch.empty_like(z[0])
+    y = torch.empty((batch, 2048, 1), device=dev)
+    nsub = default_sub_batches("bf16", batch)
+    bounds = [round(k * batch / nsub) for k in range(nsub + 1)]
+    side = [torch.cuda.Stream() for _ in range(nsub)]
+
+    def launch(main):
+        fork = torch.cuda.Event()
+        fork.record(main)
+        for k in range(nsub):
+            side[k].wait_event(fork)
+            model.process_batch(ss[bounds[k]:bounds[k + 1]], x_in[bounds[k]:bounds[k + 1]],
+                                y[bounds[k]:bounds[k + 1]], cuda_stream=side[k])
+        for k in range(nsub):
+            main.wait_stream(side[k])
+
+    st = torch.cuda.current_stream()
+    for i in range(warmup):
+        x_in.copy_(z[i])
+        launch(st)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream()
+    cap.wait_stream(st)
+    with torch.cuda.graph(graph, stream=cap, capture_error_mode="relaxed"):
+        launch(cap)
+    st.wait_stream(cap)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for i in range(steps):
+        x_in.copy_(z[warmup + i])
+        graph.replay()
+    e1.record(st)
+    torch.cuda.synchronize()
+    model.device_status()
+    ms = e0.elapsed_time(e1) / steps
+    del graph
+    model.close()
+    return batch * 2048 / (ms / 1000.0) / SR, ms
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
 
@@ -619,6 +673,18 @@ def main():
                     "ms_per_step": ms32, "dtype": "f32", "speedup_lowp_over_fp32": (ms32 / (total_ms / args.steps))}
         model32.close()
 
+    # the same decoder at larger batches (one chain per 256 streams): where the
+    # step stops being latency-bound
+    by_batch = None
+    if dtype != "f32" and streams == 256 and world == 1:
+        by_batch = {}
+        fl = sum(node_flops(nodes[i], info_u[i]) for i in conv_nodes)  # per stream-step
+        for b in (1024, 2048):
+            v, ms_b = throughput_at(b)
+            tf = v * SR / 2048 * fl / 1e12
+            by_batch[str(b)] = {"value": v, "unit": "streams", "ms_per_step": ms_b,
+                                "achieved_tflops": tf, "frac_of_bf16_peak": tf / pk.get("bf16_tflops", 1900.0)}
+
     step_sorted = sorted(step_ms)
     p50 = float(np.percentile(step_ms, 50))
     p99 = float(np.percentile(step_ms, 99))
@@ -634,6 +700,7 @@ def main():
                    "l2": "flushed between steps" if flush is not None else
                    "working set per step > L2 (arena + weights)",
                    "samples_per_s": samples / (total_ms / 1000.0)},
+        "throughput_by_batch": by_batch,
         "latency_ms": {"p50": p50, "p99": p99, "max": step_sorted[-1],
                        "buffer_ms": 2048 * frames / SR * 1000.0,
                        "meets_deadline": p99 < 2048 * frames / SR * 1000.0},

@@ -149,7 +149,14 @@ def _desc(node):
 
 
 class Model:
-    """A reconfigured model on the GPU: packed weights + stream-state arena."""
+    """A reconfigured model on the GPU: packed weights + stream-state arena.
+
+    dtype "f32" runs FFMA kernels; "bf16" / "f16" run the contractions with
+    cin % 64 == 0 on the tensor cores.  max_streams sizes the arena (0: plan
+    only); max_steps_per_call is the longest launch chain (longer buffers are
+    split).  fuse_units / merge_siblings = False launch each convolution of a
+    residual unit, and each sibling conv, on its own (identical results; for
+    comparisons)."""
 
     def __init__(self, nodes, params, dtype="f32", max_streams=1, max_steps_per_call=1, noise=True,
                  fuse_units=True, merge_siblings=True):

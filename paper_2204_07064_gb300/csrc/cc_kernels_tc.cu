@@ -17,16 +17,15 @@
 //              copies, so every stage can be in flight
 //   warp 1     TMEM allocation; lane 0 issues tcgen05.mma (128 x BN x 16,
 //              BF16 or FP16 operands, FP32 accumulation in TMEM)
-//   warps 2-   epilogue (8 or 16 warps): warp w owns accumulator rows
-//              32*(w%4) .. +31 (its TMEM lane quarter) and every EW/4-th
-//              group of 8 columns (the warps of a quarter alternate); per
-//              group it loads the rows
-//              (tcgen05.ld), applies scale and bias, turns the 32 x 8 block
-//              around in 1 KB of shared memory so that each lane holds 8
-//              consecutive channels of one column, adds the aligned residual
-//              (16-byte loads) and stores every view with 16-byte stores, at
-//              ring addresses from a per-column table built before the
-//              kernel waits on its predecessor
+//   warps 2..  epilogue (EW = 8 or 16 warps): warp w owns accumulator rows
+//              32*(w%4) .. +31 (its TMEM lane quarter) and every (EW/4)-th
+//              group of 8 columns (the warps of a quarter interleave); per
+//              group it loads the rows (tcgen05.ld), applies scale and bias,
+//              turns the 32 x 8 block around in 1 KB of shared memory so that
+//              each lane holds 8 consecutive channels of one column, adds the
+//              aligned residual (16-byte loads) and stores every view with
+//              16-byte stores, at ring addresses from a per-column table built
+//              before the kernel waits on its predecessor
 // Residual-unit fusion (FUSE): a k-wide conv and the 1x1 conv that consumes
 // only it run as one launch.  The first epilogue writes the scaled, biased,
 // activated first result in BF16/FP16 straight into shared memory in the
@@ -40,8 +39,8 @@
 // finishes columns [z, z+1) * BN/ksplit.  Each CTA pushes its partial sums of
 // the other CTAs' columns into their shared memory (distributed shared-memory
 // stores); after one cluster barrier, each CTA adds its own partial (TMEM) and
-// the received ones in the fixed order z = 0, 1, ...  The split is a property of the layer, so a stream's result
-// does not depend on the batch it runs in.
+// the received ones in the fixed order z = 0, 1, ...  The split is a property
+// of the layer, so a stream's result does not depend on the batch it runs in.
 // Every mbarrier wait is bounded in time and records an error in the model's
 // device error word instead of hanging.
 //
@@ -64,15 +63,16 @@ namespace {
 using namespace sm100;
 
 constexpr int kBM = 128;
-// producer warp, MMA warp, EW epilogue warps (8, or 16 for the one-CTA-per-SM
-// variants, whose epilogue has the SM to itself)
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s
 
-// Pipeline depth: 128-column tiles run 6 stages when the grid fits in one wave
-// and the model expects no concurrent launch chains (one CTA per SM: few CTAs
-// with long K loops need deep prefetch) or the layer is split; else 3 stages
-// (two CTAs per SM, whose epilogues overlap each other's main loops and other
-// chains' kernels); 256-column tiles use 4 stages.
+// Variants (launch_conv_tc): threads = producer warp + MMA warp + EW epilogue
+// warps.  128-column tiles run 6 stages and 16 epilogue warps (one CTA per SM:
+// few CTAs with long K loops need deep prefetch, and the epilogue has the SM
+// to itself) when the grid fits in one wave and the model expects no
+// concurrent launch chains; else 3 stages and 8 epilogue warps (two CTAs per
+// SM, whose epilogues overlap each other's main loops and other chains'
+// kernels).  Split layers run 4 stages with a receive buffer; fused units 4
+// or 2 stages with the second operand; 256-column tiles 4 stages.
 template <int BN, int STAGES, bool FUSE, int EW, bool SPLIT = false>
 struct TcLayout {
   static constexpr int kThreads = 64 + 32 * EW;
@@ -529,14 +529,6 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
       const bool has_skip = a.has_skip != 0;
       char* const f_base = arena + (int64_t)ch_l * 4;
       char* const l_base = arena + (int64_t)ch_l * 2;
-      auto pack = [&](float lo, float hi) -> uint32_t {
-        if (l_bf16) {
-          const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-          return *reinterpret_cast<const uint32_t*>(&h);
-        }
-        const __half2 h = __floats2half2_rn(lo, hi);
-        return *reinterpret_cast<const uint32_t*>(&h);
-      };
 #pragma unroll 1
       for (int cb = c_lo; cb < c_lo + c_n; cb += 32) {
         if (n0 + cb >= N) break;  // uniform over the CTA
@@ -614,7 +606,8 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
             float y[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) y[i] = q ? leaky(x[i]) : x[i];
-            const uint4 pk = make_uint4(pack(y[0], y[1]), pack(y[2], y[3]), pack(y[4], y[5]), pack(y[6], y[7]));
+            const uint4 pk = make_uint4(pack2(y[0], y[1], l_bf16), pack2(y[2], y[3], l_bf16),
+                                        pack2(y[4], y[5], l_bf16), pack2(y[6], y[7], l_bf16));
             uint32_t o = __shfl_sync(0xffffffffu, q ? lo1 : lo0, src);
             uint32_t om = __shfl_sync(0xffffffffu, q ? lm1 : lm0, src);
             if (phased) {

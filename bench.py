@@ -39,7 +39,7 @@ def default_sub_batches(dtype, streams):
 # DRAM bytes (read + write) per tensor-core launch, from one ncu capture of
 # the 32 contractions of a step of this exact workload and kernel version
 # (profiles/k_conv_tc_decoder_bf16_b256.md); null for any other workload.
-TC_TRAFFIC_PER_LAUNCH = {"decoder-bf16-b256": 6.66e6}
+TC_TRAFFIC_PER_LAUNCH = {"decoder-bf16-b256": 6.62e6}
 
 WORKLOADS = {
     # name: (dtype, streams, buffer latent frames)

@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
       prefetch_skip();
       load_skip(c_lo, half, so_next, sr_next);
     }
-    // one verdict for all epilogue threads (a reduction barrier), so the
+    // one outcome for all epilogue threads (a reduction barrier), so the
     // named barriers stay matched
     const bool waited = mbar_wait(tfull, 0, kWaitNs);
     uint32_t all_ok;

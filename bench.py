@@ -37,7 +37,7 @@ def default_sub_batches(dtype, streams):
     return 1 if dtype == "f32" else max(1, streams // 256)
 
 # DRAM bytes (read + write) per tensor-core launch, from one ncu capture of
-# the 32 contractions of a step of this exact workload and kernel version
+# the 24 tensor-core launches of a step of this exact workload and kernel version
 # (profiles/k_conv_tc_decoder_bf16_b256.md); null for any other workload.
 TC_TRAFFIC_PER_LAUNCH = {"decoder-bf16-b256": 6.62e6}
 
@@ -152,7 +152,7 @@ def run_differentiate(args):
     model.close()
 
 
-def throughput_at(batch, steps=10, warmup=3):
+def throughput_at(batch, steps=200, warmup=3):
     """Real-time streams at `batch` streams (BF16 decoder, one 2048-sample
     buffer per step), the step captured as a CUDA graph of one launch chain
     per 256 streams, timed with CUDA events over `steps` steps."""
@@ -207,27 +207,57 @@ def throughput_at(batch, steps=10, warmup=3):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 50 ms.  Each row is
+    time-stamped by nvidia-smi; `stop(window)` keeps the rows that fall inside
+    the given wall-clock window (the timed region)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.lines = []
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.proc = None
 
-    def stop(self):
+    @staticmethod
+    def parse(out, window=None):
+        """Summary of nvidia-smi rows; with `window` = (t0, t1) in time.time()
+        seconds, only the rows stamped inside it."""
+        import datetime
+        sm, mx, reasons, n_all = [], 0.0, set(), 0
+        for line in out.strip().splitlines():
+            r = [f.strip() for f in line.split(",")]
+            try:
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                mhz, mhz_max = float(r[2]), float(r[3])
+            except (ValueError, IndexError):
+                continue
+            n_all += 1
+            if window is not None and not (window[0] <= ts <= window[1]):
+                continue
+            sm.append(mhz)
+            mx = max(mx, mhz_max)
+            for name, v in zip(ClockSampler.REASONS, r[6:10]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "samples_total": n_all,
+                    "note": "no sample fell inside the timed region"} if n_all else None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm), "samples_total": n_all}
+
+    def stop(self, window=None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -236,27 +266,13 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        rows = [l.split(",") for l in out.strip().splitlines() if l.strip()]
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            try:
-                sm.append(float(r[1]))
-                mx = max(mx, float(r[2]))
-                for name, v in zip(names, r[5:9]):
-                    if v.strip().lower() == "active":
-                        reasons.add(name)
-            except (ValueError, IndexError):
-                continue
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return self.parse(out, window)
 
 
-def oracle_sample(steps, seed=1, stream_seed=11):
-    """FP64 oracle streaming of the same decoder, one stream, `steps` buffers.
-    Runs in a subprocess with one BLAS thread; returns audio seconds / wall."""
+def oracle_sample(steps, seed=1, stream_seed=11, warmup=1):
+    """FP64 oracle streaming of the same decoder, one stream: `warmup` untimed
+    buffers, then `steps` timed buffers (one wall time each).  Runs in a
+    subprocess with one BLAS thread; returns audio seconds / wall."""
     code = f"""
 import os, sys, time, json
 sys.path.insert(0, {ROOT!r})
@@ -266,18 +282,20 @@ from paper_2204_07064_gb300 import workloads as W
 nodes = W.rave_decoder(); p = W.init_params(nodes, {seed})
 _, g, _, _ = pqmf.design(16, 64)
 p[W.pqmf_node_index(nodes)] = (pqmf.synthesis_weights(g), None)
-z = W.signal(5, {steps}, 128)
+z = W.signal(5, {warmup} + {steps}, 128)
 s = M.Stream(nodes, p, seed={stream_seed})
-s.process(z[:1])
-t = time.perf_counter()
-for i in range({steps}):
+for i in range({warmup}):
     s.process(z[i:i + 1])
-wall = time.perf_counter() - t
-print(json.dumps({{"wall": wall, "audio_s": {steps} * 2048 / {SR}}}))
+walls = []
+for i in range({warmup}, {warmup} + {steps}):
+    t = time.perf_counter()
+    s.process(z[i:i + 1])
+    walls.append(time.perf_counter() - t)
+print(json.dumps({{"wall": sum(walls), "walls": walls, "audio_s": {steps} * 2048 / {SR}}}))
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                       timeout=600)
+                       timeout=max(600.0, 0.5 * (steps + warmup)))
     if r.returncode != 0:
         raise RuntimeError(r.stderr)
     d = json.loads(r.stdout.strip().splitlines()[-1])
@@ -290,24 +308,19 @@ def run_reference(args):
     if rank != 0:
         return
     dtype, streams, frames = WORKLOADS[args.workload]
-    for _ in range(args.warmup):
-        oracle_sample(1)
-    vals = []
-    walls = []
-    for _ in range(args.steps):
-        v, d = oracle_sample(2)
-        vals.append(v)
-        walls.append(d["wall"] / 2)
-    value = statistics.mean(vals)
+    # one process; each step is one 2048-sample buffer of one stream
+    value, d = oracle_sample(args.steps, warmup=args.warmup)
+    walls = d["walls"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "streams",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * statistics.mean(walls), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "streams": streams, "buffer_samples": 2048 * frames,
-                   "note": "oracle timed on 1 stream x 2 buffers per step (bounded sample)"},
+                   "note": "oracle timed on 1 stream x 1 buffer per step (bounded sample)"},
         "cpu_baseline": {"value": value, "unit": "streams", "cores": 1, "kind": "oracle",
-                         "sample": "1 stream x 2 buffers of 2048 samples per step, FP64 NumPy, 1 BLAS thread"},
+                         "sample": f"1 stream x 1 buffer of 2048 samples per step, {args.steps} steps, "
+                                   f"FP64 NumPy, 1 BLAS thread ({d['wall']:.1f} s)"},
         "e2e": {"value": value, "unit": "streams", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -371,6 +384,7 @@ def run_serving(args):
         if not sampled and now >= t_meas:
             clocks.start()
             sampled = True
+            wall_meas = time.time()
         dt = (now - last) / 1e9
         last = now
         if not args.serve_fixed:
@@ -428,7 +442,7 @@ def run_serving(args):
         if now >= t_meas:
             conc.append(int(active.sum()))
         time.sleep(0.0005)
-    clk = clocks.stop() if sampled else None
+    clk = clocks.stop((wall_meas, time.time())) if sampled else None
     st = server.stats()
     server.close()
     lat = np.asarray(lat)
@@ -464,7 +478,7 @@ def run_serving(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
@@ -517,8 +531,7 @@ def main():
     ss = [model.stream(seed=s) for s in seeds]
     rng = np.random.default_rng(rank)
     steps_total = args.warmup + args.steps
-    z = torch.tensor(rng.standard_normal((steps_total, streams, frames, 128)), dtype=torch.float32,
-                     device=dev)
+    z = torch.from_numpy(rng.standard_normal((steps_total, streams, frames, 128), dtype=np.float32)).to(dev)
     y = torch.empty((streams, 2048 * frames, 1), dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if args.flush_l2 else None
     st = torch.cuda.current_stream()
@@ -580,6 +593,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    wall0 = time.time()
     for k in range(args.steps):
         if flush is not None:
             flush.zero_()
@@ -587,15 +601,18 @@ def main():
         step(args.warmup + k)
         ends[k].record(st)
     torch.cuda.synchronize()
+    wall1 = time.time()
     if dist:
         dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop((wall0, wall1))
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
-    # the same K steps again with the library's per-launch events (kernel
-    # durations for the roofline; kept out of the headline timing)
+    # the first K2 = min(K, 500) of those steps again with the library's
+    # per-launch events (kernel durations for the roofline; kept out of the
+    # headline timing); the e2e and FP32 passes below run K2 steps as well
+    k2 = min(args.steps, 500)
     model.timing(True)
-    for k in range(args.steps):
+    for k in range(k2):
         if flush is not None:
             flush.zero_()
         model.process_batch(ss, z[args.warmup + k], y)
@@ -619,15 +636,15 @@ def main():
     zh = torch.empty((streams, frames, 128), dtype=torch.float32).pin_memory()
     zh.copy_(z[0].cpu())
     yh = torch.empty((streams, 2048 * frames, 1), dtype=torch.float32).pin_memory()
-    e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    for k in range(args.steps):
+    e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(k2)]
+    e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(k2)]
+    for k in range(k2):
         e_starts[k].record(st)
         model.process_batch(ss, zh, yh)
         e_ends[k].record(st)
         e_ends[k].synchronize()
     e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_starts, e_ends))
-    e2e_value = streams * 2048 * frames * args.steps * world / (e2e_ms / 1000.0) / SR
+    e2e_value = streams * 2048 * frames * k2 * world / (e2e_ms / 1000.0) / SR
 
     # roofline of the dominant kernel class (the contractions)
     info_u = [model.node_info(i)["frames_per_step"] for i in range(len(nodes))]
@@ -637,7 +654,7 @@ def main():
     conv_launches = sum(node_launches[i] for i in conv_nodes)
     pk, pk_kind = peaks()
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    achieved = flops * args.steps / (conv_ms / 1000.0) / 1e12 if conv_ms > 0 else 0.0
+    achieved = flops * k2 / (conv_ms / 1000.0) / 1e12 if conv_ms > 0 else 0.0
     if dtype == "f32":
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
@@ -664,11 +681,11 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        for k in range(args.steps):
+        for k in range(k2):
             model32.process_batch(ss32, z[args.warmup + k], y)
         e1.record(st)
         torch.cuda.synchronize()
-        ms32 = e0.elapsed_time(e1) / args.steps
+        ms32 = e0.elapsed_time(e1) / k2
         fp32_cmp = {"value": streams * 2048 * frames * world / (ms32 / 1000.0) / SR, "unit": "streams",
                     "ms_per_step": ms32, "dtype": "f32", "speedup_lowp_over_fp32": (ms32 / (total_ms / args.steps))}
         model32.close()
@@ -688,7 +705,7 @@ def main():
     step_sorted = sorted(step_ms)
     p50 = float(np.percentile(step_ms, 50))
     p99 = float(np.percentile(step_ms, 99))
-    launches_per_step = (sum(node_launches) / args.steps) + 1  # + the step-counter advance
+    launches_per_step = (sum(node_launches) / k2) + 1  # + the step-counter advance
     line = {
         "metric": METRIC, "value": value, "unit": "streams", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

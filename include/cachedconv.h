@@ -153,8 +153,34 @@ cc_status cc_model_state_bytes(const cc_model* model, size_t* state_bytes, size_
 cc_status cc_stream_create(cc_model* model, uint64_t seed, void* cuda_stream, cc_stream** out);
 cc_status cc_stream_destroy(cc_stream* stream);
 
-/* Zero the stream's caches and its step counter (enqueued on cuda_stream). */
+/* Zero the stream's caches and its step counter and restore the identity
+ * input manipulation (below); waits for cuda_stream. */
 cc_status cc_stream_reset(cc_stream* stream, void* cuda_stream);
+
+/* Latent manipulation (section 5.1, Fig. 7; section 5.2): from the stream's
+ * next model step on, every input frame x (input frame index t, counted from
+ * the stream's start) enters the model as
+ *   x'[c] = scale[c] * x[c] + bias[c] + noise[c] * u(t, c)
+ * inside the kernel that writes the input into the stream's caches (two FP32
+ * fused multiply-adds).  For a decoder the input is the latent: bias[c]
+ * shifts dimension c, scale[c] = 0 with bias[c] = v replaces it by v, and
+ * noise[c] adds uniform noise of that amplitude.  u(t, c) in [-1, 1) is the
+ * SplitMix64 draw with counter t * channels + c from the generator seeded
+ * with (stream seed XOR 0x6C6174656E742D6E), the same counter-based draw as
+ * the heads' noise in a separate seed domain, so streamed and offline runs
+ * see the same noise.  scale, bias and noise are host arrays of `channels`
+ * floats (must equal the model's input channels; NULL means all 1 / 0 / 0;
+ * values must be finite, else CC_ERR_INVALID_ARG).  They are copied to the
+ * stream's slot with an asynchronous copy on cuda_stream, and the call
+ * returns once the copy has completed: steps enqueued on cuda_stream after
+ * the call, or on any stream after it returns, see the new values.  (With a
+ * cc_server, call it while the stream has no request outstanding.)  A stream
+ * starts with the identity (1, 0, 0) and cc_stream_reset restores it;
+ * cc_stream_get_state does not carry it.  The hand-written backward does not
+ * differentiate through a manipulation: cc_backward_begin and
+ * cc_backward_chunk return CC_ERR_STATE for a stream that has one. */
+cc_status cc_stream_set_input_manipulation(cc_stream* stream, const float* scale, const float* bias,
+                                           const float* noise, int32_t channels, void* cuda_stream);
 
 /* Process one buffer: n_in input frames ([n_in][in_channels]) -> n_out output
  * frames ([n_out][out_channels]).  n_in must be a multiple of in_per_step and

@@ -19,6 +19,8 @@ plain, slow, obviously-correct restatement of the paper (Caillon & Esling,
 * ``noise``  SplitMix64 (Steele, Lea & Flood 2014) as a counter-based
              generator for the deterministic noise branch.
 * ``metrics`` Eq. 4 / Eq. 5 distances and the SNR / max-abs checks.
+* ``manipulate`` per-dimension scale, bias and noise of the model input
+             (latent manipulation, sections 5.1 and 5.2).
 
 All floating point is numpy float64.
 """

@@ -59,6 +59,7 @@ _SIGNATURES = {
     "cc_stream_create": [_P, _U64, _P, C.POINTER(_P)],
     "cc_stream_destroy": [_P],
     "cc_stream_reset": [_P, _P],
+    "cc_stream_set_input_manipulation": [_P, _P, _P, _P, _I32, _P],
     "cc_stream_process": [_P, _P, _I64, _P, _I64, _P],
     "cc_process_batch": [_P, C.POINTER(_P), _I32, _P, _I64, _I64, _P, _I64, _I64, _P],
     "cc_stream_state_size": [_P, C.POINTER(_SZ)],
@@ -277,6 +278,18 @@ class Stream:
 
     def reset(self, cuda_stream=None):
         _check(lib().cc_stream_reset(self.handle, _cuda_stream(cuda_stream)))
+
+    def set_input_manipulation(self, scale=None, bias=None, noise=None, cuda_stream=None):
+        """Latent manipulation: from the next step on, input frames enter the
+        model as scale * x + bias + noise * u per channel, u a seeded uniform
+        draw in [-1, 1) (None: 1 / 0 / 0; scalars broadcast).  Replace channel
+        c by v with scale[c] = 0, bias[c] = v."""
+        n = self.model.io["in_channels"]
+        arrs = [None if v is None else np.ascontiguousarray(np.broadcast_to(v, (n,)), dtype=np.float32)
+                for v in (scale, bias, noise)]
+        ptrs = [None if a is None else a.ctypes.data for a in arrs]
+        _check(lib().cc_stream_set_input_manipulation(self.handle, ptrs[0], ptrs[1], ptrs[2], n,
+                                                      _cuda_stream(cuda_stream)))
 
     def get_state(self, cuda_stream=None):
         n = _SZ()

@@ -27,6 +27,7 @@
 
 namespace cc {
 int32_t stream_slot(const cc_stream* s);
+bool stream_manipulated(const cc_stream* s);
 Model* stream_model(const cc_stream* s);
 }  // namespace cc
 
@@ -365,6 +366,8 @@ cc_status cc_backward_begin(cc_grads* g, cc_stream* const* streams, int32_t coun
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   for (int32_t i = 0; i < count; ++i) {
     if (!streams[i] || cc::stream_model(streams[i]) != g->m) return cc::fail(CC_ERR_INVALID_ARG, "stream %d", i);
+    if (cc::stream_manipulated(streams[i]))
+      return cc::fail(CC_ERR_STATE, "stream %d has an input manipulation; the backward does not differentiate it", i);
     const cudaError_t e = cudaMemsetAsync(g->adj + (size_t)cc::stream_slot(streams[i]) * g->m->slot_bytes, 0,
                                           g->m->slot_bytes, st);
     if (e != cudaSuccess) return cc::fail(CC_ERR_CUDA, "adjoint reset: %s", cudaGetErrorString(e));
@@ -394,6 +397,8 @@ cc_status cc_backward_chunk(cc_grads* g, cc_stream* const* streams, int32_t coun
   BW_CUDA(cudaEventSynchronize(g->upload_done));
   for (int32_t i = 0; i < count; ++i) {
     if (!streams[i] || cc::stream_model(streams[i]) != m) return fail(CC_ERR_INVALID_ARG, "stream %d", i);
+    if (cc::stream_manipulated(streams[i]))
+      return fail(CC_ERR_STATE, "stream %d has an input manipulation; the backward does not differentiate it", i);
     g->h_slots[i] = cc::stream_slot(streams[i]);
   }
   BW_CUDA(cudaMemcpyAsync(g->d_slots, g->h_slots, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));

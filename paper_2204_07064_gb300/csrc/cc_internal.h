@@ -132,8 +132,9 @@ struct AddArgs {
 };
 
 struct InputArgs {
-  const float* src;    // count x [ncols][C]
-  int64_t src_stride;  // floats between streams
+  const float* src;     // count x [ncols][C]
+  int64_t src_stride;   // floats between streams
+  const float* manip;   // [max_streams][3][C] by slot: scale, bias, noise-amplitude rows
   int32_t ncols, chans, out_u;
   OutViews out;
   Batch batch;

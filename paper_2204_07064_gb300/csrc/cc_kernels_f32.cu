@@ -437,6 +437,14 @@ __device__ __forceinline__ float noise_uniform(uint64_t seed, int64_t frame, int
   return (float)(z >> 40) * 0x1p-23f - 1.0f;
 }
 
+// Input-manipulation noise: the same uniform draw, from the generator whose
+// seed is the stream seed XOR kInputNoiseTag (a domain apart from the heads'
+// noise), counter = frame * channels + channel over input frames.
+constexpr uint64_t kInputNoiseTag = 0x6C6174656E742D6Eull;
+__device__ __forceinline__ float input_noise(uint64_t seed, int64_t frame, int32_t c, int32_t channels) {
+  return noise_uniform(seed ^ kInputNoiseTag, frame, c, channels);
+}
+
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 // One thread per (stream, frame): the ring rows of the three branches and of
@@ -519,7 +527,15 @@ __global__ void k_input(const InputArgs a) {
     const int32_t j = (int32_t)(nj % a.ncols);
     const int32_t s = (int32_t)(nj / a.ncols);
     const int64_t t = steps_of(a.batch, s) * a.out_u + j;
-    store_views(a.batch, s, a.out, t, j, c, C, a.src[(int64_t)s * a.src_stride + (int64_t)j * C + c]);
+    // the stream's input manipulation x' = scale * x + bias + amp * u(t, c)
+    // (the identity 1, 0, 0 leaves x unchanged)
+    const int32_t slot = a.batch.slots[s];
+    const float* mp = a.manip + (int64_t)slot * 3 * C;
+    const float x = a.src[(int64_t)s * a.src_stride + (int64_t)j * C + c];
+    float v = fmaf(mp[c], x, mp[C + c]);
+    const float amp = mp[2 * C + c];
+    if (amp != 0.f) v = fmaf(amp, input_noise(a.batch.seeds[slot], t, c, C), v);
+    store_views(a.batch, s, a.out, t, j, c, C, v);
   }
 }
 

@@ -612,6 +612,7 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
       InputArgs a{};
       a.src = in;
       a.src_stride = in_stride;
+      a.manip = in_manip;
       a.ncols = p.u * steps;
       a.chans = d.c_out;
       a.out_u = p.u;
@@ -912,6 +913,7 @@ Model::~Model() {
   if (arena) cudaFree(arena);
   if (counters) cudaFree(counters);
   if (seeds) cudaFree(seeds);
+  if (in_manip) cudaFree(in_manip);
   for (auto& kv : slot_lists) {
     if (kv.second.d) cudaFree(kv.second.d);
     if (kv.second.h) cudaFreeHost(kv.second.h);
@@ -934,10 +936,12 @@ struct cc_stream {
   int32_t slot;
   uint64_t seed;
   int32_t* d_slot;
+  bool manip_set = false;  // a non-identity input manipulation is in place
 };
 
 namespace cc {
 int32_t stream_slot(const cc_stream* s) { return s->slot; }
+bool stream_manipulated(const cc_stream* s) { return s->manip_set; }
 Model* stream_model(const cc_stream* s) { return s->model; }
 }  // namespace cc
 
@@ -1004,8 +1008,10 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
     }
   }
   if (!s) s = cc::encode_gather_maps(*m);
+  const size_t manip_floats = (size_t)3 * m->nodes.front().d.c_out * m->max_streams;
   if (!s && (cudaMalloc(&m->counters, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
              cudaMalloc(&m->seeds, sizeof(uint64_t) * m->max_streams) != cudaSuccess ||
+             cudaMalloc(&m->in_manip, sizeof(float) * manip_floats) != cudaSuccess ||
 
              cudaMalloc(&m->err, sizeof(int32_t)) != cudaSuccess ||
              false))
@@ -1014,6 +1020,15 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
              cudaMemset(m->err, 0, sizeof(int32_t)) != cudaSuccess ||
              cudaMemset(m->seeds, 0, sizeof(uint64_t) * m->max_streams) != cudaSuccess))
     s = fail(CC_ERR_CUDA, "memset failed");
+  if (!s) {  // every slot starts with the identity input manipulation
+    const int32_t C = m->nodes.front().d.c_out;
+    std::vector<float> ident(manip_floats, 0.f);
+    for (int32_t slot = 0; slot < m->max_streams; ++slot)
+      std::fill_n(ident.begin() + (size_t)slot * 3 * C, C, 1.f);
+    if (cudaMemcpy(m->in_manip, ident.data(), sizeof(float) * manip_floats, cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      s = fail(CC_ERR_CUDA, "input manipulation upload failed");
+  }
   if (s) {
     delete m;
     return s;
@@ -1076,13 +1091,30 @@ cc_status cc_model_state_bytes(const cc_model* model, size_t* state_bytes, size_
   return CC_OK;
 }
 
+// Uploads one slot's input manipulation (scale, bias, noise amplitude: host,
+// [C] each; NULL means 1 / 0 / 0) on `st` and waits for it.
+static cc_status upload_manip(cc::Model* m, int32_t slot, const float* scale, const float* bias,
+                              const float* noise, cudaStream_t st) {
+  const int32_t C = m->nodes.front().d.c_out;
+  std::vector<float> rows(3 * (size_t)C);
+  for (int32_t c = 0; c < C; ++c) {
+    rows[c] = scale ? scale[c] : 1.f;
+    rows[C + c] = bias ? bias[c] : 0.f;
+    rows[2 * C + c] = noise ? noise[c] : 0.f;
+  }
+  CC_CUDA(cudaMemcpyAsync(m->in_manip + (size_t)slot * 3 * C, rows.data(), sizeof(float) * rows.size(),
+                          cudaMemcpyHostToDevice, st));
+  CC_CUDA(cudaStreamSynchronize(st));  // rows leave scope on return
+  return CC_OK;
+}
+
 static cc_status zero_slot(cc::Model* m, int32_t slot, uint64_t seed, cudaStream_t st) {
   CC_CUDA(cudaMemsetAsync(m->arena + (size_t)slot * m->slot_bytes, 0, m->slot_bytes, st));
   CC_CUDA(cudaMemsetAsync(m->counters + slot, 0, sizeof(int64_t), st));
   const uint64_t host_seed = seed;
   CC_CUDA(cudaMemcpyAsync(m->seeds + slot, &host_seed, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
   CC_CUDA(cudaStreamSynchronize(st));  // host_seed leaves scope on return
-  return CC_OK;
+  return upload_manip(m, slot, nullptr, nullptr, nullptr, st);
 }
 
 cc_status cc_stream_create(cc_model* model, uint64_t seed, void* cuda_stream, cc_stream** out) {
@@ -1141,7 +1173,26 @@ cc_status cc_stream_destroy(cc_stream* s) {
 
 cc_status cc_stream_reset(cc_stream* s, void* cuda_stream) {
   if (!s) return fail(CC_ERR_INVALID_ARG, "null stream");
+  s->manip_set = false;
   return zero_slot(s->model, s->slot, s->seed, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+cc_status cc_stream_set_input_manipulation(cc_stream* s, const float* scale, const float* bias,
+                                           const float* noise, int32_t channels, void* cuda_stream) {
+  if (!s) return fail(CC_ERR_INVALID_ARG, "null stream");
+  cc::Model* m = s->model;
+  const int32_t C = m->nodes.front().d.c_out;
+  if (channels != C) return fail(CC_ERR_INVALID_ARG, "channels %d != the model's %d input channels", channels, C);
+  bool ident = true;
+  for (int32_t c = 0; c < C; ++c) {
+    const float a = scale ? scale[c] : 1.f, b = bias ? bias[c] : 0.f, q = noise ? noise[c] : 0.f;
+    if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(q))
+      return fail(CC_ERR_INVALID_ARG, "non-finite value at channel %d", c);
+    ident = ident && a == 1.f && b == 0.f && q == 0.f;
+  }
+  const cc_status r = upload_manip(m, s->slot, scale, bias, noise, reinterpret_cast<cudaStream_t>(cuda_stream));
+  if (!r) s->manip_set = !ident;
+  return r;
 }
 
 cc_status cc_stream_process(cc_stream* s, const float* in, int64_t n_in, float* out, int64_t n_out,

@@ -80,6 +80,7 @@ struct Model {
   int32_t* err = nullptr;  // device error word (bounded waits that gave up)
   int64_t* counters = nullptr;
   uint64_t* seeds = nullptr;
+  float* in_manip = nullptr;  // [max_streams][3][input channels]: per-slot scale, bias, noise amplitude
   std::mutex mu;
   std::vector<int32_t> free_slots;
   std::vector<cc_stream*> live_streams;  // destroyed with the model

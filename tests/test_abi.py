@@ -34,7 +34,11 @@ def _plan(nodes):
     return api.Model(nodes, {}, max_streams=0)
 
 
-@pytest.mark.parametrize("builder", [W.tiny_stack, W.rave_decoder, W.rave_encoder])
+def _autoencoder():
+    return W.chain(W.rave_encoder(), W.rave_decoder())
+
+
+@pytest.mark.parametrize("builder", [W.tiny_stack, W.rave_decoder, W.rave_encoder, _autoencoder])
 def test_plan_matches_oracle_analysis(cclib, builder):
     nodes = builder()
     info = M.analyze(nodes)
@@ -52,6 +56,16 @@ def test_plan_matches_oracle_analysis(cclib, builder):
         assert ni["frames_per_step"] == info["rate"][i] * info["in_per_step"]
     state, slot = m.state_bytes
     assert state == 4 * M.cache_elements(nodes, info)
+    m.close()
+
+
+def test_audio_to_audio_delay_composes(cclib):
+    """Delays compose through a chain (section 3.1): the encoder's 3-frame
+    latent delay reaches the output as 3 x 2048 samples on top of the
+    decoder's own 12424."""
+    m = _plan(_autoencoder())
+    assert m.total_delay == 3 * 2048 + 12424
+    assert m.io == dict(in_channels=1, out_channels=1, in_per_step=2048, out_per_step=2048)
     m.close()
 
 

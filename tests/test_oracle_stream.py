@@ -111,3 +111,24 @@ def test_linear_shift_invariance_without_activations():
     np.testing.assert_allclose(ys[13:], y[:-13], atol=1e-12)
     y2 = M.Stream(nodes, p).run(2.0 * x + xs, [600])
     np.testing.assert_allclose(y2, 2.0 * y + ys, atol=1e-11)
+
+
+def test_chain_equals_encoder_then_decoder_without_noise():
+    """The audio -> audio chain (one layer list) computes the encoder followed
+    by the decoder on the same weights; with the noise branch off the two are
+    the same arithmetic.  (With noise on they differ only by the noise
+    index: the chain's heads see the encoder's delay in their aligned frame
+    index.)"""
+    enc = W.rave_encoder(latent=8, capacity=4, ratios=(2, 2), bands=4, pqmf_taps=16)
+    dec = W.rave_decoder(latent=8, capacity=4, ratios=(2, 2), dilations=(1, 3), bands=4, pqmf_taps=16)
+    nodes = W.chain(enc, dec)
+    p = W.init_params(nodes, 5)
+    off = len(enc) - 1
+    pe = {i: p[i] for i in range(len(enc)) if i in p}
+    pd = {k: p[off + k] for k in range(1, len(dec)) if off + k in p}
+    x = W.signal(6, 64 * 5, 1, std=0.1)
+    y_chain = M.run_causal(nodes, p, x, noise_on=False)
+    y_two = M.run_causal(dec, pd, M.run_causal(enc, pe, x), noise_on=False)
+    assert np.array_equal(y_chain, y_two)
+    info_e, info_d, info_c = M.analyze(enc), M.analyze(dec), M.analyze(nodes)
+    assert info_c["delay"] == info_e["delay"] * 16 + info_d["delay"]  # 16 samples per latent frame

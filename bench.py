@@ -42,14 +42,19 @@ def default_sub_batches(dtype, streams):
 TC_TRAFFIC_PER_LAUNCH = {"decoder-bf16-b256": 6.62e6}
 
 WORKLOADS = {
-    # name: (dtype, streams, buffer latent frames)
-    "decoder-bf16-b256": ("bf16", 256, 1),
-    "decoder-f16-b256": ("f16", 256, 1),
-    "decoder-fp32-b256": ("f32", 256, 1),
-    "decoder-fp32-b1": ("f32", 1, 1),
-    "decoder-bf16-b1024": ("bf16", 1024, 1),
-    "decoder-bf16-b2048": ("bf16", 2048, 1),
+    # name: (dtype, streams, model steps (2048 output samples each) per buffer, model)
+    "decoder-bf16-b256": ("bf16", 256, 1, "decoder"),
+    "decoder-f16-b256": ("f16", 256, 1, "decoder"),
+    "decoder-fp32-b256": ("f32", 256, 1, "decoder"),
+    "decoder-fp32-b1": ("f32", 1, 1, "decoder"),
+    "decoder-bf16-b1024": ("bf16", 1024, 1, "decoder"),
+    "decoder-bf16-b2048": ("bf16", 2048, 1, "decoder"),
+    # audio -> audio: the encoder feeding the decoder as one streamed model
+    "autoencoder-bf16-b256": ("bf16", 256, 1, "autoencoder"),
+    "autoencoder-fp32-b256": ("f32", 256, 1, "autoencoder"),
 }
+MODEL_NAMES = {"decoder": "RAVE-like decoder, random init",
+               "autoencoder": "RAVE-like encoder -> decoder (audio -> audio), random init"}
 DEFAULT_WORKLOAD = "decoder-bf16-b256"
 
 
@@ -72,14 +77,20 @@ def node_flops(node, frames_out_per_step):
     return 0
 
 
-def build_decoder(dtype, streams, seed=1):
+def build_decoder(dtype, streams, seed=1, kind="decoder"):
+    """The decoder (latent in, audio out) or, for kind "autoencoder", the
+    encoder feeding the decoder (audio in, audio out), random weights."""
     from paper_2204_07064_gb300 import api
     from paper_2204_07064_gb300 import workloads as W
 
-    nodes = W.rave_decoder()
+    nodes = W.rave_decoder() if kind == "decoder" else W.chain(W.rave_encoder(), W.rave_decoder())
     params = W.init_params(nodes, seed)
     _, g, _ = api.pqmf_design(16, 64, 5.0)
-    params[W.pqmf_node_index(nodes)] = (api.inverse_pqmf_weights(g), None)
+    for i, nd in enumerate(nodes):
+        if nd["name"] == "ipqmf":
+            params[i] = (api.inverse_pqmf_weights(g), None)
+        if nd["name"] == "pqmf":
+            params[i] = (api.pqmf_analysis_weights(g), None)
     model = api.Model(nodes, params, dtype=dtype, max_streams=streams, max_steps_per_call=1)
     return nodes, params, model
 
@@ -269,27 +280,39 @@ class ClockSampler:
         return self.parse(out, window)
 
 
-def oracle_sample(steps, seed=1, stream_seed=11, warmup=1):
-    """FP64 oracle streaming of the same decoder, one stream: `warmup` untimed
-    buffers, then `steps` timed buffers (one wall time each).  Runs in a
-    subprocess with one BLAS thread; returns audio seconds / wall."""
+def oracle_sample(steps, seed=1, stream_seed=11, warmup=1, kind="decoder"):
+    """FP64 oracle streaming of the same model (decoder, or encoder -> decoder),
+    one stream: `warmup` untimed buffers, then `steps` timed buffers of one
+    model step each (one wall time each).  Runs in a subprocess with one BLAS
+    thread; returns audio seconds / wall."""
     code = f"""
 import os, sys, time, json
 sys.path.insert(0, {ROOT!r})
 import numpy as np
 from oracle import model as M, pqmf
 from paper_2204_07064_gb300 import workloads as W
-nodes = W.rave_decoder(); p = W.init_params(nodes, {seed})
+if {kind!r} == "decoder":
+    nodes = W.rave_decoder()
+    z = W.signal(5, {warmup} + {steps}, 128)
+    n = 1
+else:
+    nodes = W.chain(W.rave_encoder(), W.rave_decoder())
+    z = W.signal(5, ({warmup} + {steps}) * 2048, 1, std=0.1)
+    n = 2048
+p = W.init_params(nodes, {seed})
 _, g, _, _ = pqmf.design(16, 64)
-p[W.pqmf_node_index(nodes)] = (pqmf.synthesis_weights(g), None)
-z = W.signal(5, {warmup} + {steps}, 128)
+for i, nd in enumerate(nodes):
+    if nd["name"] == "ipqmf":
+        p[i] = (pqmf.synthesis_weights(g), None)
+    if nd["name"] == "pqmf":
+        p[i] = (pqmf.analysis_weights(g), None)
 s = M.Stream(nodes, p, seed={stream_seed})
 for i in range({warmup}):
-    s.process(z[i:i + 1])
+    s.process(z[i * n:(i + 1) * n])
 walls = []
 for i in range({warmup}, {warmup} + {steps}):
     t = time.perf_counter()
-    s.process(z[i:i + 1])
+    s.process(z[i * n:(i + 1) * n])
     walls.append(time.perf_counter() - t)
 print(json.dumps({{"wall": sum(walls), "walls": walls, "audio_s": {steps} * 2048 / {SR}}}))
 """
@@ -307,9 +330,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    dtype, streams, frames = WORKLOADS[args.workload]
+    dtype, streams, frames, kind = WORKLOADS[args.workload]
     # one process; each step is one 2048-sample buffer of one stream
-    value, d = oracle_sample(args.steps, warmup=args.warmup)
+    value, d = oracle_sample(args.steps, warmup=args.warmup, kind=kind)
     walls = d["walls"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "streams",
@@ -525,13 +548,17 @@ def main():
     __graft_entry__.build()
     from paper_2204_07064_gb300 import workloads as W
 
-    dtype, streams, frames = WORKLOADS[args.workload]
-    nodes, params, model = build_decoder(dtype, streams)
+    dtype, streams, frames, kind = WORKLOADS[args.workload]
+    nodes, params, model = build_decoder(dtype, streams, kind=kind)
     seeds = W.stream_seeds(1000 + rank, streams)
     ss = [model.stream(seed=s) for s in seeds]
     rng = np.random.default_rng(rank)
     steps_total = args.warmup + args.steps
-    z = torch.from_numpy(rng.standard_normal((steps_total, streams, frames, 128), dtype=np.float32)).to(dev)
+    io = model.io
+    in_shape = (frames * io["in_per_step"], io["in_channels"])  # one buffer of one stream
+    in_std = 1.0 if kind == "decoder" else 0.1  # latents N(0, 1); audio N(0, 0.1^2)
+    z = torch.from_numpy(in_std * rng.standard_normal((steps_total, streams) + in_shape,
+                                                      dtype=np.float32)).to(dev)
     y = torch.empty((streams, 2048 * frames, 1), dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev) if args.flush_l2 else None
     st = torch.cuda.current_stream()
@@ -633,7 +660,7 @@ def main():
                               "config": {"workload": args.workload}, "note": "--only-timed"}))
         return
     # end to end through the C ABI with pinned host buffers (copies in the timed region)
-    zh = torch.empty((streams, frames, 128), dtype=torch.float32).pin_memory()
+    zh = torch.empty((streams,) + in_shape, dtype=torch.float32).pin_memory()
     zh.copy_(z[0].cpu())
     yh = torch.empty((streams, 2048 * frames, 1), dtype=torch.float32).pin_memory()
     e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(k2)]
@@ -674,7 +701,7 @@ def main():
     # the same batch through the FP32 (FFMA) path: the metric compares both
     fp32_cmp = None
     if dtype != "f32":
-        model32 = build_decoder("f32", streams)[2]
+        model32 = build_decoder("f32", streams, kind=kind)[2]
         ss32 = [model32.stream(seed=s) for s in seeds]
         for i in range(args.warmup):
             model32.process_batch(ss32, z[i], y)
@@ -693,7 +720,7 @@ def main():
     # the same decoder at larger batches (one chain per 256 streams): where the
     # step stops being latency-bound
     by_batch = None
-    if dtype != "f32" and streams == 256 and world == 1:
+    if dtype != "f32" and streams == 256 and world == 1 and kind == "decoder":
         by_batch = {}
         fl = sum(node_flops(nodes[i], info_u[i]) for i in conv_nodes)  # per stream-step
         for b in (1024, 2048):
@@ -710,7 +737,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "streams", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-        "config": {"workload": args.workload, "model": "RAVE-like decoder, random init",
+        "config": {"workload": args.workload, "model": MODEL_NAMES[kind],
                    "streams_per_gpu": streams, "buffer_samples": 2048 * frames, "sample_rate": SR,
                    "concurrent_chains": nsub, "cuda_graph": graph is not None,
                    "parallelism": f"replicas x{world}",
@@ -729,7 +756,7 @@ def main():
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, d = oracle_sample(64)
+        v, d = oracle_sample(64, kind=kind)
         line["cpu_baseline"] = {"value": v, "unit": "streams", "cores": 1, "kind": "oracle",
                                 "sample": f"1 stream x 64 buffers of 2048 samples, FP64 NumPy, "
                                           f"1 BLAS thread ({d['wall']:.1f} s)"}

@@ -35,10 +35,11 @@ def test_clock_samples_kept_only_inside_the_timed_window():
     assert bench.ClockSampler.parse("") is None
 
 
-def test_reference_arm_prints_one_line_with_the_contract_keys():
+@pytest.mark.parametrize("workload", [bench.DEFAULT_WORKLOAD, "autoencoder-bf16-b256"])
+def test_reference_arm_prints_one_line_with_the_contract_keys(workload):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "3", "--warmup", "3"], capture_output=True, text=True, timeout=300,
-                       cwd=ROOT)
+                        "--steps", "3", "--warmup", "3", "--workload", workload], capture_output=True, text=True,
+                       timeout=300, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -48,7 +49,7 @@ def test_reference_arm_prints_one_line_with_the_contract_keys():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "streams", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"] == bench.DEFAULT_WORKLOAD
+    assert d["config"]["workload"] == workload
 
 
 @pytest.mark.parametrize("dtype,streams,expect", [("f32", 256, 1), ("bf16", 256, 1), ("bf16", 1024, 4),

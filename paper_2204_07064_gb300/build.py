@@ -3,11 +3,17 @@
 Each translation unit is compiled in parallel, then linked into
 ``paper_2204_07064_gb300/_lib/libcachedconv.so`` against the shared CUDA
 runtime.  Nothing here runs at import time; ``__graft_entry__.build()`` and the
-test suite call ``build()``.
+test suite call ``build()``.  Several processes may call it at once (one per
+rank under torchrun): an exclusive lock on ``_lib/.build.lock`` lets one of
+them build while the others wait and then find the library up to date, and
+every object and the library are written to a temporary name and renamed
+into place, so a process that has already loaded the library never sees it
+rewritten.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -45,8 +51,14 @@ def _stale(target, deps):
 
 
 def build(verbose=False, force=False, ptxas_verbose=False):
-    nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
+    with open(os.path.join(OUT_DIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)  # released when the file closes
+        return _build_locked(verbose, force, ptxas_verbose)
+
+
+def _build_locked(verbose, force, ptxas_verbose):
+    nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "cachedconv.h"))
     objs = []
@@ -57,13 +69,15 @@ def build(verbose=False, force=False, ptxas_verbose=False):
         objs.append(obj)
         if force or _stale(obj, [path] + headers):
             cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-Xcompiler", "-Wall", "-c", path, "-o", obj]
+                   "-Xcompiler", "-Wall", "-c", path, "-o", obj + ".tmp.o"]
             if ptxas_verbose and src.endswith(".cu"):
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(cmd[-1], cmd[-1][:-len(".tmp.o")])
         return cmd, r
 
     if jobs:
@@ -76,7 +90,8 @@ def build(verbose=False, force=False, ptxas_verbose=False):
                     raise RuntimeError(f"nvcc failed for {cmd[-3]}")
     if force or jobs or _stale(LIB, objs):
         libdir = _cuda_lib_dir(nvcc)
-        cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs,
+        tmp = os.path.join(OUT_DIR, ".libcachedconv.tmp.so")
+        cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
                "-L" + libdir, "-Xlinker", "-rpath=" + libdir]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if verbose or r.returncode != 0:
@@ -84,6 +99,7 @@ def build(verbose=False, force=False, ptxas_verbose=False):
             print(r.stdout + r.stderr)
         if r.returncode != 0:
             raise RuntimeError("link of libcachedconv.so failed")
+        os.replace(tmp, LIB)
     return LIB
 
 

@@ -112,3 +112,49 @@ def test_host_pqmf_design_matches_oracle(cclib):
         np.testing.assert_allclose(h, h2, atol=1e-13)
         np.testing.assert_allclose(g, g2, atol=1e-13)
         assert abs(wc - wc2) < 1e-12
+
+
+def test_missing_library_fails_loudly():
+    """No CPU fallback: with the library absent, the first call raises."""
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = f"""
+import sys
+sys.path.insert(0, {root!r})
+from paper_2204_07064_gb300 import build, api, workloads as W
+build.LIB = "/nonexistent/libcachedconv.so"
+try:
+    api.Model(W.tiny_stack(), {{}}, max_streams=0)
+except RuntimeError as e:
+    assert "not built" in str(e), e
+    print("raised")
+"""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "raised"
+
+
+def test_product_package_never_imports_the_oracle():
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = f"""
+import sys
+sys.path.insert(0, {root!r})
+import paper_2204_07064_gb300
+from paper_2204_07064_gb300 import api, autograd, workloads, build
+assert not any(m == "oracle" or m.startswith("oracle.") for m in sys.modules), sorted(sys.modules)
+print("clean")
+"""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "clean"
+    pkg = os.path.join(root, "paper_2204_07064_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", src, re.M), f

@@ -76,6 +76,30 @@ def whole_job_streams(streams_per_rank, world, steps, samples_per_step, ms):
     return streams_per_rank * world * samples_per_step * steps / (ms / 1000.0) / SR
 
 
+def device_free_bytes(dev):
+    try:
+        import torch
+
+        torch.cuda.synchronize(dev)
+        return int(torch.cuda.mem_get_info(dev)[0])
+    except Exception:
+        return None
+
+
+def model_memory(model, streams, free_before, free_after):
+    """Memory of streaming (section 4.1 reports the cached padding as a constant
+    extra 180 kiB per stream): the persistent cache state per stream, the arena
+    slot per stream (state plus per-call rows and low-precision mirrors), the
+    arena, and the device memory the model took (free-memory delta around its
+    creation: weights, arena, bookkeeping)."""
+    state, slot = model.state_bytes
+    out = {"state_bytes_per_stream": int(state), "slot_bytes_per_stream": int(slot),
+           "arena_bytes": int(slot) * int(streams), "device_bytes_model": None}
+    if free_before is not None and free_after is not None:
+        out["device_bytes_model"] = int(free_before - free_after)
+    return out
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -567,7 +591,9 @@ def main():
     from paper_2204_07064_gb300 import workloads as W
 
     dtype, streams, frames, kind = WORKLOADS[args.workload]
+    free0 = device_free_bytes(dev)
     nodes, params, model = build_decoder(dtype, streams, kind=kind)
+    memory = model_memory(model, streams, free0, device_free_bytes(dev))
     seeds = W.stream_seeds(1000 + rank, streams)
     ss = [model.stream(seed=s) for s in seeds]
     rng = np.random.default_rng(rank)
@@ -769,6 +795,7 @@ def main():
                 "h2d_bytes_per_step": int(zh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)},
         "roofline": roof,
         "fp32_same_batch": fp32_cmp,
+        "memory": memory,
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk,
     }

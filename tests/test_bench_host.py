@@ -56,3 +56,13 @@ def test_reference_arm_prints_one_line_with_the_contract_keys(workload):
                                                   ("f16", 2048, 8), ("bf16", 100, 1)])
 def test_default_sub_batches(dtype, streams, expect):
     assert bench.default_sub_batches(dtype, streams) == expect
+
+
+def test_model_memory_fields():
+    class _Model:  # the two numbers cc_model_state_bytes reports
+        state_bytes = (110592, 1081344)
+
+    m = bench.model_memory(_Model(), 256, 9_000_000_000, 8_600_000_000)
+    assert m == {"state_bytes_per_stream": 110592, "slot_bytes_per_stream": 1081344,
+                 "arena_bytes": 1081344 * 256, "device_bytes_model": 400_000_000}
+    assert bench.model_memory(_Model(), 1, None, None)["device_bytes_model"] is None

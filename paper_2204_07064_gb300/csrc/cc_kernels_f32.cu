@@ -353,10 +353,13 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Narrow contraction (M <= 32 rows, Kt <= 64, cin % 4 == 0): one thread per
+// Narrow contraction (M <= 16 rows, Kt <= 64, cin % 4 == 0): one thread per
 // GEMM column with the weights in shared memory (every thread reads the same
 // weight: a broadcast) and its window read once, 16 bytes at a time.  Used by
 // the tail of the decoder (the noise branch's second conv, the inverse PQMF).
+// Only the 16-row form is instantiated: fully unrolled, a 32-row form is
+// 2048 dependent FMAs whose compilation alone takes minutes; such layers take
+// the general kernels.
 // ---------------------------------------------------------------------------
 template <int TM>
 __global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
@@ -558,10 +561,9 @@ cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   if (N <= 0) return cudaSuccess;
   auto tiles = [&](int bm, int bn) { return ((a.M + bm - 1) / bm) * ((N + bn - 1) / bn); };
-  if (a.M <= 32 && a.Kt <= 64 && a.cin % 4 == 0) {
+  if (a.M <= 16 && a.Kt <= 64 && a.cin % 4 == 0) {
     dim3 grid((unsigned)((N + 127) / 128));
-    if (a.M <= 16) return launch_pdl(k_conv_small_f32<16>, grid, dim3(128), 0, st, a);
-    return launch_pdl(k_conv_small_f32<32>, grid, dim3(128), 0, st, a);
+    return launch_pdl(k_conv_small_f32<16>, grid, dim3(128), 0, st, a);
   }
   if (a.cin % 8 == 0 && a.M >= 128 && tiles(128, 128) >= 2 * 152) {
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((a.M + 127) / 128));

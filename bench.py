@@ -322,11 +322,11 @@ class ClockSampler:
         return self.parse(out, window)
 
 
-def oracle_sample(steps, seed=1, stream_seed=11, warmup=1, kind="decoder"):
+def oracle_sample(steps, seed=1, stream_seed=11, warmup=1, kind="decoder", threads=1):
     """FP64 oracle streaming of the same model (decoder, or encoder -> decoder),
     one stream: `warmup` untimed buffers, then `steps` timed buffers of one
-    model step each (one wall time each).  Runs in a subprocess with one BLAS
-    thread; returns audio seconds / wall."""
+    model step each (one wall time each).  Runs in a subprocess with `threads`
+    BLAS threads; returns audio seconds / wall."""
     code = f"""
 import os, sys, time, json
 sys.path.insert(0, {ROOT!r})
@@ -358,7 +358,8 @@ for i in range({warmup}, {warmup} + {steps}):
     walls.append(time.perf_counter() - t)
 print(json.dumps({{"wall": sum(walls), "walls": walls, "audio_s": {steps} * 2048 / {SR}}}))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        timeout=max(600.0, 0.5 * (steps + warmup)))
     if r.returncode != 0:
@@ -791,6 +792,10 @@ def main():
         "latency_ms": {"p50": p50, "p99": p99, "max": step_sorted[-1],
                        "buffer_ms": 2048 * frames / SR * 1000.0,
                        "meets_deadline": p99 < 2048 * frames / SR * 1000.0},
+        # real-time factor (section 4.1): processing time / audio duration, of
+        # one step of the whole batch and per stream
+        "rtf": {"step": (total_ms / args.steps) / (2048 * frames / SR * 1000.0),
+                "per_stream": (total_ms / args.steps) / (2048 * frames / SR * 1000.0) / streams},
         "e2e": {"value": e2e_value, "unit": "streams",
                 "h2d_bytes_per_step": int(zh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4)},
         "roofline": roof,
@@ -804,6 +809,12 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": "streams", "cores": 1, "kind": "oracle",
                                 "sample": f"1 stream x 64 buffers of 2048 samples, FP64 NumPy, "
                                           f"1 BLAS thread ({d['wall']:.1f} s)"}
+        # the same sample with one BLAS thread per host core
+        ncores = os.cpu_count() or 1
+        v_all, d_all = oracle_sample(64, kind=kind, threads=ncores)
+        line["cpu_baseline_all_cores"] = {"value": v_all, "unit": "streams", "cores": ncores, "kind": "oracle",
+                                          "sample": f"as cpu_baseline with {ncores} BLAS threads "
+                                                    f"({d_all['wall']:.1f} s)"}
     if rank == 0:
         print(json.dumps(line))
     if dist:

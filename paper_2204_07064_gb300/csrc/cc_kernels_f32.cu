@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
 // weight: a broadcast) and its window read once, 16 bytes at a time.  Used by
 // the tail of the decoder (the noise branch's second conv, the inverse PQMF).
 // Only the 16-row form is instantiated: fully unrolled, a 32-row form is
-// 2048 dependent FMAs whose compilation alone takes minutes; such layers take
-// the general kernels.
+// 2048 FMAs on which the compiler's optimiser (not ptxas) spends minutes;
+// such layers take the general kernels.
 // ---------------------------------------------------------------------------
 template <int TM>
 __global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {

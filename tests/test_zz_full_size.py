@@ -1,8 +1,14 @@
-"""Parity at the launch configuration bench.py times for the audio -> audio
-workload (autoencoder-bf16-b256): the RAVE-like encoder feeding the decoder,
-BF16, a model of 256 streams, every call one 2048-sample buffer for all 256
-streams.  Sampled streams are checked sample by sample against the FP64
-oracle at the BF16 bar (SNR >= 35 dB, max-abs <= 2e-2 x peak)."""
+"""Full and maximum sizes.
+
+* Parity at the launch configuration bench.py times for the audio -> audio
+  workload (autoencoder-bf16-b256): the RAVE-like encoder feeding the decoder,
+  BF16, a model of 256 streams, every call one 2048-sample buffer for all 256
+  streams.  Sampled streams are checked sample by sample against the FP64
+  oracle at the BF16 bar (SNR >= 35 dB, max-abs <= 2e-2 x peak).
+* The largest arena: the tensor-core epilogue addresses the arena with 32-bit
+  offsets in 16-byte units, so a model whose arena would reach 64 GiB is
+  refused with CC_ERR_NO_MEMORY before the arena is allocated, and one just
+  below the limit is accepted."""
 import numpy as np
 import pytest
 
@@ -48,3 +54,19 @@ def test_autoencoder_bf16_256_streams_sampled(cclib, cuda):
         assert snr >= 35.0, f"stream {i}: SNR {snr:.1f} dB"
         assert err <= 2e-2 * peak, f"stream {i}: max-abs {err:.3e} > 2e-2 x {peak:.3e}"
     model.close()
+
+
+def test_arena_limit_of_64_gib(cclib, cuda):
+    dec = W.rave_decoder()
+    p = W.init_params(dec, 1)
+    slot = api.Model(dec, {}, dtype="bf16", max_streams=0).state_bytes[1]
+    too_many = (1 << 36) // slot + 1
+    assert too_many * slot >= 1 << 36
+    with pytest.raises(api.CCError) as e:
+        api.Model(dec, p, dtype="bf16", max_streams=too_many)
+    assert e.value.status == -4
+    # just below the limit the arena is taken (about 64 GB of the GPU's 288)
+    m = api.Model(dec, p, dtype="bf16", max_streams=too_many - 1)
+    s = m.stream(seed=1)
+    s.close()
+    m.close()

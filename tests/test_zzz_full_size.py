@@ -8,7 +8,10 @@
 * The largest arena: the tensor-core epilogue addresses the arena with 32-bit
   offsets in 16-byte units, so a model whose arena would reach 64 GiB is
   refused with CC_ERR_NO_MEMORY before the arena is allocated, and one just
-  below the limit is accepted."""
+  below the limit is accepted.
+
+The file runs after every other test, so that a failure here never hides
+another test's result."""
 import numpy as np
 import pytest
 

@@ -132,7 +132,8 @@ cc_status cc_model_total_delay(const cc_model* model, int64_t* out_frames);
 
 /* Channels and frames per model step.  A step is the smallest input length
  * that gives every layer a whole number of frames (e.g. 1 latent frame for a
- * x2048 decoder, 2048 samples for a /2048 encoder). */
+ * x2048 decoder, 2048 samples for a /2048 encoder): the buffer granularity at
+ * which strided layers stay aligned (section 3.1). */
 cc_status cc_model_io(const cc_model* model, int32_t* in_channels, int32_t* out_channels,
                       int32_t* in_per_step, int32_t* out_per_step);
 
@@ -144,12 +145,15 @@ cc_status cc_model_node_info(const cc_model* model, int32_t node, int64_t* delay
                              int32_t* extra_delay, int32_t* align3, int32_t* kept_frames,
                              int32_t* frames_per_step);
 
-/* Bytes of persistent cache state per stream (the cached padding), and bytes
- * of one arena slot (state plus per-call rows). */
+/* Bytes of persistent cache state per stream (the cached padding of section
+ * 2.2; section 4.1 measures it as the streaming method's only extra memory),
+ * and bytes of one arena slot (state plus per-call rows). */
 cc_status cc_model_state_bytes(const cc_model* model, size_t* state_bytes, size_t* slot_bytes);
 
 /* Create a stream: take a free arena slot (NO_MEMORY when none is left: admission
- * by cache memory), zero its caches.  `seed` keys the heads' noise. */
+ * by cache memory), zero its caches -- the zero left padding of the causal
+ * model (section 3) -- and wait for cuda_stream.  `seed` keys the heads' noise.
+ * Destroy returns the slot (it synchronises the device first). */
 cc_status cc_stream_create(cc_model* model, uint64_t seed, void* cuda_stream, cc_stream** out);
 cc_status cc_stream_destroy(cc_stream* stream);
 
@@ -182,11 +186,13 @@ cc_status cc_stream_reset(cc_stream* stream, void* cuda_stream);
 cc_status cc_stream_set_input_manipulation(cc_stream* stream, const float* scale, const float* bias,
                                            const float* noise, int32_t channels, void* cuda_stream);
 
-/* Process one buffer: n_in input frames ([n_in][in_channels]) -> n_out output
- * frames ([n_out][out_channels]).  n_in must be a multiple of in_per_step and
+/* Process one buffer (cached padding, section 2.2 and Fig. 1: every layer
+ * reads its last frames from the stream's caches in place of zero padding):
+ * n_in input frames ([n_in][in_channels]) -> n_out output frames
+ * ([n_out][out_channels]).  n_in must be a multiple of in_per_step and
  * n_out == n_in / in_per_step * out_per_step (else BAD_LENGTH).  The output of
  * a call is the reconfigured model's output for these frames: it equals the
- * offline model's output delayed by cc_model_total_delay frames. */
+ * offline model's output delayed by cc_model_total_delay frames (section 4.2). */
 cc_status cc_stream_process(cc_stream* stream, const float* in, int64_t n_in, float* out,
                             int64_t n_out, void* cuda_stream);
 
@@ -199,24 +205,27 @@ cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, int32_t c
                            const float* in, int64_t in_stride, int64_t n_in, float* out,
                            int64_t out_stride, int64_t n_out, void* cuda_stream);
 
-/* Checkpoint / resume: the whole stream state (its arena slot, holding every
- * cache, plus its step counter) as an opaque host blob of exactly
- * cc_stream_state_size() bytes.  Both calls synchronise cuda_stream.  A blob
- * restores into any stream of the same model. */
+/* Checkpoint / resume (the paper has no counterpart): the whole stream state
+ * (its arena slot, holding every cache of section 2.2, plus its step counter)
+ * as an opaque host blob of exactly cc_stream_state_size() bytes.  Both calls
+ * synchronise cuda_stream.  A blob restores into any stream of the same
+ * model. */
 cc_status cc_stream_state_size(const cc_stream* stream, size_t* bytes);
 cc_status cc_stream_get_state(cc_stream* stream, void* host_blob, size_t bytes, void* cuda_stream);
 cc_status cc_stream_set_state(cc_stream* stream, const void* host_blob, size_t bytes,
                               void* cuda_stream);
 
-/* Synchronises the device and reports whether any tensor-core pipeline wait
- * of this model gave up since the last call (TIMEOUT, *code = bit set of the
+/* Failure detection (the paper has no counterpart).  Synchronises the device
+ * and reports whether any tensor-core pipeline wait of this model gave up
+ * since the last call (TIMEOUT, *code = bit set of the
  * waiting roles: 1 producer, 2 epilogue, 4 MMA issuer); clears the record.
  * Such a wait is bounded (2 s) so that a stalled pipeline returns instead of
  * hanging the GPU; the affected outputs are then undefined. */
 cc_status cc_model_device_status(cc_model* model, int32_t* code);
 
-/* Per-node device timing (CUDA events recorded around every launch on the
- * launching stream).  enable=1 starts accumulating; cc_model_timing_read
+/* Per-node device timing for measurement (the paper has no counterpart; its
+ * section 4.1 times whole buffers).  CUDA events are recorded around every
+ * launch on the launching stream.  enable=1 starts accumulating; cc_model_timing_read
  * synchronises and returns, per node, the summed milliseconds and launch count
  * since the last enable. */
 cc_status cc_model_timing(cc_model* model, int32_t enable);
@@ -227,7 +236,9 @@ cc_status cc_model_timing_read(cc_model* model, double* ms_per_node, int64_t* la
  * Gradients of a loss over a long streamed signal, chunk by chunk in reverse
  * time order with per-chunk activation checkpointing.  The streamed output
  * equals the causal offline model (section 4.2), so these are that model's
- * gradients with respect to the input and to every weight and bias.
+ * gradients with respect to the input and to every weight and bias.  (The
+ * paper trains offline and streams only at inference, section 4.3; this
+ * chunked form has no counterpart there.)
  *
  * Protocol, for streams processed forward chunk by chunk:
  *   forward:  before chunk c, cc_stream_snapshot each stream into a device
@@ -261,7 +272,9 @@ cc_status cc_stream_snapshot(cc_stream* stream, void* dev_buf, size_t bytes, voi
 cc_status cc_stream_restore(cc_stream* stream, const void* dev_buf, size_t bytes, void* cuda_stream);
 
 /* ---------------------------------------------------------------- serving
- * Continuous batching of many real-time streams of one model.  Clients submit
+ * Continuous batching of many real-time streams of one model: the paper's
+ * per-buffer real-time processing (section 1, section 4.1) for many streams at
+ * once; the paper itself runs one stream and has no server.  Clients submit
  * requests from any thread; a scheduler thread repeatedly advances, by one
  * model step and in one batched launch chain, every stream that has a request
  * still owed output and a full step of input buffered (oldest request first,

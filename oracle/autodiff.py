@@ -24,7 +24,9 @@ def _act(x, act):
 
 
 def causal_forward(nodes, params_t, x, seed=0, noise_on=True):
-    """x: torch float64 [C][T]; params_t: {node: (w, b)} torch float64 tensors.
+    """The causal model of section 3 in torch float64, for autograd.
+
+    x: torch float64 [C][T]; params_t: {node: (w, b)} torch float64 tensors.
     Returns the last node's output [C_out][T_out]."""
     info = M.analyze(nodes)
     vals = []
@@ -65,7 +67,8 @@ def causal_forward(nodes, params_t, x, seed=0, noise_on=True):
 
 
 def gradients(nodes, params, x, weight_out, seed=0, noise_on=True):
-    """Loss L = sum(weight_out * y) over the causal model's output y
+    """Offline gradients of the causal model (section 3), the reference for
+    the chunked backward.  Loss L = sum(weight_out * y) over the causal model's output y
     ([T_out][C_out], channels-last like the library).  Returns (L, dL/dx as
     [T][C], {node: (dL/dw, dL/db)}) in float64 numpy."""
     xt = torch.tensor(np.asarray(x, np.float64).T.copy(), requires_grad=True)

@@ -12,11 +12,12 @@ LEAKY_SLOPE = 0.2
 
 
 def leaky_relu(x):
-    """LeakyReLU with slope 0.2 (the activation of the RAVE-like workloads)."""
+    """LeakyReLU with slope 0.2 (the activation of the RAVE-like workloads, section 2.3)."""
     return np.where(x >= 0, x, LEAKY_SLOPE * x)
 
 
 def activate(x, act):
+    """The layer input's activation, none or LeakyReLU (section 2.3's RAVE-like layers)."""
     if act is None:
         return x
     if act == "leaky":
@@ -80,7 +81,7 @@ def conv1d(x, w, b=None, stride=1, dilation=1, pad_left=0, pad_right=0):
 
 
 def conv_transpose_full(x, w, stride):
-    """Transposed convolution, full output (no crop):
+    """Transposed convolution of section 2.1, full output (no crop):
 
         y^n[q*S + k] += sum_m w^{m,n}[k] x^m[q],   length (T-1)*S + K.
 
@@ -99,7 +100,8 @@ def conv_transpose_full(x, w, stride):
 
 
 def conv_transpose_full_loops(x, w, stride):
-    """The scatter definition as explicit loops (tiny inputs only)."""
+    """Section 2.1's transposed convolution by its scatter definition, as explicit
+    loops (tiny inputs only)."""
     m_in, n_out, k = w.shape
     t = x.shape[1]
     y = np.zeros((n_out, (t - 1) * stride + k))

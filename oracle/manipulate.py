@@ -27,7 +27,9 @@ TAG = 0x6C6174656E742D6E
 
 
 def input_noise(seed, t0, count, channels):
-    """u(t, c) for input frames t0 .. t0+count-1, float64 [count][channels]."""
+    """u(t, c) for input frames t0 .. t0+count-1, float64 [count][channels]:
+    section 5.2's per-dimension random noise, in this project's reading
+    (uniform, SplitMix64 counter t * channels + c, tagged seed)."""
     s = (seed ^ TAG) & N.MASK
     out = np.empty((count, channels))
     for i in range(count):
@@ -37,9 +39,10 @@ def input_noise(seed, t0, count, channels):
 
 
 def manipulate(x, scale=1.0, bias=0.0, amp=0.0, seed=0, t0=0):
-    """The manipulated input frames.  x: [T][C]; scale, bias, amp broadcast to
-    [T][C] (per frame and channel); t0 = index of x's first frame in the
-    stream."""
+    """The manipulated input frames (Fig. 7's bias and replacement, section
+    5.1; section 5.2's scale, bias and noise).  x: [T][C]; scale, bias, amp
+    broadcast to [T][C] (per frame and channel); t0 = index of x's first frame
+    in the stream."""
     x = np.asarray(x, dtype=np.float64)
     T, C = x.shape
     scale = np.broadcast_to(np.asarray(scale, dtype=np.float64), (T, C))
@@ -54,8 +57,8 @@ def manipulate(x, scale=1.0, bias=0.0, amp=0.0, seed=0, t0=0):
 def piecewise(T, C, changes, default):
     """A [T][C] parameter array that holds ``default`` until the first change;
     ``changes`` = [(frame, value [C] or scalar), ...] in frame order, each value
-    held from its frame on (how a user's control reaches the stream between
-    buffers)."""
+    held from its frame on: the real-time interaction of section 5.1, a user's
+    control reaching the stream between buffers."""
     out = np.empty((T, C))
     out[:] = default
     for f, v in changes:

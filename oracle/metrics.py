@@ -13,10 +13,13 @@ import numpy as np
 
 
 def waveform_distance(x, y):
+    """Eq. 5: waveform distance L_w(x, y) = ||x - y||_2 (section 4.2)."""
     return float(np.sqrt(np.sum((np.asarray(x, np.float64) - np.asarray(y, np.float64)) ** 2)))
 
 
 def amplitude_stft(x, n_fft=2048, hop=512):
+    """Amplitude STFT S of Eq. 4 (section 4.2), read as a 2048-point periodic
+    Hann window with hop 512."""
     x = np.asarray(x, np.float64).ravel()
     n = np.arange(n_fft)
     win = np.sin(np.pi * n / n_fft) ** 2  # periodic Hann, the window of section 3.3
@@ -31,12 +34,16 @@ def amplitude_stft(x, n_fft=2048, hop=512):
 
 
 def spectral_distance(x, y, eps=1.0, n_fft=2048, hop=512):
+    """Eq. 4: spectral distance ||log(S(x) + eps) - log(S(y) + eps)||_2,
+    eps = 1 (section 4.2)."""
     sx = amplitude_stft(x, n_fft, hop)
     sy = amplitude_stft(y, n_fft, hop)
     return float(np.sqrt(np.sum((np.log(sx + eps) - np.log(sy + eps)) ** 2)))
 
 
 def snr_db(ref, out):
+    """SNR of `out` against `ref` in dB: the low-precision parity bar (no
+    paper passage; the paper's forms are FP32)."""
     ref = np.asarray(ref, np.float64)
     err = np.asarray(out, np.float64) - ref
     den = np.sum(err ** 2)
@@ -44,9 +51,11 @@ def snr_db(ref, out):
 
 
 def rms(x):
+    """Root mean square, the scale of the FP32 parity bar (no paper passage)."""
     x = np.asarray(x, np.float64)
     return float(np.sqrt(np.mean(x ** 2)))
 
 
 def max_abs(ref, out):
+    """Largest absolute difference, the element-wise parity check (no paper passage)."""
     return float(np.max(np.abs(np.asarray(out, np.float64) - np.asarray(ref, np.float64))))

@@ -98,7 +98,8 @@ def analyze(nodes):
 
 
 def history(nodes, info):
-    """Cached-padding length each consumer needs from each of its inputs."""
+    """Cached-padding length each consumer needs from each of its inputs (the
+    cached padding of section 2.2 with Eq. 2's extra delay)."""
     hist = []
     for i, nd in enumerate(nodes):
         op = nd["op"]
@@ -114,7 +115,7 @@ def history(nodes, info):
 
 
 def cache_frames(nodes, info):
-    """Per node: frames of its output kept between buffers (max over consumers)."""
+    """Per node (section 2.2's cache): frames of its output kept between buffers (max over consumers)."""
     keep = [0] * len(nodes)
     for i, (nd, hs) in enumerate(zip(nodes, history(nodes, info))):
         for u, h in zip(nd["inputs"], hs):
@@ -123,13 +124,15 @@ def cache_frames(nodes, info):
 
 
 def cache_elements(nodes, info):
-    """Closed-form streaming state size: sum over nodes of kept frames x channels."""
+    """Closed-form streaming state size: sum over nodes of kept frames x
+    channels (section 4.1 reports this memory as the method's only overhead)."""
     keep = cache_frames(nodes, info)
     return sum(k * nd["c_out"] for k, nd in zip(keep, nodes))
 
 
 def warmup_frames(nodes):
-    """Leading output frames of the offline original that the causal model may
+    """The start-up boundary effect of section 4.2's comparison.  Leading output
+    frames of the offline original that the causal model may
     not reproduce (the paper compensates latency but does not discuss this
     start-up effect).  An inner layer's left zero padding at negative times is
     replaced, in the causal model, by that layer's pre-roll output; a frame is
@@ -175,7 +178,8 @@ def _sigmoid(x):
 
 
 def heads_combine(wave, amp, noise_logit, seed, t0, noise_on=True):
-    """RAVE-like output combination: tanh(wave) * sigmoid(amp) + sigmoid(noise) * u,
+    """RAVE-like output combination (section 2.3's heads with the noise
+    synthesiser): tanh(wave) * sigmoid(amp) + sigmoid(noise) * u,
     u drawn for aligned frames t0, t0+1, ... ([C][T] arrays)."""
     y = np.tanh(wave) * _sigmoid(amp)
     if noise_on:
@@ -246,10 +250,12 @@ def run_offline(nodes, params, x, causal, seed=0, noise_on=True):
 
 
 def run_original(nodes, params, x, seed=0, noise_on=True):
+    """The original non-causal model offline (pads L/R, crops; Eq. 1, section 2.1)."""
     return run_offline(nodes, params, x, causal=False, seed=seed, noise_on=noise_on)
 
 
 def run_causal(nodes, params, x, seed=0, noise_on=True):
+    """The causally reconfigured model offline (section 3: all padding left, Eq. 2, Eq. 3)."""
     return run_offline(nodes, params, x, causal=True, seed=seed, noise_on=noise_on)
 
 
@@ -281,6 +287,7 @@ class Stream:
 
     @property
     def in_per_step(self):
+        """Smallest input length giving every layer whole frames (section 3.1's alignment)."""
         return self.info["in_per_step"]
 
     def _window(self, i, j, new):
@@ -291,7 +298,8 @@ class Stream:
         return win
 
     def process(self, buf):
-        """buf: [n][C_in], n a multiple of in_per_step.  Returns [n_out][C_out]."""
+        """One DSP call (section 1, Fig. 1).  buf: [n][C_in], n a multiple of
+        in_per_step.  Returns [n_out][C_out]."""
         buf = np.asarray(buf, dtype=np.float64)
         if buf.shape[0] % self.in_per_step:
             raise ValueError("buffer length must be a multiple of in_per_step")
@@ -332,7 +340,8 @@ class Stream:
         return outs[-1].T.copy()
 
     def run(self, x, partition):
-        """Stream x [T][C] through buffers of the given lengths; concatenate."""
+        """Stream x [T][C] through buffers of the given lengths and concatenate
+        (section 4.2's buffer-size experiment)."""
         pieces, pos = [], 0
         for n in partition:
             pieces.append(self.process(x[pos:pos + n]))

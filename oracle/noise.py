@@ -24,6 +24,7 @@ MUL2 = 0x94D049BB133111EB
 
 
 def mix(z):
+    """SplitMix64 output function (Steele, Lea & Flood 2014): the bijective mix of one state."""
     z &= MASK
     z = ((z ^ (z >> 30)) * MUL1) & MASK
     z = ((z ^ (z >> 27)) * MUL2) & MASK
@@ -31,7 +32,8 @@ def mix(z):
 
 
 def splitmix64_sequence(seed, count):
-    """The first ``count`` outputs of a SplitMix64 generator seeded with ``seed``."""
+    """The first ``count`` outputs of a SplitMix64 generator seeded with
+    ``seed`` (Steele, Lea & Flood 2014)."""
     state = seed & MASK
     out = []
     for _ in range(count):
@@ -41,18 +43,21 @@ def splitmix64_sequence(seed, count):
 
 
 def draw(seed, counter):
-    """The (counter+1)-th SplitMix64 output from ``seed``; counter may be negative."""
+    """The (counter+1)-th SplitMix64 output from ``seed`` (the counter form of
+    Steele, Lea & Flood 2014); counter may be negative."""
     return mix((seed + ((counter + 1) & MASK) * GAMMA) & MASK)
 
 
 def uniform(seed, band, frame, bands):
-    """u in [-1, 1) for one band and aligned frame."""
+    """u in [-1, 1) for one band and aligned frame: the heads' noise of section
+    2.3, in this project's deterministic reading."""
     z = draw(seed, frame * bands + band)
     return (z >> 40) * 2.0 ** -23 - 1.0
 
 
 def uniform_block(seed, t0, count, bands):
-    """u[t, b] for frames t0 .. t0+count-1 (frames may be negative), float64."""
+    """u[t, b] for frames t0 .. t0+count-1 (frames may be negative), float64:
+    the heads' noise of section 2.3."""
     import numpy as np
 
     out = np.empty((count, bands))

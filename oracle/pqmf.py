@@ -30,13 +30,15 @@ DEFAULT_BETA = 5.0
 
 
 def kaiser(n_taps, beta):
-    """Kaiser window w[n] = I0(beta sqrt(1 - (2n/(N-1) - 1)^2)) / I0(beta)."""
+    """Kaiser window w[n] = I0(beta sqrt(1 - (2n/(N-1) - 1)^2)) / I0(beta), the
+    PQMF prototype's window (Lin & Vaidyanathan 1998)."""
     n = np.arange(n_taps)
     arg = 1.0 - (2.0 * n / (n_taps - 1) - 1.0) ** 2
     return np.i0(beta * np.sqrt(np.maximum(arg, 0.0))) / np.i0(beta)
 
 
 def prototype(n_taps, wc, beta):
+    """Kaiser-windowed sinc prototype of cutoff wc (the PQMF of section 2.3's RAVE-like model)."""
     c = (n_taps - 1) / 2.0
     m = np.arange(n_taps) - c
     with np.errstate(invalid="ignore", divide="ignore"):
@@ -73,7 +75,8 @@ def design_cutoff(n_taps, bands, beta, grid=4000):
 
 
 def design(bands=16, n_taps=64, beta=DEFAULT_BETA):
-    """Returns (h, g, p, wc): analysis / synthesis filters [bands][n_taps], prototype."""
+    """The PQMF of section 2.3 (Nguyen 1994; Lin & Vaidyanathan 1998).  Returns
+    (h, g, p, wc): analysis / synthesis filters [bands][n_taps], prototype."""
     wc = design_cutoff(n_taps, bands, beta)
     p = prototype(n_taps, wc, beta)
     c = (n_taps - 1) / 2.0
@@ -89,11 +92,11 @@ def design(bands=16, n_taps=64, beta=DEFAULT_BETA):
 
 
 def analysis_weights(g):
-    """Conv(1 -> M) kernel [M][1][N] of the analysis layer."""
+    """Conv(1 -> M) kernel [M][1][N] of the analysis layer (section 2.3's multiband decomposition)."""
     return g[:, None, :].copy()
 
 
 def synthesis_weights(g):
-    """ConvT(M -> 1) kernel [M][1][N] of the synthesis layer."""
+    """ConvT(M -> 1) kernel [M][1][N] of the synthesis layer (section 2.3's multiband recomposition)."""
     bands = g.shape[0]
     return (bands * g)[:, None, :].copy()

@@ -158,3 +158,16 @@ print("clean")
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle\b", src, re.M), f
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every ctypes signature of the Python binding has as many arguments as the
+    C declaration (a missing or extra argument would shift the others)."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    decls = {}
+    for m in re.finditer(r"\b(cc_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+        params = m.group(2).strip()
+        decls[m.group(1)] = 0 if params in ("", "void") else len(params.split(","))
+    for name, argtypes in api._SIGNATURES.items():
+        assert name in decls, name
+        assert len(argtypes) == decls[name], (name, len(argtypes), decls[name])

@@ -171,3 +171,27 @@ def test_binding_argument_counts_match_the_header():
     for name, argtypes in api._SIGNATURES.items():
         assert name in decls, name
         assert len(argtypes) == decls[name], (name, len(argtypes), decls[name])
+
+
+def test_binding_argument_types_match_the_header():
+    """Scalar widths and pointer-ness of every argument agree with the header
+    (an int32 passed for an int64 would leave the upper half undefined)."""
+    import ctypes as C
+
+    scalar = {"int32_t": C.c_int32, "cc_status": C.c_int32, "int64_t": C.c_int64, "uint64_t": C.c_uint64,
+              "size_t": C.c_size_t,
+              "double": C.c_double}
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    for m in re.finditer(r"\b(cc_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", src):
+        name, params = m.group(1), m.group(2).strip()
+        if name not in api._SIGNATURES or params in ("", "void"):
+            continue
+        for i, (decl, t) in enumerate(zip(params.split(","), api._SIGNATURES[name])):
+            decl = " ".join(decl.split())
+            if "*" in decl:
+                is_ptr = t is C.c_void_p or t is C.c_char_p or (isinstance(t, type) and issubclass(t, C._Pointer))
+                assert is_ptr, (name, i, decl, t)
+            else:
+                ctype = decl.replace("const ", "").split()[0]
+                assert ctype in scalar, (name, i, decl)
+                assert t is scalar[ctype], (name, i, decl, t)

@@ -195,3 +195,47 @@ def test_binding_argument_types_match_the_header():
                 ctype = decl.replace("const ", "").split()[0]
                 assert ctype in scalar, (name, i, decl)
                 assert t is scalar[ctype], (name, i, decl, t)
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "cachedconv.h"
+int main(void) {
+  cc_node_desc nodes[2] = {0};
+  nodes[0].op = CC_OP_INPUT; nodes[0].c_in = 4; nodes[0].c_out = 4;
+  nodes[1].op = CC_OP_CONV; nodes[1].n_inputs = 1; nodes[1].inputs[0] = 0;
+  nodes[1].c_in = 4; nodes[1].c_out = 4; nodes[1].kernel = 3; nodes[1].stride = 1;
+  nodes[1].dilation = 1; nodes[1].pad_left = 1; nodes[1].pad_right = 1; nodes[1].has_bias = 1;
+  cc_model_config cfg = {CC_F32, 0, 1, 1, 0};
+  cc_model* m = NULL;
+  cc_status s = cc_model_create(nodes, 2, NULL, NULL, &cfg, &m);
+  if (s != CC_OK) { printf("create: %s %s\n", cc_status_str(s), cc_last_error()); return 1; }
+  int64_t d = -1;
+  s = cc_model_total_delay(m, &d);
+  printf("%d %lld\n", (int)s, (long long)d);
+  cc_model_destroy(m);
+  return 0;
+}
+"""
+
+
+def test_c_program_uses_the_abi(cclib):
+    """The header is plain C (C99, no warnings) and a C program links against
+    the library: a plan-only model (no GPU needed) of one k=3 conv with pads
+    1/1 reports the one-frame delay of the causal reconfiguration (section 3)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(api.library_path())
+    exe = os.path.join(libdir, "abi_c_check")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(root, "include"), "-x", "c", "-", "-L", libdir, "-lcachedconv",
+                        "-Wl,-rpath," + libdir, "-o", exe], input=C_PROGRAM, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.split() == ["0", "1"]

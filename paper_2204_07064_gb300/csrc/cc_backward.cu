@@ -197,12 +197,6 @@ struct BwdMerge {
   char* adj;
 };
 
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
 __global__ void k_bwd_merge(BwdMerge a) {
   const int64_t total = (int64_t)a.b.count * a.n * a.chans;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
@@ -223,11 +217,7 @@ __global__ void k_bwd_merge(BwdMerge a) {
       const float nz = fwd_ptr(a.b, s, a.in[2], t - a.A[2])[c];
       const float th = tanhf(w), sa = 1.f / (1.f + expf(-am)), sn = 1.f / (1.f + expf(-nz));
       float u = 0.f;
-      if (a.noise) {
-        const uint64_t seed = a.b.seeds[a.b.slots[s]];
-        const uint64_t counter = (uint64_t)((t - a.delay) * a.chans + c);
-        u = (float)(mix64(seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull) >> 40) * 0x1p-23f - 1.0f;
-      }
+      if (a.noise) u = noise_uniform(a.b.seeds[a.b.slots[s]], t - a.delay, c, a.chans);
       const float gw = g * (1.f - th * th) * sa, ga = g * th * sa * (1.f - sa), gn = g * u * sn * (1.f - sn);
       const float gs[3] = {gw, ga, gn};
       for (int k = 0; k < 3; ++k)

@@ -1,5 +1,5 @@
-// Device helpers shared by the kernels: ring addressing, activation and the
-// multi-view output store.
+// Device helpers shared by the kernels: ring addressing, activation, the
+// multi-view output store and the counter-based noise.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -71,6 +71,23 @@ __device__ __forceinline__ void store_views(const Batch& b, int32_t s, const Out
     reinterpret_cast<float*>(base + o.f32.off)[ring_row(t, o.f32.rows) * o.f32.chans + ch] = v;
   if (o.lp[0].rows) store_lp(base, o.lp[0], ring_row(t, o.lp[0].rows), ch, v);
   if (o.lp[1].rows) store_lp(base, o.lp[1], ring_row(t, o.lp[1].rows), ch, leaky(v));
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator: its
+// (n+1)-th output from `seed` is mix(seed + (n+1) * 0x9E3779B97F4A7C15), so
+// any (stream, band, frame) draws its value directly.
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// u in [-1, 1) (exact in float32) for band `band` of `bands` at frame
+// `frame`: counter = frame * bands + band.
+__device__ __forceinline__ float noise_uniform(uint64_t seed, int64_t frame, int32_t band, int32_t bands) {
+  const uint64_t counter = (uint64_t)(frame * bands + band);
+  const uint64_t z = splitmix_mix(seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull);
+  return (float)(z >> 40) * 0x1p-23f - 1.0f;
 }
 
 }  // namespace cc

@@ -426,20 +426,6 @@ __global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
 // ---------------------------------------------------------------------------
 // Element-wise kernels
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
-  // SplitMix64 output function (Steele, Lea & Flood 2014)
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ float noise_uniform(uint64_t seed, int64_t frame, int32_t band,
-                                               int32_t bands) {
-  const uint64_t counter = (uint64_t)(frame * bands + band);
-  const uint64_t z = splitmix_mix(seed + (counter + 1ull) * 0x9E3779B97F4A7C15ull);
-  return (float)(z >> 40) * 0x1p-23f - 1.0f;
-}
-
 // Input-manipulation noise: the same uniform draw, from the generator whose
 // seed is the stream seed XOR kInputNoiseTag (a domain apart from the heads'
 // noise), counter = frame * channels + channel over input frames.

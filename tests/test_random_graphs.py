@@ -1,7 +1,8 @@
 """Random streamable layer lists (seeded), CPU only.
 
 For each graph, a chain of dilated convs, strided convs, transposed convs and
-residual units (a branch conv added back to its input, Eq. 3 alignment):
+residual units (a branch conv added back to its input, Eq. 3 alignment), and
+in half of them a final heads merge of three branches of different reach:
 
 * the library's planning pass (a plan-only model, no GPU) reproduces the
   oracle's section 3 analysis node by node: cumulated delay, Eq. 2 extra
@@ -56,6 +57,14 @@ def random_graph(seed):
                 b = conv(b, int(rng.choice([1, 3])), 1, 1, f"r{i}b", W.LEAKY)
             nodes.append(W._node("add", [cur, b], C, C, bias=False, name=f"add{i}"))
             cur = len(nodes) - 1
+    if rng.random() < 0.5:
+        # the heads merge: three branches of different reach (Eq. 3 over three
+        # inputs; the noise is keyed on the aligned frame index)
+        br = [conv(cur, int(rng.choice([1, 3, 5, 7])), int(rng.integers(1, 3)), 1, f"h{q}", W.LEAKY)
+              for q in range(3)]
+        if rng.random() < 0.5:
+            br[2] = conv(br[2], 3, 1, 1, "h2b", W.LEAKY)
+        nodes.append(W._node("heads", br, C, C, bias=False, name="heads"))
     return nodes
 
 

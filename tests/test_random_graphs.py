@@ -114,3 +114,22 @@ def test_oracle_stream_and_delay_on_random_graphs(seed):
     if T - D > Wu:
         np.testing.assert_allclose(y_causal[Wu + D:], y_orig[Wu:T - D], rtol=0,
                                    atol=1e-12 * max(1.0, np.abs(y_orig).max()))
+
+
+@pytest.mark.parametrize("seed", SEEDS[:20])
+def test_torch_gradient_reference_forward_on_random_graphs(seed):
+    """The torch FP64 causal model (the gradient reference of the
+    differentiation form) equals the numpy causal model on the same random
+    graphs, noise on."""
+    import torch
+
+    from oracle import autodiff as AD
+
+    nodes = random_graph(seed)
+    p = W.init_params(nodes, 200 + seed)
+    info = M.analyze(nodes)
+    x = np.random.default_rng(2000 + seed).standard_normal((info["in_per_step"] * 8, nodes[0]["c_out"]))
+    ref = M.run_causal(nodes, p, x, seed=5)
+    pt = {i: (torch.tensor(w), None if b is None else torch.tensor(b)) for i, (w, b) in p.items()}
+    y = AD.causal_forward(nodes, pt, torch.tensor(x.T.copy()), seed=5).detach().numpy().T
+    np.testing.assert_allclose(y, ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))

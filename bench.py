@@ -283,34 +283,44 @@ class ClockSampler:
             self.proc = None
 
     @staticmethod
-    def parse(out, window=None):
+    def parse(out, window=None, fallback=None):
         """Summary of nvidia-smi rows; with `window` = (t0, t1) in time.time()
-        seconds, only the rows stamped inside it."""
+        seconds, only the rows stamped inside it.  When no row falls inside
+        (a timed region shorter than the sampling interval), the rows inside
+        `fallback` (a wall-clock interval of the same load right after it)
+        are used instead, and the summary says so."""
         import datetime
-        sm, mx, reasons, n_all = [], 0.0, set(), 0
+        rows = []
         for line in out.strip().splitlines():
             r = [f.strip() for f in line.split(",")]
             try:
                 ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
-                mhz, mhz_max = float(r[2]), float(r[3])
+                rows.append((ts, float(r[2]), float(r[3]),
+                             {name for name, v in zip(ClockSampler.REASONS, r[6:10]) if v.lower() == "active"}))
             except (ValueError, IndexError):
                 continue
-            n_all += 1
-            if window is not None and not (window[0] <= ts <= window[1]):
-                continue
-            sm.append(mhz)
-            mx = max(mx, mhz_max)
-            for name, v in zip(ClockSampler.REASONS, r[6:10]):
-                if v.lower() == "active":
-                    reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
-                    "samples_total": n_all,
-                    "note": "no sample fell inside the timed region"} if n_all else None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm), "samples_total": n_all}
+        if not rows:
+            return None
 
-    def stop(self, window=None):
+        def inside(iv):
+            return [x for x in rows if iv is None or iv[0] <= x[0] <= iv[1]]
+
+        picked, note = inside(window), None
+        if not picked and window is not None and fallback is not None:
+            picked = inside(fallback)
+            note = "no sample inside the timed region (shorter than the sampling interval); samples from the same " \
+                   "load right after it"
+        if not picked:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "samples_total": len(rows),
+                    "note": "no sample fell inside the timed region"}
+        out = {"sm_mhz": statistics.median(x[1] for x in picked), "sm_max_mhz": max(x[2] for x in picked),
+               "reasons": sorted(set().union(*(x[3] for x in picked))), "samples": len(picked),
+               "samples_total": len(rows)}
+        if note:
+            out["note"] = note
+        return out
+
+    def stop(self, window=None, fallback=None):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -319,7 +329,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        return self.parse(out, window)
+        return self.parse(out, window, fallback)
 
 
 def oracle_sample(steps, seed=1, stream_seed=11, warmup=1, kind="decoder", threads=1):
@@ -676,7 +686,6 @@ def main():
     wall1 = time.time()
     if dist:
         dist.barrier()
-    clk = clocks.stop((wall0, wall1))
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     # the first K2 = min(K, 500) of those steps again with the library's
@@ -689,6 +698,7 @@ def main():
             flush.zero_()
         model.process_batch(ss, z[args.warmup + k], y)
     torch.cuda.synchronize()
+    clk = clocks.stop((wall0, wall1), fallback=(wall1, time.time()))
     node_ms, node_launches = model.timing_read()
     model.timing(False)
     total_ms = max_over_ranks(total_ms, dist, dev)

@@ -33,6 +33,12 @@ def test_clock_samples_kept_only_inside_the_timed_window():
     empty = bench.ClockSampler.parse(out, (t + 1.0, t + 2.0))
     assert empty["samples"] == 0 and empty["sm_mhz"] is None
     assert bench.ClockSampler.parse("") is None
+    # a timed region shorter than the sampling interval: the samples of the
+    # same load right after it stand in, and the summary says so
+    short = bench.ClockSampler.parse(out, (t + 0.01, t + 0.02), fallback=(t + 0.02, t + 0.2))
+    assert short["samples"] == 2 and short["sm_mhz"] == 2055.0 and "right after" in short["note"]
+    inside_first = bench.ClockSampler.parse(out, (t, t + 0.2), fallback=(t + 0.2, t + 1.0))
+    assert inside_first["samples"] == 2 and "note" not in inside_first
 
 
 @pytest.mark.parametrize("workload", [bench.DEFAULT_WORKLOAD, "autoencoder-bf16-b256"])

@@ -136,7 +136,9 @@ def warmup_frames(nodes):
     not reproduce (the paper compensates latency but does not discuss this
     start-up effect).  An inner layer's left zero padding at negative times is
     replaced, in the causal model, by that layer's pre-roll output; a frame is
-    exact once none of its inputs reaches into such a region.  Conservative."""
+    exact once none of its inputs reaches into such a region.  For weights with
+    no zero tap (random weights) the count is tight: the frame just before it
+    differs."""
     n = len(nodes)
     bad = [0] * n
     zneg = [False] * n  # causal values at negative (original) times are zero
@@ -158,7 +160,10 @@ def warmup_frames(nodes):
             if zneg[u] and bad[u] == 0:
                 bad[i] = 0
             else:
-                bad[i] = max(0, bad[u] * s + k - 1 - p)
+                # full-output index f sums inputs q with 0 <= f - q*s < k; it is
+                # exact once its first input, ceil((f - k + 1) / s), is past the
+                # bad region: f >= s*bad[u] - s + k, i.e. cropped t >= that - p
+                bad[i] = max(0, bad[u] * s - s + k - p)
             zneg[i] = zneg[u] and not nd["bias"]
         elif op == "add":
             bad[i] = max(bad[u] for u in nd["inputs"])

@@ -343,10 +343,16 @@ cc_status cc_pqmf_design(int32_t bands, int32_t taps, double beta, double* analy
  * needing more is rejected with CC_ERR_INVALID_ARG (message in
  * cc_last_error).  The call makes no cudaMalloc / cudaFree or other
  * allocating call.  Its first call on a device looks up that device's copy
- * of the array (with the device current); make this first call before any
- * stream capture.  All calls share the one array and each overwrites it:
- * calls that overlap on the GPU (different CUDA streams, or other threads)
- * race; serialise them on one stream.  Asynchronous on cuda_stream. */
+ * of the array (with the device current); with the CUDA runtime's default
+ * lazy module loading that first lookup also loads the library's device code
+ * and reserves the array, which may allocate and synchronise.  So make one
+ * warm-up call per device outside the real-time path and before any stream
+ * capture: a call with n == 0 (the other pointers may then be NULL) does
+ * exactly this set-up and nothing else.  All calls share the one array and
+ * each overwrites it: calls that overlap on the GPU (different CUDA streams,
+ * or other threads) race; serialise them on one stream.  No pointer needs
+ * more than 4-byte alignment (the bias is copied into the array).
+ * Asynchronous on cuda_stream. */
 cc_status cc_cached_conv1d_static(const float* x, int64_t n, int32_t c_in, int32_t c_out,
                                   int32_t kernel, int32_t dilation, int32_t pad_left,
                                   int32_t pad_right, int32_t act_in, const float* weight,

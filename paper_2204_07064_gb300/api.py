@@ -358,6 +358,15 @@ def cached_conv1d_static(x, weight, bias, cache, y, dilation=1, pad_left=0, pad_
         _cuda_stream(cuda_stream)))
 
 
+def cached_conv1d_static_warmup(cuda_stream=None):
+    """The set-up of cc_cached_conv1d_static on the current device (an empty
+    call): looks up the device's copy of the static scratch, which may load
+    the library's device code.  Call once per device before the real-time
+    path and before any stream capture."""
+    _check(lib().cc_cached_conv1d_static(None, 0, 1, 1, 1, 1, 0, 0, 0, None, None, None, None,
+                                         _cuda_stream(cuda_stream)))
+
+
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_batch", C.c_int32), ("bucket", C.c_int32), ("use_graphs", C.c_int32),

@@ -55,17 +55,24 @@ cc_status scratch_for_current_device(unsigned char** out) {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Header (slot 0, zero steps), weights repacked [c_out][c_in][K] ->
-// [c_out][K][c_in], and the window ring: cached frames at times -hist..-1
-// (rows R-hist..R-1), the new buffer at times 0..n-1 (rows 0..n-1).
-__global__ void k_static_prepare(unsigned char* scratch, size_t w_off, size_t win_off, const float* x,
-                                 int64_t n, int32_t cin, int32_t cout, int32_t K, const float* w,
-                                 const float* cache, int32_t hist) {
+// Header (slot 0, zero steps), a copy of the bias (the convolution kernel
+// reads it four channels at a time, so it must be 16-byte aligned, which a
+// caller's pointer into a packed parameter buffer need not be), weights
+// repacked [c_out][c_in][K] -> [c_out][K][c_in], and the window ring: cached
+// frames at times -hist..-1 (rows R-hist..R-1), the new buffer at times
+// 0..n-1 (rows 0..n-1).
+__global__ void k_static_prepare(unsigned char* scratch, size_t b_off, size_t w_off, size_t win_off,
+                                 const float* x, int64_t n, int32_t cin, int32_t cout, int32_t K,
+                                 const float* w, const float* bias, const float* cache, int32_t hist) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if (tid == 0) {
     *reinterpret_cast<int32_t*>(scratch) = 0;
     *reinterpret_cast<int64_t*>(scratch + 8) = 0;
+  }
+  if (bias) {
+    float* B = reinterpret_cast<float*>(scratch + b_off);
+    for (int64_t i = tid; i < cout; i += stride) B[i] = bias[i];
   }
   float* A = reinterpret_cast<float*>(scratch + w_off);
   const int64_t nw = (int64_t)cout * cin * K;
@@ -120,11 +127,17 @@ extern "C" cc_status cc_cached_conv1d_static(const float* x, int64_t n, int32_t 
   const int64_t hist = (int64_t)pad_left + pad_right;
   if ((int64_t)(kernel - 1) * dilation > hist)
     return fail(CC_ERR_INVALID_ARG, "kernel span exceeds the padding: the layer cannot stream");
+  // the device's copy of the array is looked up before the empty-buffer
+  // return, so that a call with n == 0 is a warm-up that does the set-up
+  unsigned char* scratch = nullptr;
+  cc_status s = scratch_for_current_device(&scratch);
+  if (s) return s;
   if (n == 0) return CC_OK;
   if (!x || !weight || !y || (hist > 0 && !cache)) return fail(CC_ERR_INVALID_ARG, "null buffer");
   const size_t w_bytes = (size_t)c_out * c_in * kernel * sizeof(float);
   const size_t win_bytes = (size_t)(hist + n) * c_in * sizeof(float);
-  const size_t w_off = kHeaderBytes;
+  const size_t b_off = kHeaderBytes;
+  const size_t w_off = b_off + align256((size_t)c_out * sizeof(float));
   const size_t win_off = align256(w_off + w_bytes);
   const size_t need = win_off + align256(win_bytes);
   if (need > kStaticScratchBytes || hist + n > INT32_MAX)
@@ -132,19 +145,16 @@ extern "C" cc_status cc_cached_conv1d_static(const float* x, int64_t n, int32_t 
                 "layer needs %zu bytes of scratch (packed weights + %lld-frame window); the static "
                 "scratch holds %zu bytes",
                 need, (long long)(hist + n), kStaticScratchBytes);
-  unsigned char* scratch = nullptr;
-  cc_status s = scratch_for_current_device(&scratch);
-  if (s) return s;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   const int64_t prep_work = std::max<int64_t>((int64_t)c_out * c_in * kernel, (hist + n) * c_in);
-  k_static_prepare<<<grid_for(prep_work), 256, 0, st>>>(scratch, w_off, win_off, x, n, c_in, c_out,
-                                                         kernel, weight, cache, (int32_t)hist);
+  k_static_prepare<<<grid_for(prep_work), 256, 0, st>>>(scratch, b_off, w_off, win_off, x, n, c_in, c_out,
+                                                         kernel, weight, bias, cache, (int32_t)hist);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CC_ERR_CUDA, "prepare launch failed: %s", cudaGetErrorString(e));
 
   ConvArgs a{};
   a.A = reinterpret_cast<const float*>(scratch + w_off);
-  a.bias = bias;
+  a.bias = bias ? reinterpret_cast<const float*>(scratch + b_off) : nullptr;
   a.M = c_out;
   a.Kt = kernel * c_in;
   a.taps = kernel;

@@ -5,14 +5,19 @@ process audio: a real-time audio callback must not block (cudaMalloc can
 synchronise the device and take an unbounded time), and a plug-in embedded in
 a host may only use memory reserved up front.  For them the library offers a
 variant of its FP32 cached convolution whose scratch lives in a fixed device
-array.  This test calls it through the C ABI on two consecutive buffers and
-compares each output with the ordinary entry point (a model of one conv
-layer processed with cc_stream_process), within the FP32 tolerance the
-other parity tests use.  It runs last so that a failure here never hides
-another test's result."""
+array.  These tests call it through the C ABI on consecutive buffers and
+compare each output with the ordinary entry point (a model of one conv layer
+processed with cc_stream_process) and the concatenated outputs with the FP64
+oracle's causal convolution of the concatenated input, within the FP32
+tolerance the other parity tests use.  The cases reach every FP32 kernel
+shape the step can take, a buffer shorter than the cached history, uneven
+pads and a bias that is not 16-byte aligned; one test checks that calls after
+the warm-up leave device memory unchanged.  The file runs last so that a
+failure here never hides another test's result."""
 import numpy as np
 import pytest
 
+from oracle import conv as OC
 from oracle import metrics
 from paper_2204_07064_gb300 import api
 from paper_2204_07064_gb300 import workloads as W
@@ -21,36 +26,91 @@ pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-5
 
+# (c_in, c_out, kernel, dilation, pad_left, act, frames per call, calls); the
+# FP32 kernel each reaches: narrow (M <= 16, K*c_in <= 64), 64 x 64 tile,
+# skinny GEMV without / with 16-byte window loads, 128 x 128 tile
+CASES = [
+    (16, 16, 3, 2, 2, "leaky", 512, 2),     # narrow kernel, symmetric pads
+    (64, 32, 3, 9, 9, None, 300, 2),        # 64 x 64 tile
+    (6, 5, 3, 9, 9, "leaky", 3, 5),         # GEMV (c_in % 4 != 0); 3 frames < 18 cached: the cache wraps
+    (64, 40, 3, 1, 1, None, 16, 3),         # GEMV with vector loads (N < 32)
+    (32, 48, 5, 2, 2, None, 100, 2),        # uneven pads: 2 left, 6 right
+    (128, 256, 3, 1, 1, "leaky", 19456, 2), # 128 x 128 tile (>= 2 x 152 tiles)
+]
 
-@pytest.mark.parametrize("c_in,c_out,k,d,act,n", [(16, 16, 3, 2, "leaky", 512), (64, 32, 3, 9, None, 300)])
-def test_static_scratch_conv_matches_stream_process(cclib, cuda, c_in, c_out, k, d, act, n):
+
+def _layer(c_in, c_out, k, d, pad_left, act):
+    nodes = [W.input_node(c_in),
+             W._node("conv", [0], c_in, c_out, k=k, dilation=d, pad_left=pad_left,
+                     pad_right=(k - 1) * d - pad_left, act_in=act)]
+    return nodes, W.init_params(nodes, 3)
+
+
+@pytest.mark.parametrize("c_in,c_out,k,d,pad_left,act,n,calls", CASES)
+def test_static_scratch_conv_matches_stream_process_and_oracle(cclib, cuda, c_in, c_out, k, d, pad_left, act,
+                                                               n, calls):
     import torch
 
-    half = (k - 1) * d // 2
-    nodes = [W.input_node(c_in),
-             W._node("conv", [0], c_in, c_out, k=k, dilation=d, pad_left=half,
-                     pad_right=(k - 1) * d - half, act_in=act)]
-    params = W.init_params(nodes, 3)
+    hist = (k - 1) * d
+    pad_right = hist - pad_left
+    nodes, params = _layer(c_in, c_out, k, d, pad_left, act)
     w, b = params[1]
     model = api.Model(nodes, params, max_streams=1, max_steps_per_call=n)
     stream = model.stream()
     wt = torch.tensor(w, dtype=torch.float32, device=cuda)
-    bt = torch.tensor(b, dtype=torch.float32, device=cuda)
-    cache = torch.zeros(((k - 1) * d, c_in), dtype=torch.float32, device=cuda)
+    # the bias as a view one float into a larger buffer: 4-byte but not
+    # 16-byte aligned, as a pointer into a packed parameter block may be
+    bbuf = torch.zeros(c_out + 1, dtype=torch.float32, device=cuda)
+    bbuf[1:] = torch.tensor(b, dtype=torch.float32)
+    bt = bbuf[1:]
+    cache = torch.zeros((hist, c_in), dtype=torch.float32, device=cuda)
     rng = np.random.default_rng(7)
-    for call in range(2):
-        x = torch.tensor(rng.standard_normal((n, c_in)), dtype=torch.float32, device=cuda)
+    xs, outs = [], []
+    for call in range(calls):
+        xh = rng.standard_normal((n, c_in))
+        xs.append(xh)
+        x = torch.tensor(xh, dtype=torch.float32, device=cuda)
         y_ref = torch.empty((n, c_out), dtype=torch.float32, device=cuda)
         stream.process(x, y_ref)
         y = torch.full((n, c_out), float("nan"), dtype=torch.float32, device=cuda)
-        api.cached_conv1d_static(x, wt, bt, cache, y, dilation=d, pad_left=half,
-                                 pad_right=(k - 1) * d - half, act_in=act)
+        api.cached_conv1d_static(x, wt, bt, cache, y, dilation=d, pad_left=pad_left,
+                                 pad_right=pad_right, act_in=act)
         torch.cuda.synchronize()
         ref = y_ref.cpu().numpy().astype(np.float64)
         out = y.cpu().numpy().astype(np.float64)
         assert np.all(np.isfinite(out))
         err = metrics.max_abs(ref, out)
-        assert err <= FP32_TOL * metrics.rms(ref), f"call {call}: max-abs {err:.3e}"
+        assert err <= FP32_TOL * metrics.rms(ref), f"call {call}: max-abs {err:.3e} vs cc_stream_process"
+        outs.append(out)
+    # the FP64 oracle: Eq. 1 over the whole concatenated input, all padding on
+    # the left (section 3's reconfiguration), no right padding
+    x_all = np.concatenate(xs).T
+    want = OC.conv1d(OC.activate(x_all, act), w, b, 1, d, hist, 0).T
+    got = np.concatenate(outs)
+    err = metrics.max_abs(want, got)
+    assert err <= FP32_TOL * metrics.rms(want), f"max-abs {err:.3e} vs the oracle"
+
+
+def test_static_scratch_calls_leave_device_memory_unchanged(cclib, cuda):
+    import torch
+
+    c_in, c_out, k, d, n = 32, 32, 3, 4, 256
+    nodes, params = _layer(c_in, c_out, k, d, 4, "leaky")
+    w, b = params[1]
+    wt = torch.tensor(w, dtype=torch.float32, device=cuda)
+    bt = torch.tensor(b, dtype=torch.float32, device=cuda)
+    cache = torch.zeros(((k - 1) * d, c_in), dtype=torch.float32, device=cuda)
+    x = torch.randn((n, c_in), dtype=torch.float32, device=cuda)
+    y = torch.empty((n, c_out), dtype=torch.float32, device=cuda)
+    api.cached_conv1d_static_warmup()  # the one set-up call, outside the timed / real-time path
+    api.cached_conv1d_static(x, wt, bt, cache, y, dilation=d, pad_left=4, pad_right=4, act_in="leaky")
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info(cuda)[0], torch.cuda.memory_allocated(cuda)
+    for _ in range(8):
+        api.cached_conv1d_static(x, wt, bt, cache, y, dilation=d, pad_left=4, pad_right=4, act_in="leaky")
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(cuda)[0] == free0
+    assert torch.cuda.memory_allocated(cuda) == alloc0
 
 
 def test_static_scratch_rejects_oversized_layer(cclib, cuda):

@@ -127,12 +127,12 @@ def build_decoder(dtype, streams, seed=1, kind="decoder"):
 
     nodes = W.rave_decoder() if kind == "decoder" else W.chain(W.rave_encoder(), W.rave_decoder())
     params = W.init_params(nodes, seed)
-    _, g, _ = api.pqmf_design(16, 64, 5.0)
+    analysis, synthesis = api.pqmf_layer_weights(16, 64, 5.0)
     for i, nd in enumerate(nodes):
         if nd["name"] == "ipqmf":
-            params[i] = (api.inverse_pqmf_weights(g), None)
+            params[i] = (synthesis, None)
         if nd["name"] == "pqmf":
-            params[i] = (api.pqmf_analysis_weights(g), None)
+            params[i] = (analysis, None)
     model = api.Model(nodes, params, dtype=dtype, max_streams=streams, max_steps_per_call=1)
     return nodes, params, model
 
@@ -159,12 +159,12 @@ def run_differentiate(args):
     dec = W.rave_decoder()
     nodes = W.chain(enc, dec)
     params = W.init_params(nodes, 4)
-    _, g, _ = api.pqmf_design(16, 64, 5.0)
+    analysis, synthesis = api.pqmf_layer_weights(16, 64, 5.0)
     for i, nd in enumerate(nodes):
         if nd["name"] == "pqmf":
-            params[i] = (api.pqmf_analysis_weights(g), None)
+            params[i] = (analysis, None)
         if nd["name"] == "ipqmf":
-            params[i] = (api.inverse_pqmf_weights(g), None)
+            params[i] = (synthesis, None)
     count, chunks = args.diff_streams, args.diff_chunks
     model = api.Model(nodes, params, dtype="f32", max_streams=count, max_steps_per_call=1)
     streams = [model.stream(seed=s) for s in W.stream_seeds(4, count)]

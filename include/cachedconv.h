@@ -86,13 +86,19 @@ typedef struct {
 
 typedef struct {
   int32_t compute;            /* cc_dtype                                             */
-  int32_t max_streams;        /* number of per-stream state slots in the arena; 0 builds a
-                                 plan only (analysis queries, no device memory, no
-                                 weights needed; streams cannot be created)           */
+  int32_t max_streams;        /* number of per-stream state slots in the arena (with
+                                 arena_bytes > 0: an upper bound, 0 = none); both 0
+                                 builds a plan only (analysis queries, no device
+                                 memory, no weights needed; streams cannot be created) */
   int32_t max_steps_per_call; /* model steps one launch chain covers (longer buffers are
                                  split); sizes the per-slot scratch rows              */
   int32_t noise;              /* 1: heads add sigmoid(in2)*u; 0: u = 0 (section 4.2)  */
   int32_t flags;              /* CC_FLAG_* bits (0: defaults)                          */
+  int64_t arena_bytes;        /* > 0: device memory budget of the stream arena; the
+                                 model holds as many stream slots as fit
+                                 (floor(arena_bytes / slot bytes), capped by
+                                 max_streams if that is > 0), so streams are admitted
+                                 by cache memory; NO_MEMORY if not even one fits     */
 } cc_model_config;
 
 /* cc_model_config.flags: launch each convolution of a residual unit on its own
@@ -145,6 +151,9 @@ cc_status cc_model_node_info(const cc_model* model, int32_t node, int64_t* delay
                              int32_t* extra_delay, int32_t* align3, int32_t* kept_frames,
                              int32_t* frames_per_step);
 
+/* Stream slots of the arena (its admission capacity) and how many are free. */
+cc_status cc_model_capacity(const cc_model* model, int32_t* max_streams, int32_t* free_slots);
+
 /* Bytes of persistent cache state per stream (the cached padding of section
  * 2.2; section 4.1 measures it as the streaming method's only extra memory),
  * and bytes of one arena slot (state plus per-call rows). */
@@ -189,21 +198,59 @@ cc_status cc_stream_set_input_manipulation(cc_stream* stream, const float* scale
 /* Process one buffer (cached padding, section 2.2 and Fig. 1: every layer
  * reads its last frames from the stream's caches in place of zero padding):
  * n_in input frames ([n_in][in_channels]) -> n_out output frames
- * ([n_out][out_channels]).  n_in must be a multiple of in_per_step and
- * n_out == n_in / in_per_step * out_per_step (else BAD_LENGTH).  The output of
- * a call is the reconfigured model's output for these frames: it equals the
- * offline model's output delayed by cc_model_total_delay frames (section 4.2). */
+ * ([n_out][out_channels]).  Outside FIFO mode n_in must be a multiple of
+ * in_per_step and n_out == n_in / in_per_step * out_per_step (else
+ * BAD_LENGTH).  The output of a call is the reconfigured model's output for
+ * these frames: it equals the offline model's output delayed by
+ * cc_model_total_delay frames (section 4.2).  In FIFO mode (below) any
+ * lengths are accepted as long as the output asked for is queued or due. */
 cc_status cc_stream_process(cc_stream* stream, const float* in, int64_t n_in, float* out,
                             int64_t n_out, void* cuda_stream);
 
-/* Process one buffer for each of `count` distinct streams of one model in a
- * single launch chain (streams batched into the contraction's N dimension).
+/* Buffers that are not whole model steps (the paper's DSP call takes whatever
+ * buffer the host hands it, section 1; its model steps are the strided
+ * layers' alignment unit, section 3.1).  enable = 1 switches the stream to
+ * FIFO mode: input frames short of a whole step wait in the stream's input
+ * queue, a step runs as soon as its input is complete, and output frames wait
+ * in an output queue until a call asks for them.  The output queue starts
+ * with `prefill_frames` zero frames: the extra latency the caller accepts,
+ * added to the stream's delay (cc_stream_delay).  A call may ask for at most
+ * the queued frames plus those its input completes (else BAD_LENGTH, with no
+ * state changed).  For fixed calls of b input and b' output frames, prefill =
+ * out_per_step - gcd(b', out_per_step) serves every call (out_per_step - b'
+ * when b' divides out_per_step); a caller that attaches each model step's input
+ * to the first call needing its output needs none.  enable = 0 drops the
+ * queues and returns to whole-step calls.  cc_stream_reset empties the input
+ * queue and restores the prefill; the state blob does not carry the queues.
+ * All calls of a FIFO-mode stream must be ordered on one CUDA stream.
+ * Synchronises cuda_stream. */
+cc_status cc_stream_set_fifo(cc_stream* stream, int32_t enable, int64_t prefill_frames, void* cuda_stream);
+/* Latency of this stream's output, in output frames: cc_model_total_delay
+ * plus the FIFO prefill (section 4.2's latency compensation). */
+cc_status cc_stream_delay(const cc_stream* stream, int64_t* out_frames);
+/* Frames waiting in the FIFO queues (0 outside FIFO mode); either pointer may be NULL. */
+cc_status cc_stream_fifo_state(const cc_stream* stream, int64_t* in_frames, int64_t* out_frames);
+
+/* Process one buffer for each of `count` distinct streams of one model
+ * (a ragged batch): stream i gives n_in[i] input frames at in[i] and receives
+ * n_out[i] output frames at out[i] (host or device pointers; in[i] / out[i]
+ * may be NULL where the length is 0), each under cc_stream_process's length
+ * rules for its mode.  Streams that run the same number of model steps share
+ * one launch chain (streams batched into the contraction's N dimension); the
+ * buffers are staged through device memory.  A stream may appear only once. */
+cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, const float* const* in,
+                           const int64_t* n_in, float* const* out, const int64_t* n_out, int32_t count,
+                           void* cuda_stream);
+
+/* The fast form of cc_process_batch for equal-length buffers laid out with a
+ * fixed stride (no staging, so it can be captured in a CUDA graph):
  * in:  count buffers of n_in frames, stream i at in + i*in_stride (floats);
  * out: count buffers of n_out frames, stream i at out + i*out_stride.
- * Same length rules as cc_stream_process.  A stream may appear only once. */
-cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, int32_t count,
-                           const float* in, int64_t in_stride, int64_t n_in, float* out,
-                           int64_t out_stride, int64_t n_out, void* cuda_stream);
+ * Whole-step lengths only (cc_stream_process outside FIFO mode); streams in
+ * FIFO mode are refused (STATE). */
+cc_status cc_process_batch_strided(cc_model* model, cc_stream* const* streams, int32_t count,
+                                   const float* in, int64_t in_stride, int64_t n_in, float* out,
+                                   int64_t out_stride, int64_t n_out, void* cuda_stream);
 
 /* Checkpoint / resume (the paper has no counterpart): the whole stream state
  * (its arena slot, holding every cache of section 2.2, plus its step counter)
@@ -324,6 +371,14 @@ cc_status cc_server_stats(cc_server* server, int64_t* batches, int64_t* stream_s
  * The paper uses such a bank inside RAVE (section 2.3) but does not specify it. */
 cc_status cc_pqmf_design(int32_t bands, int32_t taps, double beta, double* analysis,
                          double* synthesis, double* cutoff);
+/* The same bank as the trained-layout weights of the two PQMF layers of a
+ * RAVE-like model: the analysis Conv1d(1 -> bands, kernel taps, stride bands),
+ * [bands][1][taps] = g_b (correlating with g_b filters by its time reverse,
+ * the analysis filter h_b), and the synthesis ConvTranspose1d(bands -> 1,
+ * kernel taps, stride bands), [bands][1][taps] = bands * g_b (the factor M of
+ * the cosine-modulated bank's reconstruction).  Either pointer may be NULL. */
+cc_status cc_pqmf_layer_weights(int32_t bands, int32_t taps, double beta, float* analysis_conv,
+                                float* synthesis_convt);
 
 /* One cached Conv1d step that allocates no device memory.  The paper has no
  * counterpart: this entry point exists for callers that must not allocate

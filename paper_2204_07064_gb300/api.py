@@ -40,7 +40,8 @@ class NodeDesc(C.Structure):
 
 class ModelConfig(C.Structure):
     _fields_ = [("compute", C.c_int32), ("max_streams", C.c_int32),
-                ("max_steps_per_call", C.c_int32), ("noise", C.c_int32), ("flags", C.c_int32)]
+                ("max_steps_per_call", C.c_int32), ("noise", C.c_int32), ("flags", C.c_int32),
+                ("arena_bytes", C.c_int64)]
 
 
 _LIB = None
@@ -61,7 +62,13 @@ _SIGNATURES = {
     "cc_stream_reset": [_P, _P],
     "cc_stream_set_input_manipulation": [_P, _P, _P, _P, _I32, _P],
     "cc_stream_process": [_P, _P, _I64, _P, _I64, _P],
-    "cc_process_batch": [_P, C.POINTER(_P), _I32, _P, _I64, _I64, _P, _I64, _I64, _P],
+    "cc_model_capacity": [_P, C.POINTER(_I32), C.POINTER(_I32)],
+    "cc_stream_set_fifo": [_P, _I32, _I64, _P],
+    "cc_stream_delay": [_P, C.POINTER(_I64)],
+    "cc_stream_fifo_state": [_P, C.POINTER(_I64), C.POINTER(_I64)],
+    "cc_process_batch": [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(_I64), C.POINTER(_P), C.POINTER(_I64),
+                         _I32, _P],
+    "cc_process_batch_strided": [_P, C.POINTER(_P), _I32, _P, _I64, _I64, _P, _I64, _I64, _P],
     "cc_stream_state_size": [_P, C.POINTER(_SZ)],
     "cc_stream_get_state": [_P, _P, _SZ, _P],
     "cc_stream_set_state": [_P, _P, _SZ, _P],
@@ -69,6 +76,7 @@ _SIGNATURES = {
     "cc_model_timing": [_P, _I32],
     "cc_model_timing_read": [_P, C.POINTER(_DBL), C.POINTER(_I64), _I32],
     "cc_pqmf_design": [_I32, _I32, _DBL, C.POINTER(_DBL), C.POINTER(_DBL), C.POINTER(_DBL)],
+    "cc_pqmf_layer_weights": [_I32, _I32, _DBL, _P, _P],
     "cc_cached_conv1d_static": [_P, _I64, _I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _P, _P,
                                 _P, _P],
     "cc_server_create": [_P, C.c_void_p, C.POINTER(_P)],
@@ -160,7 +168,7 @@ class Model:
     comparisons)."""
 
     def __init__(self, nodes, params, dtype="f32", max_streams=1, max_steps_per_call=1, noise=True,
-                 fuse_units=True, merge_siblings=True):
+                 fuse_units=True, merge_siblings=True, arena_bytes=0):
         L = lib()
         n = len(nodes)
         descs = (NodeDesc * n)(*[_desc(nd) for nd in nodes])
@@ -178,7 +186,7 @@ class Model:
                     self._keep.append(b32)
                     bp[i] = b32.ctypes.data
         cfg = ModelConfig(DTYPES[dtype], max_streams, max_steps_per_call, int(bool(noise)),
-                          (0 if fuse_units else 1) | (0 if merge_siblings else 2))
+                          (0 if fuse_units else 1) | (0 if merge_siblings else 2), int(arena_bytes))
         h = _P()
         _check(L.cc_model_create(descs, n, wp, bp, C.byref(cfg), C.byref(h)))
         self._keep = None
@@ -186,8 +194,8 @@ class Model:
         self.handle = h
         self.nodes = nodes
         self.dtype = dtype
-        self.max_streams = max_streams
         self.max_steps_per_call = max_steps_per_call
+        self.max_streams = self.capacity[0] if (max_streams or arena_bytes) else 0
 
     def close(self):
         if getattr(self, "handle", None):
@@ -223,6 +231,13 @@ class Model:
                     frames_per_step=u.value)
 
     @property
+    def capacity(self):
+        """(stream slots of the arena, free slots)."""
+        a, b = _I32(), _I32()
+        _check(lib().cc_model_capacity(self.handle, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    @property
     def state_bytes(self):
         a, b = _SZ(), _SZ()
         _check(lib().cc_model_state_bytes(self.handle, C.byref(a), C.byref(b)))
@@ -232,15 +247,28 @@ class Model:
         return Stream(self, seed, cuda_stream)
 
     def process_batch(self, streams, x, y, cuda_stream=None):
-        """x: [count][n_in][C_in], y: [count][n_out][C_out] float32 (device or host)."""
+        """Equal-length buffers (cc_process_batch_strided): x [count][n_in][C_in],
+        y [count][n_out][C_out] float32 (device or host)."""
         count = len(streams)
         arr = (_P * count)(*[s.handle for s in streams])
         n_in = x.shape[1]
         n_out = y.shape[1]
         in_stride = int(np.prod(x.shape[1:]))
         out_stride = int(np.prod(y.shape[1:]))
-        _check(lib().cc_process_batch(self.handle, arr, count, _ptr(x), in_stride, n_in, _ptr(y),
-                                      out_stride, n_out, _cuda_stream(cuda_stream)))
+        _check(lib().cc_process_batch_strided(self.handle, arr, count, _ptr(x), in_stride, n_in, _ptr(y),
+                                              out_stride, n_out, _cuda_stream(cuda_stream)))
+
+    def process_ragged(self, streams, xs, ys, cuda_stream=None):
+        """A ragged batch (cc_process_batch): stream i reads xs[i] [n_in_i][C_in]
+        and writes ys[i] [n_out_i][C_out] (float32, device or host; None for
+        an empty buffer)."""
+        count = len(streams)
+        arr = (_P * count)(*[s.handle for s in streams])
+        ip = (_P * count)(*[None if x is None else _ptr(x) for x in xs])
+        op = (_P * count)(*[None if y is None else _ptr(y) for y in ys])
+        ni = (_I64 * count)(*[0 if x is None else x.shape[0] for x in xs])
+        no = (_I64 * count)(*[0 if y is None else y.shape[0] for y in ys])
+        _check(lib().cc_process_batch(self.handle, arr, ip, ni, op, no, count, _cuda_stream(cuda_stream)))
 
     def device_status(self):
         """Raises CCError(TIMEOUT) if a bounded device wait gave up since the last call."""
@@ -278,6 +306,24 @@ class Stream:
 
     def reset(self, cuda_stream=None):
         _check(lib().cc_stream_reset(self.handle, _cuda_stream(cuda_stream)))
+
+    def set_fifo(self, enable=True, prefill=0, cuda_stream=None):
+        """FIFO mode: buffers of any length; the output queue starts with
+        `prefill` zero frames (added to the stream's delay)."""
+        _check(lib().cc_stream_set_fifo(self.handle, int(bool(enable)), int(prefill), _cuda_stream(cuda_stream)))
+
+    @property
+    def delay(self):
+        """Output latency of this stream in output frames (model delay + FIFO prefill)."""
+        v = _I64()
+        _check(lib().cc_stream_delay(self.handle, C.byref(v)))
+        return v.value
+
+    @property
+    def fifo_state(self):
+        a, b = _I64(), _I64()
+        _check(lib().cc_stream_fifo_state(self.handle, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def set_input_manipulation(self, scale=None, bias=None, noise=None, cuda_stream=None):
         """Latent manipulation: from the next step on, input frames enter the
@@ -333,15 +379,14 @@ def pqmf_design(bands=16, taps=64, beta=5.0):
     return h, g, wc.value
 
 
-def inverse_pqmf_weights(g):
-    """ConvT(bands -> 1) kernel [bands][1][taps] = bands * g_b."""
-    return (g.shape[0] * g)[:, None, :].copy()
-
-
-def pqmf_analysis_weights(g):
-    """Conv(1 -> bands) kernel [bands][1][taps] = g_b (correlating with g_b
-    filters by its time reverse, the analysis filter h_b)."""
-    return g[:, None, :].copy()
+def pqmf_layer_weights(bands=16, taps=64, beta=5.0):
+    """Trained-layout weights of the PQMF layers (cc_pqmf_layer_weights):
+    analysis Conv(1 -> bands) [bands][1][taps] and synthesis
+    ConvT(bands -> 1) [bands][1][taps], float32."""
+    a = np.zeros((bands, 1, taps), np.float32)
+    s = np.zeros((bands, 1, taps), np.float32)
+    _check(lib().cc_pqmf_layer_weights(bands, taps, beta, a.ctypes.data, s.ctypes.data))
+    return a, s
 
 
 def cached_conv1d_static(x, weight, bias, cache, y, dilation=1, pad_left=0, pad_right=0,

@@ -1,7 +1,7 @@
 """torch.autograd.Function over the streamed model (chunked, checkpointed).
 
 Forward: the input is streamed chunk by chunk through the library
-(cc_process_batch); before each chunk every stream's state is copied into a
+(cc_process_batch_strided); before each chunk every stream's state is copied into a
 device checkpoint (cc_stream_snapshot), so memory grows with the number of
 chunks times the per-stream cache, not with the signal's activations.
 Backward: the checkpoints are restored in reverse order and the library's

@@ -97,3 +97,16 @@ extern "C" cc_status cc_pqmf_design(int32_t bands, int32_t taps, double beta, do
   if (cutoff) *cutoff = wc;
   return CC_OK;
 }
+
+extern "C" cc_status cc_pqmf_layer_weights(int32_t bands, int32_t taps, double beta, float* analysis_conv,
+                                           float* synthesis_convt) {
+  if (bands < 2 || taps < 2 || beta < 0.0) return cc::fail(CC_ERR_INVALID_ARG, "bad PQMF size");
+  std::vector<double> g((size_t)bands * taps);
+  const cc_status s = cc_pqmf_design(bands, taps, beta, nullptr, g.data(), nullptr);
+  if (s) return s;
+  for (size_t i = 0; i < g.size(); ++i) {
+    if (analysis_conv) analysis_conv[i] = (float)g[i];
+    if (synthesis_convt) synthesis_convt[i] = (float)(bands * g[i]);
+  }
+  return CC_OK;
+}

@@ -921,6 +921,8 @@ Model::~Model() {
   }
   if (stage_in) cudaFree(stage_in);
   if (stage_out) cudaFree(stage_out);
+  if (rag_in) cudaFree(rag_in);
+  if (rag_out) cudaFree(rag_out);
   for (auto e : event_pool) cudaEventDestroy(e);
 }
 
@@ -931,15 +933,37 @@ Model::~Model() {
 // ===========================================================================
 using cc::fail;
 
-struct cc_stream {
-  cc::Model* model;
-  int32_t slot;
-  uint64_t seed;
-  int32_t* d_slot;
-  bool manip_set = false;  // a non-identity input manipulation is in place
-};
-
 namespace cc {
+// Device list of the batch's slots for launches on CUDA stream `st`: one list
+// per CUDA stream (batches on different streams may run concurrently),
+// re-uploaded only when the slots change.  The pinned staging buffer may
+// still feed the stream's previous upload, so that upload is waited for first.
+cc_status upload_slot_list(Model* m, const std::vector<int32_t>& slots, cudaStream_t st, const int32_t** d_list) {
+  Model::SlotList* L;
+  {
+    std::lock_guard<std::mutex> g(m->mu);
+    L = &m->slot_lists[st];
+    if (!L->d) {
+      if (cudaMalloc(&L->d, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
+          cudaMallocHost(&L->h, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
+          cudaEventCreateWithFlags(&L->uploaded, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CC_ERR_NO_MEMORY, "batch slot list");
+      }
+    }
+  }
+  if (!L->valid || L->cache != slots) {
+    CC_CUDA(cudaEventSynchronize(L->uploaded));
+    std::memcpy(L->h, slots.data(), sizeof(int32_t) * slots.size());
+    CC_CUDA(cudaMemcpyAsync(L->d, L->h, sizeof(int32_t) * slots.size(), cudaMemcpyHostToDevice, st));
+    CC_CUDA(cudaEventRecord(L->uploaded, st));
+    L->cache = slots;
+    L->valid = true;
+  }
+  *d_list = L->d;
+  return CC_OK;
+}
+
 int32_t stream_slot(const cc_stream* s) { return s->slot; }
 bool stream_manipulated(const cc_stream* s) { return s->manip_set; }
 Model* stream_model(const cc_stream* s) { return s->model; }
@@ -969,8 +993,8 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
   *out = nullptr;
   if (config->compute != CC_F32 && config->compute != CC_BF16 && config->compute != CC_F16)
     return fail(CC_ERR_INVALID_ARG, "unknown compute dtype %d", config->compute);
-  if (config->max_streams < 0 || config->max_steps_per_call <= 0)
-    return fail(CC_ERR_INVALID_ARG, "max_streams must be >= 0 and max_steps_per_call > 0");
+  if (config->max_streams < 0 || config->max_steps_per_call <= 0 || config->arena_bytes < 0)
+    return fail(CC_ERR_INVALID_ARG, "max_streams and arena_bytes must be >= 0 and max_steps_per_call > 0");
   auto* m = new cc::Model();
   m->dtype = config->compute;
   m->lp_dtype = config->compute == CC_F16 ? cc::kDtF16 : cc::kDtBF16;
@@ -986,6 +1010,17 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
     cc::plan_fusion(*m);
     cc::plan_siblings(*m);
     s = cc::plan_arena(*m);
+  }
+  if (!s && config->arena_bytes > 0) {
+    // admission by cache memory: as many slots as the byte budget holds
+    const int64_t fit = config->arena_bytes / (int64_t)m->slot_bytes;
+    int64_t slots = config->max_streams > 0 ? std::min<int64_t>(fit, config->max_streams) : fit;
+    slots = std::min<int64_t>(slots, INT32_MAX);
+    if (slots < 1)
+      s = fail(CC_ERR_NO_MEMORY, "arena budget of %lld bytes holds no stream slot (%zu bytes each)",
+               (long long)config->arena_bytes, m->slot_bytes);
+    else
+      m->max_streams = (int32_t)slots;
   }
   if (!s && m->max_streams == 0) {  // plan only: analysis queries, no device memory
     *out = reinterpret_cast<cc_model*>(m);
@@ -1044,6 +1079,7 @@ cc_status cc_model_destroy(cc_model* model) {
   if (m->max_streams > 0) cudaDeviceSynchronize();
   for (cc_stream* s : m->live_streams) {  // streams die with their model
     if (s->d_slot) cudaFree(s->d_slot);
+    cc::free_fifo(s);
     delete s;
   }
   m->live_streams.clear();
@@ -1080,6 +1116,15 @@ cc_status cc_model_node_info(const cc_model* model, int32_t node, int64_t* delay
     for (int q = 0; q < 3; ++q) align3[q] = p.A[q];
   if (kept) *kept = p.keep;
   if (fps) *fps = p.u;
+  return CC_OK;
+}
+
+cc_status cc_model_capacity(const cc_model* model, int32_t* max_streams, int32_t* free_slots) {
+  if (!model) return fail(CC_ERR_INVALID_ARG, "null model");
+  auto* m = const_cast<cc::Model*>(reinterpret_cast<const cc::Model*>(model));
+  std::lock_guard<std::mutex> g(m->mu);
+  if (max_streams) *max_streams = m->max_streams;
+  if (free_slots) *free_slots = (int32_t)m->free_slots.size();
   return CC_OK;
 }
 
@@ -1159,6 +1204,7 @@ cc_status cc_stream_destroy(cc_stream* s) {
   if (!s) return fail(CC_ERR_INVALID_ARG, "null stream");
   cudaDeviceSynchronize();
   cudaFree(s->d_slot);
+  cc::free_fifo(s);
   {
     cc::Model* m = s->model;
     std::lock_guard<std::mutex> g(m->mu);
@@ -1174,7 +1220,15 @@ cc_status cc_stream_destroy(cc_stream* s) {
 cc_status cc_stream_reset(cc_stream* s, void* cuda_stream) {
   if (!s) return fail(CC_ERR_INVALID_ARG, "null stream");
   s->manip_set = false;
-  return zero_slot(s->model, s->slot, s->seed, reinterpret_cast<cudaStream_t>(cuda_stream));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (s->fifo) {  // back to the state FIFO mode started in: no pending input, the prefill queued
+    const int32_t cout = s->model->nodes.back().d.c_out;
+    s->in_frames = 0;
+    s->out_cur = 0;
+    s->out_frames = s->prefill;
+    if (s->prefill) CC_CUDA(cudaMemsetAsync(s->out_q[0], 0, sizeof(float) * s->prefill * cout, st));
+  }
+  return zero_slot(s->model, s->slot, s->seed, st);
 }
 
 cc_status cc_stream_set_input_manipulation(cc_stream* s, const float* scale, const float* bias,
@@ -1199,14 +1253,15 @@ cc_status cc_stream_process(cc_stream* s, const float* in, int64_t n_in, float* 
                             void* cuda_stream) {
   if (!s) return fail(CC_ERR_INVALID_ARG, "null stream");
   cc::Model* m = s->model;
+  if (s->fifo) return cc::process_ragged(m, &s, &in, &n_in, &out, &n_out, 1, reinterpret_cast<cudaStream_t>(cuda_stream));
   const int32_t cin = m->nodes.front().d.c_in, cout = m->nodes.back().d.c_out;
   return m->process(s->d_slot, 1, in, n_in * cin, n_in, out, n_out * cout, n_out,
                     reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
-cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, int32_t count, const float* in,
-                           int64_t in_stride, int64_t n_in, float* out, int64_t out_stride, int64_t n_out,
-                           void* cuda_stream) {
+cc_status cc_process_batch_strided(cc_model* model, cc_stream* const* streams, int32_t count, const float* in,
+                                   int64_t in_stride, int64_t n_in, float* out, int64_t out_stride, int64_t n_out,
+                                   void* cuda_stream) {
   if (!model || !streams || count <= 0) return fail(CC_ERR_INVALID_ARG, "null argument or empty batch");
   auto* m = reinterpret_cast<cc::Model*>(model);
   if (count > m->max_streams) return fail(CC_ERR_INVALID_ARG, "batch larger than max_streams");
@@ -1214,6 +1269,8 @@ cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, int32_t c
   std::vector<int32_t> slots(count);
   for (int i = 0; i < count; ++i) {
     if (!streams[i] || streams[i]->model != m) return fail(CC_ERR_INVALID_ARG, "stream %d not of this model", i);
+    if (streams[i]->fifo)
+      return fail(CC_ERR_STATE, "stream %d is in FIFO mode: use cc_process_batch or cc_stream_process", i);
     slots[i] = streams[i]->slot;
   }
   {
@@ -1222,29 +1279,19 @@ cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, int32_t c
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
       return fail(CC_ERR_INVALID_ARG, "a stream appears twice in one batch");
   }
-  cc::Model::SlotList* L;
-  {
-    std::lock_guard<std::mutex> g(m->mu);
-    L = &m->slot_lists[st];
-    if (!L->d) {
-      if (cudaMalloc(&L->d, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
-          cudaMallocHost(&L->h, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
-          cudaEventCreateWithFlags(&L->uploaded, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(CC_ERR_NO_MEMORY, "batch slot list");
-      }
-    }
-  }
-  if (!L->valid || L->cache != slots) {
-    // the pinned staging buffer may still feed this CUDA stream's previous upload
-    CC_CUDA(cudaEventSynchronize(L->uploaded));
-    std::memcpy(L->h, slots.data(), sizeof(int32_t) * count);
-    CC_CUDA(cudaMemcpyAsync(L->d, L->h, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
-    CC_CUDA(cudaEventRecord(L->uploaded, st));
-    L->cache = slots;
-    L->valid = true;
-  }
-  return m->process(L->d, count, in, in_stride, n_in, out, out_stride, n_out, st);
+  const int32_t* d_list = nullptr;
+  cc_status r = cc::upload_slot_list(m, slots, st, &d_list);
+  if (r) return r;
+  return m->process(d_list, count, in, in_stride, n_in, out, out_stride, n_out, st);
+}
+
+cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, const float* const* in,
+                           const int64_t* n_in, float* const* out, const int64_t* n_out, int32_t count,
+                           void* cuda_stream) {
+  if (!model || !streams || !n_in || !n_out || count <= 0)
+    return fail(CC_ERR_INVALID_ARG, "null argument or empty batch");
+  auto* m = reinterpret_cast<cc::Model*>(model);
+  return cc::process_ragged(m, streams, in, n_in, out, n_out, count, reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
 cc_status cc_stream_state_size(const cc_stream* s, size_t* bytes) {

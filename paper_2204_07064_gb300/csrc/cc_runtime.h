@@ -100,6 +100,10 @@ struct Model {
   float* stage_in = nullptr;
   float* stage_out = nullptr;
   size_t stage_in_bytes = 0, stage_out_bytes = 0;
+  // ragged-batch / FIFO staging: one row of whole steps per stream
+  float* rag_in = nullptr;
+  float* rag_out = nullptr;
+  size_t rag_in_bytes = 0, rag_out_bytes = 0;
   // per-node timing
   bool timing_on = false;
   std::vector<TimingRec> timing_recs;
@@ -121,4 +125,30 @@ struct Model {
   cudaError_t take_event(cudaEvent_t* ev);
 };
 
+}  // namespace cc
+
+// A stream: one arena slot of cache state (section 2.2), its noise seed, and,
+// in FIFO mode (buffers that need not be whole model steps), the input frames
+// still short of a step and the output frames produced but not yet delivered.
+struct cc_stream {
+  cc::Model* model;
+  int32_t slot;
+  uint64_t seed;
+  int32_t* d_slot;
+  bool manip_set = false;  // a non-identity input manipulation is in place
+  bool fifo = false;
+  int64_t prefill = 0;     // zero output frames queued when FIFO mode was switched on
+  float* in_q = nullptr;   // [in_per_step][in channels] device: pending input frames
+  int64_t in_frames = 0;
+  float* out_q[2] = {nullptr, nullptr};  // [out_cap][out channels] device, ping-pong
+  int64_t out_frames = 0, out_cap = 0;
+  int32_t out_cur = 0;
+};
+
+namespace cc {
+// FIFO and ragged-batch processing (cc_batch.cu)
+cc_status process_ragged(Model* m, cc_stream* const* streams, const float* const* in, const int64_t* n_in,
+                         float* const* out, const int64_t* n_out, int32_t count, cudaStream_t st);
+cc_status upload_slot_list(Model* m, const std::vector<int32_t>& slots, cudaStream_t st, const int32_t** d_list);
+void free_fifo(cc_stream* s);
 }  // namespace cc

@@ -114,6 +114,16 @@ def test_host_pqmf_design_matches_oracle(cclib):
         assert abs(wc - wc2) < 1e-12
 
 
+def test_host_pqmf_layer_weights_match_oracle(cclib):
+    """The PQMF layers' trained-layout weights come from the library: analysis
+    conv g_b, synthesis convT bands * g_b (float32 of the same design)."""
+    a, s = api.pqmf_layer_weights(16, 64, 5.0)
+    _, g, _, _ = pqmf.design(16, 64, 5.0)
+    assert a.shape == s.shape == (16, 1, 64) and a.dtype == s.dtype == np.float32
+    np.testing.assert_allclose(a, pqmf.analysis_weights(g), rtol=0, atol=1e-7)
+    np.testing.assert_allclose(s, pqmf.synthesis_weights(g), rtol=0, atol=16e-7)
+
+
 def test_missing_library_fails_loudly():
     """No CPU fallback: with the library absent, the first call raises."""
     import subprocess
@@ -206,7 +216,7 @@ int main(void) {
   nodes[1].op = CC_OP_CONV; nodes[1].n_inputs = 1; nodes[1].inputs[0] = 0;
   nodes[1].c_in = 4; nodes[1].c_out = 4; nodes[1].kernel = 3; nodes[1].stride = 1;
   nodes[1].dilation = 1; nodes[1].pad_left = 1; nodes[1].pad_right = 1; nodes[1].has_bias = 1;
-  cc_model_config cfg = {CC_F32, 0, 1, 1, 0};
+  cc_model_config cfg = {CC_F32, 0, 1, 1, 0, 0};
   cc_model* m = NULL;
   cc_status s = cc_model_create(nodes, 2, NULL, NULL, &cfg, &m);
   if (s != CC_OK) { printf("create: %s %s\n", cc_status_str(s), cc_last_error()); return 1; }

@@ -99,6 +99,9 @@ typedef struct {
                                  (floor(arena_bytes / slot bytes), capped by
                                  max_streams if that is > 0), so streams are admitted
                                  by cache memory; NO_MEMORY if not even one fits     */
+  int64_t wait_limit_ns;      /* limit of every device-side pipeline wait (0: 2 s);
+                                 a wait that runs out records TIMEOUT (see
+                                 cc_model_device_status) instead of hanging          */
 } cc_model_config;
 
 /* cc_model_config.flags: launch each convolution of a residual unit on its own
@@ -266,9 +269,18 @@ cc_status cc_stream_set_state(cc_stream* stream, const void* host_blob, size_t b
  * and reports whether any tensor-core pipeline wait of this model gave up
  * since the last call (TIMEOUT, *code = bit set of the
  * waiting roles: 1 producer, 2 epilogue, 4 MMA issuer); clears the record.
- * Such a wait is bounded (2 s) so that a stalled pipeline returns instead of
- * hanging the GPU; the affected outputs are then undefined. */
+ * Such a wait is bounded (cc_model_config.wait_limit_ns) so that a stalled
+ * pipeline returns instead of hanging the GPU: the kernel lets the copies it
+ * issued land, frees its tensor memory and exits; the affected outputs are
+ * then undefined, and the streams of that call should be reset. */
 cc_status cc_model_device_status(cc_model* model, int32_t* code);
+/* Failure-detection test hook: each of the next `launches` tensor-core
+ * launches of this model leaves, in its first CTA, the window rows of the
+ * first K slice unrequested, so that CTA's pipeline waits run out after
+ * wait_limit_ns and cc_model_device_status reports TIMEOUT.  Nothing faults
+ * or hangs: every wait gives up and the kernel returns.  0 turns it off.
+ * Synchronises the device.  STATE for a plan-only model. */
+cc_status cc_model_test_withhold_copy(cc_model* model, int32_t launches);
 
 /* Per-node device timing for measurement (the paper has no counterpart; its
  * section 4.1 times whole buffers).  CUDA events are recorded around every

@@ -41,7 +41,7 @@ class NodeDesc(C.Structure):
 class ModelConfig(C.Structure):
     _fields_ = [("compute", C.c_int32), ("max_streams", C.c_int32),
                 ("max_steps_per_call", C.c_int32), ("noise", C.c_int32), ("flags", C.c_int32),
-                ("arena_bytes", C.c_int64)]
+                ("arena_bytes", C.c_int64), ("wait_limit_ns", C.c_int64)]
 
 
 _LIB = None
@@ -73,6 +73,7 @@ _SIGNATURES = {
     "cc_stream_get_state": [_P, _P, _SZ, _P],
     "cc_stream_set_state": [_P, _P, _SZ, _P],
     "cc_model_device_status": [_P, C.POINTER(_I32)],
+    "cc_model_test_withhold_copy": [_P, _I32],
     "cc_model_timing": [_P, _I32],
     "cc_model_timing_read": [_P, C.POINTER(_DBL), C.POINTER(_I64), _I32],
     "cc_pqmf_design": [_I32, _I32, _DBL, C.POINTER(_DBL), C.POINTER(_DBL), C.POINTER(_DBL)],
@@ -168,7 +169,7 @@ class Model:
     comparisons)."""
 
     def __init__(self, nodes, params, dtype="f32", max_streams=1, max_steps_per_call=1, noise=True,
-                 fuse_units=True, merge_siblings=True, arena_bytes=0):
+                 fuse_units=True, merge_siblings=True, arena_bytes=0, wait_limit_ns=0):
         L = lib()
         n = len(nodes)
         descs = (NodeDesc * n)(*[_desc(nd) for nd in nodes])
@@ -186,7 +187,8 @@ class Model:
                     self._keep.append(b32)
                     bp[i] = b32.ctypes.data
         cfg = ModelConfig(DTYPES[dtype], max_streams, max_steps_per_call, int(bool(noise)),
-                          (0 if fuse_units else 1) | (0 if merge_siblings else 2), int(arena_bytes))
+                          (0 if fuse_units else 1) | (0 if merge_siblings else 2), int(arena_bytes),
+                          int(wait_limit_ns))
         h = _P()
         _check(L.cc_model_create(descs, n, wp, bp, C.byref(cfg), C.byref(h)))
         self._keep = None
@@ -275,6 +277,16 @@ class Model:
         code = _I32()
         _check(lib().cc_model_device_status(self.handle, C.byref(code)))
         return code.value
+
+    def device_status_code(self):
+        """(status, role bits) of cc_model_device_status, without raising."""
+        code = _I32()
+        st = lib().cc_model_device_status(self.handle, C.byref(code))
+        return st, code.value
+
+    def test_withhold_copy(self, launches=1):
+        """Failure-detection test hook (cc_model_test_withhold_copy)."""
+        _check(lib().cc_model_test_withhold_copy(self.handle, int(launches)))
 
     def timing(self, enable):
         _check(lib().cc_model_timing(self.handle, int(enable)))

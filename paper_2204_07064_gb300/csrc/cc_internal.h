@@ -111,7 +111,9 @@ struct TcArgs {
   int32_t k2, act2;
   Ring skip;
   Batch batch;
-  int32_t* err;  // device error word: set when a bounded wait gives up
+  int32_t* err;      // device error word: set when a bounded wait gives up
+  uint64_t wait_ns;  // limit of every pipeline wait
+  int32_t* withhold;  // failure-detection test counter (see the producer)
 };
 
 struct HeadsArgs {

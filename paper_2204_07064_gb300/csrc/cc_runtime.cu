@@ -683,6 +683,8 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
         }
         a.batch = batch;
         a.err = err;
+        a.wait_ns = wait_ns;
+        a.withhold = withhold;
         // 3D window boxes: stride 1 and a box of min(ncols, 128) frames that
         // tiles the 128-column halves of a tile exactly
         int li = -1;
@@ -910,6 +912,7 @@ Model::~Model() {
     if (p.dscale) cudaFree(p.dscale);
   }
   if (err) cudaFree(err);
+  if (withhold) cudaFree(withhold);
   if (arena) cudaFree(arena);
   if (counters) cudaFree(counters);
   if (seeds) cudaFree(seeds);
@@ -993,13 +996,16 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
   *out = nullptr;
   if (config->compute != CC_F32 && config->compute != CC_BF16 && config->compute != CC_F16)
     return fail(CC_ERR_INVALID_ARG, "unknown compute dtype %d", config->compute);
-  if (config->max_streams < 0 || config->max_steps_per_call <= 0 || config->arena_bytes < 0)
-    return fail(CC_ERR_INVALID_ARG, "max_streams and arena_bytes must be >= 0 and max_steps_per_call > 0");
+  if (config->max_streams < 0 || config->max_steps_per_call <= 0 || config->arena_bytes < 0 ||
+      config->wait_limit_ns < 0)
+    return fail(CC_ERR_INVALID_ARG,
+                "max_streams, arena_bytes and wait_limit_ns must be >= 0 and max_steps_per_call > 0");
   auto* m = new cc::Model();
   m->dtype = config->compute;
   m->lp_dtype = config->compute == CC_F16 ? cc::kDtF16 : cc::kDtBF16;
   m->max_streams = config->max_streams;
   m->max_steps = config->max_steps_per_call;
+  if (config->wait_limit_ns > 0) m->wait_ns = (uint64_t)config->wait_limit_ns;
   m->noise = config->noise ? 1 : 0;
   m->fuse_units = (config->flags & CC_FLAG_NO_UNIT_FUSION) ? 0 : 1;
   m->merge_siblings = (config->flags & CC_FLAG_NO_SIBLING_MERGE) ? 0 : 1;
@@ -1049,10 +1055,11 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
              cudaMalloc(&m->in_manip, sizeof(float) * manip_floats) != cudaSuccess ||
 
              cudaMalloc(&m->err, sizeof(int32_t)) != cudaSuccess ||
-             false))
+             cudaMalloc(&m->withhold, sizeof(int32_t)) != cudaSuccess))
     s = fail(CC_ERR_NO_MEMORY, "model bookkeeping allocation failed");
   if (!s && (cudaMemset(m->counters, 0, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
              cudaMemset(m->err, 0, sizeof(int32_t)) != cudaSuccess ||
+             cudaMemset(m->withhold, 0, sizeof(int32_t)) != cudaSuccess ||
              cudaMemset(m->seeds, 0, sizeof(uint64_t) * m->max_streams) != cudaSuccess))
     s = fail(CC_ERR_CUDA, "memset failed");
   if (!s) {  // every slot starts with the identity input manipulation
@@ -1340,6 +1347,15 @@ cc_status cc_model_device_status(cc_model* model, int32_t* code) {
   }
   if (code) *code = v;
   if (v) return fail(CC_ERR_TIMEOUT, "a bounded device wait gave up (code %d)", v);
+  return CC_OK;
+}
+
+cc_status cc_model_test_withhold_copy(cc_model* model, int32_t launches) {
+  if (!model || launches < 0) return fail(CC_ERR_INVALID_ARG, "null model or negative count");
+  auto* m = reinterpret_cast<cc::Model*>(model);
+  if (!m->withhold) return fail(CC_ERR_STATE, "a plan-only model launches nothing");
+  CC_CUDA(cudaDeviceSynchronize());
+  CC_CUDA(cudaMemcpy(m->withhold, &launches, sizeof(int32_t), cudaMemcpyHostToDevice));
   return CC_OK;
 }
 

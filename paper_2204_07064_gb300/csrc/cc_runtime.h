@@ -78,6 +78,8 @@ struct Model {
   size_t slot_bytes = 0, state_bytes = 0, weight_bytes = 0;
   char* arena = nullptr;
   int32_t* err = nullptr;  // device error word (bounded waits that gave up)
+  int32_t* withhold = nullptr;  // failure-detection test counter (launches left to withhold a copy)
+  uint64_t wait_ns = 2000000000ull;  // limit of every device-side pipeline wait
   int64_t* counters = nullptr;
   uint64_t* seeds = nullptr;
   float* in_manip = nullptr;  // [max_streams][3][input channels]: per-slot scale, bias, noise amplitude

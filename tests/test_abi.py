@@ -216,7 +216,7 @@ int main(void) {
   nodes[1].op = CC_OP_CONV; nodes[1].n_inputs = 1; nodes[1].inputs[0] = 0;
   nodes[1].c_in = 4; nodes[1].c_out = 4; nodes[1].kernel = 3; nodes[1].stride = 1;
   nodes[1].dilation = 1; nodes[1].pad_left = 1; nodes[1].pad_right = 1; nodes[1].has_bias = 1;
-  cc_model_config cfg = {CC_F32, 0, 1, 1, 0, 0};
+  cc_model_config cfg = {CC_F32, 0, 1, 1, 0, 0, 0};
   cc_model* m = NULL;
   cc_status s = cc_model_create(nodes, 2, NULL, NULL, &cfg, &m);
   if (s != CC_OK) { printf("create: %s %s\n", cc_status_str(s), cc_last_error()); return 1; }

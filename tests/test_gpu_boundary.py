@@ -102,7 +102,7 @@ def test_ragged_batch_rejects_bad_lengths_and_duplicates(cclib, cuda):
 
 
 def test_fifo_decoder_sub_step_buffers(cclib, cuda):
-    """A decoder whose model step emits 64 samples, asked for 16-sample buffers:
+    """A decoder whose model step emits 32 samples, asked for 8-sample buffers:
     each step's latent frame comes with the first call that needs its output,
     so no prefill is needed and the delay is the model's."""
     import torch
@@ -110,14 +110,14 @@ def test_fifo_decoder_sub_step_buffers(cclib, cuda):
     nodes, p = _small_decoder()
     model = api.Model(nodes, p, max_streams=1, max_steps_per_call=1)
     ops = model.io["out_per_step"]
-    assert ops == 64
+    assert ops == 32
     s = model.stream(seed=5)
     s.set_fifo(True, prefill=0)
     assert s.delay == model.total_delay
     frames = 6
     z = W.signal(9, frames, 16)
     outs, sent, asked = [], 0, 0
-    for b in [16] * (frames * ops // 16):
+    for b in [8] * (frames * ops // 8):
         asked += b
         need = -(-asked // ops)
         x = torch.tensor(z[sent:need], dtype=torch.float32, device=cuda).reshape(need - sent, 16)
@@ -129,7 +129,7 @@ def test_fifo_decoder_sub_step_buffers(cclib, cuda):
     _check(ref, np.concatenate(outs).astype(np.float64))
     assert s.fifo_state == (0, 0)
     # asking for output whose input has not come is refused, with nothing changed
-    y = torch.empty((16, 1), dtype=torch.float32, device=cuda)
+    y = torch.empty((8, 1), dtype=torch.float32, device=cuda)
     with pytest.raises(api.CCError) as e:
         s.process(torch.empty((0, 16), dtype=torch.float32, device=cuda), y)
     assert e.value.status == -3

@@ -820,8 +820,8 @@ def main():
         u_in = info_u[nd["inputs"][0]] if nd["inputs"] else info_u[i]
         b = node_bytes(nd, u_in, info_u[i]) * streams * frames
         avg_s = node_ms[i] / node_launches[i] / 1000.0
-        kind = {"input": "k_input", "heads": "k_heads", "add": "k_add"}.get(nd["op"], "FP32 conv kernel")
-        kernels.append({"node": nd["name"] or nd["op"], "kernel": kind, "bound": "hbm",
+        kname = {"input": "k_input", "heads": "k_heads", "add": "k_add"}.get(nd["op"], "FP32 conv kernel")
+        kernels.append({"node": nd["name"] or nd["op"], "kernel": kname, "bound": "hbm",
                         "bytes_per_launch": b, "avg_launch_us": avg_s * 1e6,
                         "achieved_gbs": b / avg_s / 1e9, "peak_gbs": hbm_peak,
                         "frac": b / avg_s / 1e9 / hbm_peak, "share_of_step": node_ms[i] / ev_total if ev_total else None})

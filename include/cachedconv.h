@@ -115,13 +115,6 @@ typedef struct {
  * right-aligned and their outputs side by side in one ring; the results are
  * identical). */
 #define CC_FLAG_NO_SIBLING_MERGE 2
-/* cc_model_config.flags: launch every layer of the chain on its own (the
- * low-precision path otherwise runs the suffix of layers that read only their
- * own stream's frames and fit one thread block -- for the RAVE-like decoder
- * everything after the third upsampler -- as one persistent kernel in which
- * each block takes a group of streams through all of them; the results agree
- * within the low-precision bar, not bit for bit). */
-#define CC_FLAG_NO_TAIL_FUSION 4
 
 typedef struct cc_model cc_model;
 typedef struct cc_stream cc_stream;

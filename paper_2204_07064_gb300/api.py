@@ -166,13 +166,11 @@ class Model:
     only); max_steps_per_call is the longest launch chain (longer buffers are
     split).  fuse_units / merge_siblings = False launch each convolution of a
     residual unit, and each sibling conv, on its own (identical results; for
-    comparisons); tail_fusion = False launches the stream-local tail of the
-    chain layer by layer instead of as one persistent kernel (results within
-    the low-precision bar).  arena_bytes > 0 sizes the arena by bytes
-    (admission by cache memory); wait_limit_ns bounds every device wait."""
+    comparisons).  arena_bytes > 0 sizes the arena by bytes (admission by
+    cache memory); wait_limit_ns bounds every device-side pipeline wait."""
 
     def __init__(self, nodes, params, dtype="f32", max_streams=1, max_steps_per_call=1, noise=True,
-                 fuse_units=True, merge_siblings=True, arena_bytes=0, wait_limit_ns=0, tail_fusion=True):
+                 fuse_units=True, merge_siblings=True, arena_bytes=0, wait_limit_ns=0):
         L = lib()
         n = len(nodes)
         descs = (NodeDesc * n)(*[_desc(nd) for nd in nodes])
@@ -190,8 +188,7 @@ class Model:
                     self._keep.append(b32)
                     bp[i] = b32.ctypes.data
         cfg = ModelConfig(DTYPES[dtype], max_streams, max_steps_per_call, int(bool(noise)),
-                          (0 if fuse_units else 1) | (0 if merge_siblings else 2) | (0 if tail_fusion else 4),
-                          int(arena_bytes),
+                          (0 if fuse_units else 1) | (0 if merge_siblings else 2), int(arena_bytes),
                           int(wait_limit_ns))
         h = _P()
         _check(L.cc_model_create(descs, n, wp, bp, C.byref(cfg), C.byref(h)))

@@ -23,8 +23,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcachedconv.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["cc_runtime.cu", "cc_batch.cu", "cc_kernels_f32.cu", "cc_kernels_tc.cu", "cc_kernels_tail.cu",
-           "cc_static.cu", "cc_server.cu",
+SOURCES = ["cc_runtime.cu", "cc_batch.cu", "cc_kernels_f32.cu", "cc_kernels_tc.cu", "cc_static.cu", "cc_server.cu",
            "cc_backward.cu", "cc_pqmf.cpp"]
 
 

@@ -14,7 +14,6 @@
 // no activation or with LeakyReLU already applied (read by tensor-core
 // layers, which stage them into shared memory unchanged).
 #pragma once
-#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -143,52 +142,6 @@ struct InputArgs {
   Batch batch;
 };
 
-// One op of the stream-local tail kernel (cc_kernels_tail.cu).  Frames per
-// model step replace the per-launch column counts: a call of `steps` steps has
-// u_cols * steps columns per stream.
-enum : int32_t { kTailTc = 0, kTailConv32 = 1, kTailHeads = 2, kTailAdd = 3 };
-struct TailOp {
-  int32_t kind;    // kTail*
-  int32_t u_cols;  // columns per stream per step (conv: output frames; convt: input frames)
-  int32_t out_u;   // frames per step of the node this op writes
-  int32_t is_last;  // writes the caller's buffer
-  // contraction: rows M (N = M rounded up to 16 for the MMA), Kt = taps * cin
-  int32_t M, N, Kt, nk, taps, cin, dil, hist, cout, phases, act, lp_bf16;
-  const void* A_tiled;  // tensor cores: [nk] pre-tiled 128 x 64 weight blocks (one M tile)
-  const float* scale;   // tensor cores: per weight row
-  const float* bias;    // [cout] or null
-  const float* A32;     // FP32 conv: packed [M][Kt]
-  Ring in;              // input view: low precision (tensor cores) or FP32
-  int32_t in_rows_per_slot, in_row_off;  // gather form: arena row of a view row
-  OutViews out;          // destination views (ext unused: the launch's)
-  int32_t has_skip, skip_A;
-  Ring skip;
-  // fused residual unit: second (1x1) contraction of M2 rows, N2 for the MMA
-  const void* A2_tiled;
-  const float* scale2;
-  const float* bias2;
-  int32_t k2, act2, M2, N2;
-  // heads / add
-  Ring hin[3];
-  int32_t hA[3];
-  int64_t hdelay;
-  int32_t bands, noise;
-};
-
-struct TailArgs {
-  const TailOp* ops;
-  const CUtensorMap* maps;  // per op: [0..7] boxes of 64 channels x 2^i rows x 1 slot, [8] row gathers
-  int32_t n_ops;
-  int32_t steps;
-  int32_t group;    // streams per CTA work item
-  int32_t advance;  // add `steps` to the group's step counters at the end
-  Batch batch;
-  float* ext;  // caller's buffer (last op): stream s at ext + s*ext_stride
-  int64_t ext_stride;
-  int32_t* err;
-  uint64_t wait_ns;
-};
-
 // Launch with programmatic stream serialization (see pdl_wait / pdl_release):
 // the kernel's prologue may overlap the previous kernel of the stream.
 template <typename... KArgs, typename... Args>
@@ -221,8 +174,5 @@ cudaError_t launch_advance(const Batch& b, int64_t steps, cudaStream_t st);
 cudaError_t launch_conv_tc(const void* tmap_t, const void* tmap_b, const TcArgs& a, int bn,
                            cudaStream_t st);
 int tc_tile_n(int64_t n_cols, int m_tiles);
-
-// The stream-local tail (cc_kernels_tail.cu): `grid` persistent CTAs.
-cudaError_t launch_tail(const TailArgs& a, int grid, cudaStream_t st);
 
 }  // namespace cc

@@ -568,167 +568,6 @@ static cc_status pack_and_upload(Model& m, const float* const* weights, const fl
 }
 
 // ---------------------------------------------------------------------------
-// The stream-local tail: the longest suffix of the launch chain whose launches
-// each read only their own streams' frames and fit one CTA (tensor-core
-// contractions of one 128-row weight tile without split-K, narrow FP32
-// convolutions, heads, unfused adds) runs as one persistent kernel.
-// ---------------------------------------------------------------------------
-namespace {
-struct LaunchRef {
-  int node;  // the launching node (run_chain's i)
-  int q;     // fused unit's 1x1 conv, or -1
-  int wi;    // the node whose output the launch writes
-};
-}  // namespace
-
-// The launches of run_chain after the input, in order (the same skips).
-static std::vector<LaunchRef> chain_launches(const Model& m) {
-  std::vector<LaunchRef> out;
-  const int n = (int)m.nodes.size();
-  for (int i = 1; i < n; ++i) {
-    const NodePlan& p = m.nodes[i];
-    if (p.d.op == CC_OP_ADD && p.fused) continue;
-    if (p.unit_fused) continue;
-    if (p.group_leader >= 0 && p.group_leader != i) continue;
-    const int qi = p.unit_next;
-    const NodePlan& r = qi >= 0 ? m.nodes[qi] : p;
-    const int wi = (r.d.op == CC_OP_CONV || r.d.op == CC_OP_CONVT) && r.fused_add >= 0 ? r.fused_add : (qi >= 0 ? qi : i);
-    if (wi != n - 1 && !m.nodes[wi].has_ring) continue;
-    out.push_back({i, qi, wi});
-  }
-  return out;
-}
-
-static int32_t round16(int32_t x) { return (x + 15) / 16 * 16; }
-
-static bool tail_eligible(const Model& m, const LaunchRef& L) {
-  const NodePlan& p = m.nodes[L.node];
-  const cc_node_desc& d = p.d;
-  if (d.op == CC_OP_HEADS || d.op == CC_OP_ADD) return true;
-  if (d.op != CC_OP_CONV && d.op != CC_OP_CONVT) return false;
-  if (d.op == CC_OP_CONV && d.stride != 1) return false;
-  if (p.engine == 0) return L.q < 0 && (int64_t)p.M * p.Kt <= 65536;
-  if (p.ksplit != 1 || p.Mpad != 128) return false;
-  if (L.q >= 0) {
-    const NodePlan& q = m.nodes[L.q];
-    if (q.Mpad != 128 || round16(p.M) % 32 != 0 || q.Kt > 128) return false;
-  }
-  return true;
-}
-
-static cc_status plan_tail(Model& m) {
-  m.tail_node = -1;
-  if (m.dtype == CC_F32 || !m.use_tail || m.max_streams == 0) return CC_OK;
-  const std::vector<LaunchRef> L = chain_launches(m);
-  int from = (int)L.size();
-  while (from > 0 && tail_eligible(m, L[from - 1])) --from;
-  bool any_tc = false;
-  for (int k = from; k < (int)L.size(); ++k) any_tc = any_tc || m.nodes[L[k].node].engine == 1;
-  if ((int)L.size() - from < 2 || !any_tc) return CC_OK;
-  const int n = (int)m.nodes.size();
-  std::vector<TailOp> ops;
-  std::vector<CUtensorMap> maps;
-  EncodeTiledFn enc = encode_tiled();
-  for (int k = from; k < (int)L.size(); ++k) {
-    const NodePlan& p = m.nodes[L[k].node];
-    const cc_node_desc& d = p.d;
-    const NodePlan* q = L[k].q >= 0 ? &m.nodes[L[k].q] : nullptr;
-    const NodePlan& r = q ? *q : p;
-    const NodePlan& w = m.nodes[L[k].wi];
-    TailOp o{};
-    o.out.f32 = w.view[0];
-    o.out.lp[0] = w.view[1];
-    o.out.lp[1] = w.view[2];
-    o.is_last = L[k].wi == n - 1;
-    o.out_u = w.u;
-    o.lp_bf16 = m.lp_dtype == kDtBF16;
-    std::vector<CUtensorMap> om(9);
-    std::memset(om.data(), 0, sizeof(CUtensorMap) * 9);
-    if (d.op == CC_OP_CONV || d.op == CC_OP_CONVT) {
-      const NodePlan& src = m.nodes[d.inputs[0]];
-      const bool convt = d.op == CC_OP_CONVT;
-      o.u_cols = convt ? src.u : p.u;
-      o.M = p.M;
-      o.N = round16(p.M);
-      o.Kt = p.Kt;
-      o.nk = p.Kt / 64;
-      o.taps = p.taps;
-      o.cin = d.c_in;
-      o.dil = convt ? 1 : d.dilation;
-      o.hist = p.group.empty() ? p.hist_need : p.group_hist;
-      o.cout = p.group.empty() ? d.c_out : p.M;
-      o.phases = p.phases;
-      o.act = d.act_in;
-      o.bias = p.dbias;
-      if (r.fused_add >= 0) {
-        o.has_skip = 1;
-        o.skip = m.nodes[r.fused_skip].view[0];
-        o.skip_A = r.fused_skip_A;
-      }
-      if (p.engine == 1) {
-        o.kind = kTailTc;
-        o.A_tiled = p.dA_tiled;
-        o.scale = p.dscale;
-        o.in = src.view[1 + d.act_in];
-        o.in_rows_per_slot = p.in_rows_per_slot;
-        o.in_row_off = p.in_row_off;
-        if (q) {
-          o.A2_tiled = q->dA_tiled;
-          o.scale2 = q->dscale;
-          o.bias2 = q->dbias;
-          o.k2 = q->Kt / 64;
-          o.act2 = q->d.act_in;
-          o.M2 = q->M;
-          o.N2 = round16(q->M);
-        }
-        // window boxes of one slot: 64 channels x 2^li rows of [slot][pre + R][C]
-        const Ring& in = o.in;
-        const size_t pitch = (size_t)in.chans * 2;
-        if (!enc) return fail(CC_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-        const cuuint64_t d3[3] = {(cuuint64_t)in.chans, (cuuint64_t)(in.pre + in.rows), (cuuint64_t)m.max_streams};
-        const cuuint64_t s3[2] = {(cuuint64_t)pitch, (cuuint64_t)m.slot_bytes};
-        const cuuint32_t e3[3] = {1, 1, 1};
-        for (int li = 0; li < 8; ++li) {
-          const cuuint32_t b3[3] = {64, 1u << li, 1};
-          if (b3[1] > d3[1]) continue;
-          const CUresult cr = enc(&om[li],
-                                  m.lp_dtype == kDtBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
-                                  3, m.arena + in.off - (int64_t)in.pre * (int64_t)pitch, d3, s3, b3, e3,
-                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-          if (cr != CUDA_SUCCESS) return fail(CC_ERR_CUDA, "tail box tensor map encoding failed (%d)", (int)cr);
-        }
-        std::memcpy(&om[8], p.tmapB, sizeof(CUtensorMap));
-      } else {
-        o.kind = kTailConv32;
-        o.A32 = p.dA;
-        o.in = src.view[0];
-      }
-    } else {
-      o.kind = d.op == CC_OP_HEADS ? kTailHeads : kTailAdd;
-      o.u_cols = p.u;
-      o.cout = d.c_out;
-      o.bands = d.c_out;
-      o.noise = m.noise;
-      o.hdelay = p.D;
-      for (int qq = 0; qq < d.n_inputs; ++qq) {
-        o.hin[qq] = m.nodes[d.inputs[qq]].view[0];
-        o.hA[qq] = p.A[qq];
-      }
-    }
-    ops.push_back(o);
-    maps.insert(maps.end(), om.begin(), om.end());
-  }
-  CC_CUDA(cudaMalloc(&m.tail_ops, sizeof(TailOp) * ops.size()));
-  CC_CUDA(cudaMemcpy(m.tail_ops, ops.data(), sizeof(TailOp) * ops.size(), cudaMemcpyHostToDevice));
-  CC_CUDA(cudaMalloc(&m.tail_maps, sizeof(CUtensorMap) * maps.size()));
-  CC_CUDA(cudaMemcpy(m.tail_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
-  m.tail_n_ops = (int32_t)ops.size();
-  m.tail_node = L[from].node;
-  return CC_OK;
-}
-
-// ---------------------------------------------------------------------------
 // One launch chain: `steps` model steps for every stream of `batch`.
 // ---------------------------------------------------------------------------
 cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_stride, float* out,
@@ -788,27 +627,6 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
     if (d.op == CC_OP_ADD && p.fused) continue;
     if (p.unit_fused) continue;  // computed by its producer's fused launch
     if (p.group_leader >= 0 && p.group_leader != i) continue;  // computed by its group's leader
-    if (i == tail_node) {
-      // every launch from here on, and the step-counter advance, as one
-      // persistent kernel over groups of streams
-      TailArgs a{};
-      a.ops = tail_ops;
-      a.maps = tail_maps;
-      a.n_ops = tail_n_ops;
-      a.steps = steps;
-      a.group = (batch.count + sm_count - 1) / sm_count;
-      a.advance = 1;
-      a.batch = batch;
-      a.ext = out;
-      a.ext_stride = out_stride;
-      a.err = err;
-      a.wait_ns = wait_ns;
-      const int32_t groups = (batch.count + a.group - 1) / a.group;
-      cc_status s = begin(i);
-      if (s) return s;
-      CC_CUDA(launch_tail(a, std::min(groups, sm_count), st));
-      return end();
-    }
     // a fused residual unit writes the 1x1 conv's (and its fused add's) output
     const int qi = p.unit_next;
     const NodePlan* q = qi >= 0 ? &nodes[qi] : nullptr;
@@ -1106,8 +924,6 @@ Model::~Model() {
   }
   if (stage_in) cudaFree(stage_in);
   if (stage_out) cudaFree(stage_out);
-  if (tail_ops) cudaFree(tail_ops);
-  if (tail_maps) cudaFree(tail_maps);
   if (rag_in) cudaFree(rag_in);
   if (rag_out) cudaFree(rag_out);
   for (auto e : event_pool) cudaEventDestroy(e);
@@ -1193,7 +1009,6 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
   m->noise = config->noise ? 1 : 0;
   m->fuse_units = (config->flags & CC_FLAG_NO_UNIT_FUSION) ? 0 : 1;
   m->merge_siblings = (config->flags & CC_FLAG_NO_SIBLING_MERGE) ? 0 : 1;
-  m->use_tail = (config->flags & CC_FLAG_NO_TAIL_FUSION) ? 0 : 1;
   m->nodes.resize(n_nodes);
   for (int i = 0; i < n_nodes; ++i) m->nodes[i].d = nodes[i];
   cc_status s = cc::validate_and_analyze(*m);
@@ -1234,13 +1049,6 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
     }
   }
   if (!s) s = cc::encode_gather_maps(*m);
-  if (!s) {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
-      m->sm_count = sms;
-    s = cc::plan_tail(*m);
-  }
   const size_t manip_floats = (size_t)3 * m->nodes.front().d.c_out * m->max_streams;
   if (!s && (cudaMalloc(&m->counters, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
              cudaMalloc(&m->seeds, sizeof(uint64_t) * m->max_streams) != cudaSuccess ||

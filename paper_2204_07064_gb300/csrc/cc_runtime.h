@@ -113,14 +113,6 @@ struct Model {
   size_t event_pool_used = 0;
 
   int32_t force_tile_n = 0;  // autotuning: every tensor-core layer uses this N tile
-  // stream-local tail (cc_kernels_tail.cu): the launches from node tail_node on
-  // run as one persistent kernel; tail_node < 0: none
-  int32_t use_tail = 1;
-  int32_t tail_node = -1;
-  int32_t tail_n_ops = 0;
-  TailOp* tail_ops = nullptr;        // device
-  CUtensorMap* tail_maps = nullptr;  // device, [n_ops][9]
-  int32_t sm_count = 148;
 
   ~Model();
   int32_t tile_n_for(const NodePlan& p, int64_t n_cols) const;

@@ -864,7 +864,7 @@ def main():
     step_sorted = sorted(step_ms)
     p50 = float(np.percentile(step_ms, 50))
     p99 = float(np.percentile(step_ms, 99))
-    launches_per_step = (sum(node_launches) / k2) + 1  # + the step-counter advance
+    launches_per_step = model.chain_launches * nsub  # every launch of one step's chains
     line = {
         "metric": METRIC, "value": value, "unit": "streams", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,

@@ -288,6 +288,9 @@ cc_status cc_model_test_withhold_copy(cc_model* model, int32_t launches);
  * synchronises and returns, per node, the summed milliseconds and launch count
  * since the last enable. */
 cc_status cc_model_timing(cc_model* model, int32_t enable);
+/* Kernels enqueued by the most recent launch chain of this model (one chain
+ * covers up to max_steps_per_call steps of one batch): for launch accounting. */
+cc_status cc_model_chain_launches(const cc_model* model, int32_t* launches);
 cc_status cc_model_timing_read(cc_model* model, double* ms_per_node, int64_t* launches_per_node,
                                int32_t n_nodes);
 

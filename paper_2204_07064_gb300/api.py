@@ -75,6 +75,7 @@ _SIGNATURES = {
     "cc_model_device_status": [_P, C.POINTER(_I32)],
     "cc_model_test_withhold_copy": [_P, _I32],
     "cc_model_timing": [_P, _I32],
+    "cc_model_chain_launches": [_P, C.POINTER(_I32)],
     "cc_model_timing_read": [_P, C.POINTER(_DBL), C.POINTER(_I64), _I32],
     "cc_pqmf_design": [_I32, _I32, _DBL, C.POINTER(_DBL), C.POINTER(_DBL), C.POINTER(_DBL)],
     "cc_pqmf_layer_weights": [_I32, _I32, _DBL, _P, _P],
@@ -288,6 +289,13 @@ class Model:
     def test_withhold_copy(self, launches=1):
         """Failure-detection test hook (cc_model_test_withhold_copy)."""
         _check(lib().cc_model_test_withhold_copy(self.handle, int(launches)))
+
+    @property
+    def chain_launches(self):
+        """Kernels the most recent launch chain enqueued."""
+        v = _I32()
+        _check(lib().cc_model_chain_launches(self.handle, C.byref(v)))
+        return v.value
 
     def timing(self, enable):
         _check(lib().cc_model_timing(self.handle, int(enable)))

@@ -78,6 +78,7 @@ struct ConvArgs {
   int32_t skip_A;
   Ring skip;
   Batch batch;
+  int32_t advance;  // last launch of a chain: add this many steps to the streams' counters
 };
 
 // Tensor-core form of ConvArgs: A is low precision [Mpad][Kt] stored as
@@ -162,6 +163,9 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 
 // FP32 kernels (cc_kernels_f32.cu)
 cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st);
+// The narrow FP32 kernel can advance the step counters itself (ConvArgs.advance)
+// when each of its 128-column blocks covers whole streams.
+bool conv_f32_can_advance(const ConvArgs& a);
 cudaError_t launch_heads(const HeadsArgs& a, cudaStream_t st);
 cudaError_t launch_add(const AddArgs& a, cudaStream_t st);
 cudaError_t launch_input(const InputArgs& a, cudaStream_t st);

@@ -362,16 +362,7 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
 // such layers take the general kernels.
 // ---------------------------------------------------------------------------
 template <int TM>
-__global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
-  __shared__ float As[TM * 64];
-  // weights are written once at model creation: staged before the wait
-  for (int i = threadIdx.x; i < a.M * a.Kt; i += 128) As[i] = a.A[i];
-  __syncthreads();
-  pdl_wait();
-  pdl_release();
-  const int32_t n = blockIdx.x * 128 + threadIdx.x;
-  const int32_t N = a.batch.count * a.ncols;
-  if (n >= N) return;
+__device__ __forceinline__ void small_column(const ConvArgs& a, int32_t n, const float* As) {
   const int32_t s = n / a.ncols, j = n - s * a.ncols;
   const float* col = ring_ptr<const float>(a.batch, s, a.in) + a.in.choff;
   const int32_t r0 =
@@ -397,8 +388,15 @@ __global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
 #pragma unroll
   for (int k = 0; k < 64; ++k) {
     if (k >= a.Kt) break;
+    const float4* w4 = reinterpret_cast<const float4*>(As + k * TM);
 #pragma unroll
-    for (int m = 0; m < TM; ++m) acc[m] = fmaf(As[m * a.Kt + k], xw[k], acc[m]);
+    for (int q = 0; q < TM / 4; ++q) {
+      const float4 w = w4[q];
+      acc[4 * q] = fmaf(w.x, xw[k], acc[4 * q]);
+      acc[4 * q + 1] = fmaf(w.y, xw[k], acc[4 * q + 1]);
+      acc[4 * q + 2] = fmaf(w.z, xw[k], acc[4 * q + 2]);
+      acc[4 * q + 3] = fmaf(w.w, xw[k], acc[4 * q + 3]);
+    }
   }
   // an output that is only the caller's buffer with the TM rows contiguous
   // there (one phase per row of one channel, or channels of one phase):
@@ -422,6 +420,35 @@ __global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
   for (int m = 0; m < TM; ++m) ms[m] = m;
   store_column<TM>(a, n, ms, acc, (a.cout % 4 == 0) && (a.M % 4 == 0));
 }
+
+template <int TM>
+__global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
+  // weights k-major ([Kt][TM], rows past M zero): the TM weights of one
+  // reduction index are four 16-byte broadcast reads
+  __shared__ __align__(16) float As[TM * 64];
+  // weights are written once at model creation: staged before the wait
+  for (int i = threadIdx.x; i < TM * a.Kt; i += 128) {
+    const int m = i / a.Kt, k = i - m * a.Kt;
+    As[k * TM + m] = m < a.M ? a.A[m * a.Kt + k] : 0.f;
+  }
+  __syncthreads();
+  pdl_wait();
+  pdl_release();
+  const int32_t n = blockIdx.x * 128 + threadIdx.x;
+  const int32_t N = a.batch.count * a.ncols;
+  if (n < N) small_column<TM>(a, n, As);
+  if (a.advance) {
+    // the last launch of the chain: this block's columns are whole streams
+    // (128 a multiple of the columns per stream, or equal to them); once every
+    // thread has read its stream's counter, the block advances them
+    __syncthreads();
+    const int32_t s0 = blockIdx.x * 128 / a.ncols;
+    const int32_t s1 = min((blockIdx.x * 128 + 127) / a.ncols + 1, a.batch.count);
+    if ((int32_t)threadIdx.x < s1 - s0)
+      const_cast<int64_t*>(a.batch.counters)[a.batch.slots[s0 + threadIdx.x]] += a.advance;
+  }
+}
+
 
 // ---------------------------------------------------------------------------
 // Element-wise kernels
@@ -461,22 +488,53 @@ __global__ void k_heads(const HeadsArgs a) {
     float* fo = a.out.f32.rows ? reinterpret_cast<float*>(base + a.out.f32.off) + (int64_t)rf * a.out.f32.chans
                                : nullptr;
     float* eo = a.out.ext ? a.out.ext + (int64_t)s * a.out.ext_stride + (int64_t)j * a.bands : nullptr;
+    // 16-byte loads of the branches and stores of the FP32 view when every
+    // row is 16-byte aligned (channel counts and offsets multiples of 4)
+    bool vec4 = (a.bands & 3) == 0 && (!fo || (reinterpret_cast<uintptr_t>(fo) & 15) == 0);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) vec4 = vec4 && (reinterpret_cast<uintptr_t>(in[q]) & 15) == 0;
     for (int32_t b0 = 0; b0 < a.bands; b0 += 16) {
       float v[3][16];
 #pragma unroll
       for (int q = 0; q < 3; ++q)
 #pragma unroll
-        for (int k = 0; k < 16; ++k) v[q][k] = b0 + k < a.bands ? in[q][b0 + k] : 0.f;
+        for (int k = 0; k < 16; k += 4) {
+          if (vec4 && b0 + k < a.bands) {
+            const float4 t4 = *reinterpret_cast<const float4*>(in[q] + b0 + k);
+            v[q][k] = t4.x;
+            v[q][k + 1] = t4.y;
+            v[q][k + 2] = t4.z;
+            v[q][k + 3] = t4.w;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[q][k + e] = b0 + k + e < a.bands ? in[q][b0 + k + e] : 0.f;
+          }
+        }
+      float y[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const int32_t b = b0 + k;
+        y[k] = tanhf(v[0][k]) * sigmoidf_(v[1][k]);
+        if (a.noise && b < a.bands) y[k] += sigmoidf_(v[2][k]) * noise_uniform(seed, t - a.delay, b, a.bands);
+      }
+#pragma unroll
+      for (int k = 0; k < 16; k += 4) {
+        const int32_t b = b0 + k;
         if (b >= a.bands) break;
-        float y = tanhf(v[0][k]) * sigmoidf_(v[1][k]);
-        if (a.noise) y += sigmoidf_(v[2][k]) * noise_uniform(seed, t - a.delay, b, a.bands);
-        if (fo) fo[b] = y;
-        if (eo) eo[b] = y;
-        if (a.out.lp[0].rows) store_lp(base, a.out.lp[0], r0, b, y);
-        if (a.out.lp[1].rows) store_lp(base, a.out.lp[1], r1, b, leaky(y));
+        if (fo && vec4) {
+          *reinterpret_cast<float4*>(fo + b) = make_float4(y[k], y[k + 1], y[k + 2], y[k + 3]);
+        } else if (fo) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (b + e < a.bands) fo[b + e] = y[k + e];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (b + e >= a.bands) break;
+          if (eo) eo[b + e] = y[k + e];
+          if (a.out.lp[0].rows) store_lp(base, a.out.lp[0], r0, b + e, y[k + e]);
+          if (a.out.lp[1].rows) store_lp(base, a.out.lp[1], r1, b + e, leaky(y[k + e]));
+        }
       }
     }
   }
@@ -543,11 +601,18 @@ int elementwise_grid(int64_t total) {
 
 }  // namespace
 
+static bool takes_small(const ConvArgs& a) { return a.M <= 16 && a.Kt <= 64 && a.cin % 4 == 0; }
+
+bool conv_f32_can_advance(const ConvArgs& a) {
+  return takes_small(a) && a.ncols > 0 && (a.ncols == 128 || 128 % a.ncols == 0);
+}
+
 cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
   const int64_t N = (int64_t)a.batch.count * a.ncols;
   if (N <= 0) return cudaSuccess;
+  if (a.advance && !conv_f32_can_advance(a)) return cudaErrorInvalidValue;
   auto tiles = [&](int bm, int bn) { return ((a.M + bm - 1) / bm) * ((N + bn - 1) / bn); };
-  if (a.M <= 16 && a.Kt <= 64 && a.cin % 4 == 0) {
+  if (takes_small(a)) {
     dim3 grid((unsigned)((N + 127) / 128));
     return launch_pdl(k_conv_small_f32<16>, grid, dim3(128), 0, st, a);
   }

@@ -604,6 +604,7 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
   // its reader is final when the reader starts (see k_conv_tc)
   std::vector<int> made_at(n, -1);
   int launches = 0;
+  bool advanced = false;  // the step counters were advanced by the last launch
   for (int i = 0; i < n; ++i) {
     NodePlan& p = nodes[i];
     const cc_node_desc& d = p.d;
@@ -722,6 +723,11 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
           a.skip_A = p.fused_skip_A;
         }
         a.batch = batch;
+        // the chain's last launch advances the step counters itself when it can
+        if (wi == last && conv_f32_can_advance(a)) {
+          a.advance = steps;
+          advanced = true;
+        }
         CC_CUDA(launch_conv_f32(a, st));
       }
     } else if (d.op == CC_OP_ADD) {
@@ -753,7 +759,11 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
     }
     if ((s = end())) return s;
   }
-  CC_CUDA(launch_advance(batch, steps, st));
+  if (!advanced) {
+    CC_CUDA(launch_advance(batch, steps, st));
+    ++launches;
+  }
+  last_chain_launches = launches;
   return CC_OK;
 }
 
@@ -1356,6 +1366,12 @@ cc_status cc_model_test_withhold_copy(cc_model* model, int32_t launches) {
   if (!m->withhold) return fail(CC_ERR_STATE, "a plan-only model launches nothing");
   CC_CUDA(cudaDeviceSynchronize());
   CC_CUDA(cudaMemcpy(m->withhold, &launches, sizeof(int32_t), cudaMemcpyHostToDevice));
+  return CC_OK;
+}
+
+cc_status cc_model_chain_launches(const cc_model* model, int32_t* launches) {
+  if (!model || !launches) return fail(CC_ERR_INVALID_ARG, "null argument");
+  *launches = reinterpret_cast<const cc::Model*>(model)->last_chain_launches;
   return CC_OK;
 }
 

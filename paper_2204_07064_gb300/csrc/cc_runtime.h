@@ -113,6 +113,7 @@ struct Model {
   size_t event_pool_used = 0;
 
   int32_t force_tile_n = 0;  // autotuning: every tensor-core layer uses this N tile
+  int32_t last_chain_launches = 0;  // kernels the most recent launch chain enqueued
 
   ~Model();
   int32_t tile_n_for(const NodePlan& p, int64_t n_cols) const;

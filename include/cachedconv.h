@@ -69,6 +69,14 @@ typedef enum {
   CC_BF16 = 1, /* BF16 operands on tensor cores (tcgen05), FP32 accumulation            */
   CC_F16 = 2   /* FP16 operands on tensor cores (tcgen05), FP32 accumulation            */
 } cc_dtype;
+/* In the BF16/FP16 modes a conv or convT runs on the tensor cores when
+ * c_in % 64 == 0 and c_out % 8 == 0.  It multiplies its activated input
+ * rounded to that type (nearest even) by its weights rounded row by row: each
+ * GEMM row (a conv's output channel over input channels and taps; a convT's
+ * output channel and output phase over input channels and that phase's taps)
+ * is scaled to max |w| = 1 before rounding, and the FP32 scale is applied to
+ * the FP32 accumulator.  Every other layer, and every value kept for merges,
+ * stays FP32. */
 
 /* One layer of the trained (non-causal) model, in topological order. */
 typedef struct {
@@ -303,17 +311,21 @@ cc_status cc_model_timing_read(cc_model* model, double* ms_per_node, int64_t* la
  * chunked form has no counterpart there.)
  *
  * Protocol, for streams processed forward chunk by chunk:
- *   forward:  before chunk c, cc_stream_snapshot each stream into a device
- *             buffer (cc_model_state_bytes slot + 16 bytes); process the chunk.
+ *   forward:  before chunk c, cc_snapshot_batch the streams into a device
+ *             buffer (cc_model_snapshot_bytes per stream); process the chunk.
  *   backward: cc_backward_begin once; then for c = last .. first:
- *             cc_stream_restore the chunk-c snapshots and call
+ *             cc_restore_batch the chunk-c snapshots and call
  *             cc_backward_chunk with chunk c's input and output gradient.
  * cc_backward_chunk recomputes the chunk's forward (the rings then hold its
  * activations), clears the adjoint rows no later chunk could have reached,
  * and propagates adjoints through the nodes in reverse order; the adjoint of
  * the cached frames a chunk read stays in the adjoint arena for the previous
  * chunk.  Weight / bias gradients accumulate in the cc_grads buffers.
- * FP32 models only (STATE otherwise).  All signal pointers are device memory:
+ * FP32 models, and low-precision models created with CC_FLAG_NO_UNIT_FUSION
+ * (STATE otherwise): the forward then runs in BF16/FP16 on the tensor cores
+ * and the gradients are those of that arithmetic, in FP32 -- the backward
+ * multiplies the rounded weights and the rounded activations the forward
+ * multiplied (a rounding's derivative taken as 1).  All signal pointers are device memory:
  * x [n_in][in_channels], grad_y [n_out][out_channels], grad_x (may be NULL)
  * [n_in][in_channels], stream i at base + i*stride.  n_in is a whole number
  * of model steps, at most max_steps_per_call. */
@@ -328,8 +340,20 @@ cc_status cc_backward_begin(cc_grads* grads, cc_stream* const* streams, int32_t 
 cc_status cc_backward_chunk(cc_grads* grads, cc_stream* const* streams, int32_t count, const float* x,
                             int64_t x_stride, int64_t n_in, const float* grad_y, int64_t gy_stride,
                             int64_t n_out, float* grad_x, int64_t gx_stride, void* cuda_stream);
-/* Device-side stream state copies (slot + step counter + noise seed), for
- * per-chunk checkpoints in bounded device memory; bytes = slot bytes + 16. */
+/* Device-side copies of streams' state for per-chunk checkpoints: the step
+ * counter, the noise seed and the cached padding itself -- every ring's kept
+ * rows (section 2.2's cache; section 4.1 measures it as the method's only
+ * extra memory), not the whole arena slot.  cc_model_snapshot_bytes gives the
+ * bytes per stream (16 + the cached state).  The batch forms copy `count`
+ * distinct streams of one model, stream i at dev_buf + i * that size (bytes =
+ * count x that size, dev_buf 8-byte aligned), with one kernel; restoring also
+ * rewrites the mirrored rows of low-precision views.  Asynchronous on
+ * cuda_stream. */
+cc_status cc_model_snapshot_bytes(const cc_model* model, size_t* bytes);
+cc_status cc_snapshot_batch(cc_model* model, cc_stream* const* streams, int32_t count, void* dev_buf, size_t bytes,
+                            void* cuda_stream);
+cc_status cc_restore_batch(cc_model* model, cc_stream* const* streams, int32_t count, const void* dev_buf,
+                           size_t bytes, void* cuda_stream);
 cc_status cc_stream_snapshot(cc_stream* stream, void* dev_buf, size_t bytes, void* cuda_stream);
 cc_status cc_stream_restore(cc_stream* stream, const void* dev_buf, size_t bytes, void* cuda_stream);
 

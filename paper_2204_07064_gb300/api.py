@@ -93,6 +93,9 @@ _SIGNATURES = {
     "cc_grads_read": [_P, _I32, _P, _P],
     "cc_backward_begin": [_P, _P, _I32, _P],
     "cc_backward_chunk": [_P, _P, _I32, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _P],
+    "cc_model_snapshot_bytes": [_P, C.POINTER(_SZ)],
+    "cc_snapshot_batch": [_P, C.POINTER(_P), _I32, _P, _SZ, _P],
+    "cc_restore_batch": [_P, C.POINTER(_P), _I32, _P, _SZ, _P],
     "cc_stream_snapshot": [_P, _P, _SZ, _P],
     "cc_stream_restore": [_P, _P, _SZ, _P],
     "cc_status_str": [_I32],
@@ -163,7 +166,7 @@ class Model:
     """A reconfigured model on the GPU: packed weights + stream-state arena.
 
     dtype "f32" runs FFMA kernels; "bf16" / "f16" run the contractions with
-    cin % 64 == 0 on the tensor cores.  max_streams sizes the arena (0: plan
+    cin % 64 == 0 and cout % 8 == 0 on the tensor cores.  max_streams sizes the arena (0: plan
     only); max_steps_per_call is the longest launch chain (longer buffers are
     split).  fuse_units / merge_siblings = False launch each convolution of a
     residual unit, and each sibling conv, on its own (identical results; for
@@ -508,11 +511,28 @@ class Server:
 
 
 def snapshot_bytes(model):
-    return model.state_bytes[1] + 16
+    """Bytes of one stream's checkpoint: counter, seed and the cached state."""
+    v = _SZ()
+    _check(lib().cc_model_snapshot_bytes(model.handle, C.byref(v)))
+    return v.value
+
+
+def snapshot_batch(model, streams, buf, cuda_stream=None):
+    """Checkpoints of `streams` into a uint8 CUDA tensor of len(streams) x snapshot_bytes."""
+    arr = (_P * len(streams))(*[s.handle for s in streams])
+    _check(lib().cc_snapshot_batch(model.handle, arr, len(streams), buf.data_ptr(), buf.numel(),
+                                   _cuda_stream(cuda_stream)))
+
+
+def restore_batch(model, streams, buf, cuda_stream=None):
+    arr = (_P * len(streams))(*[s.handle for s in streams])
+    _check(lib().cc_restore_batch(model.handle, arr, len(streams), buf.data_ptr(), buf.numel(),
+                                  _cuda_stream(cuda_stream)))
 
 
 class Grads:
-    """Gradient accumulators + adjoint arena of an FP32 model (cc_grads_*)."""
+    """Gradient accumulators + adjoint arena of a model (cc_grads_*): FP32, or
+    low precision created with fuse_units=False."""
 
     def __init__(self, model, params):
         n = len(model.nodes)

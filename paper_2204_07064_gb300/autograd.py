@@ -1,9 +1,10 @@
 """torch.autograd.Function over the streamed model (chunked, checkpointed).
 
 Forward: the input is streamed chunk by chunk through the library
-(cc_process_batch_strided); before each chunk every stream's state is copied into a
-device checkpoint (cc_stream_snapshot), so memory grows with the number of
-chunks times the per-stream cache, not with the signal's activations.
+(cc_process_batch_strided); before each chunk the streams' cached state (the
+kept rows of every ring, not the whole arena slot) is copied into a device
+checkpoint by one kernel (cc_snapshot_batch), so memory grows with the number
+of chunks times the per-stream cache, not with the signal's activations.
 Backward: the checkpoints are restored in reverse order and the library's
 hand-written backward (cc_backward_chunk) recomputes each chunk and
 propagates the adjoints, carrying the cache adjoint from chunk to chunk;
@@ -18,7 +19,9 @@ from . import api
 
 
 class StreamedRunner:
-    """An FP32 model, its streams, gradient buffers and the chunk length."""
+    """A model (FP32, or BF16/FP16 created with fuse_units=False: the forward
+    then runs on the tensor cores and the gradients are those of that
+    arithmetic), its streams, gradient buffers and the chunk length."""
 
     def __init__(self, model, params, streams, chunk_steps):
         self.model = model
@@ -39,19 +42,17 @@ class _Streamed(torch.autograd.Function):
             raise ValueError("input length must be a whole number of chunks")
         chunks = n_in // runner.in_chunk
         nb = api.snapshot_bytes(runner.model)
-        ckpt = torch.empty((chunks + 1, count, nb), dtype=torch.uint8, device=x.device)
+        ckpt = torch.empty((chunks + 1, count * nb), dtype=torch.uint8, device=x.device)
         y = torch.empty((count, chunks * runner.out_chunk, io["out_channels"]), dtype=torch.float32,
                         device=x.device)
         xs = x.detach().contiguous()
         for c in range(chunks):
-            for k, s in enumerate(runner.streams):
-                api.stream_snapshot(s, ckpt[c, k])
+            api.snapshot_batch(runner.model, runner.streams, ckpt[c])
             xc = xs[:, c * runner.in_chunk:(c + 1) * runner.in_chunk].contiguous()
             yc = torch.empty((count, runner.out_chunk, io["out_channels"]), dtype=torch.float32, device=x.device)
             runner.model.process_batch(runner.streams, xc, yc)
             y[:, c * runner.out_chunk:(c + 1) * runner.out_chunk] = yc
-        for k, s in enumerate(runner.streams):
-            api.stream_snapshot(s, ckpt[chunks, k])
+        api.snapshot_batch(runner.model, runner.streams, ckpt[chunks])
         ctx.save_for_backward(xs, ckpt)
         ctx.runner = runner
         ctx.chunks = chunks
@@ -65,15 +66,13 @@ class _Streamed(torch.autograd.Function):
         gx = torch.zeros_like(xs)
         runner.grads.begin(runner.streams)
         for c in reversed(range(ctx.chunks)):
-            for k, s in enumerate(runner.streams):
-                api.stream_restore(s, ckpt[c, k])
+            api.restore_batch(runner.model, runner.streams, ckpt[c])
             xc = xs[:, c * runner.in_chunk:(c + 1) * runner.in_chunk].contiguous()
             gyc = gy[:, c * runner.out_chunk:(c + 1) * runner.out_chunk].contiguous()
             gxc = torch.empty_like(xc)
             runner.grads.chunk(runner.streams, xc, gyc, gxc)
             gx[:, c * runner.in_chunk:(c + 1) * runner.in_chunk] = gxc
-        for k, s in enumerate(runner.streams):
-            api.stream_restore(s, ckpt[ctx.chunks, k])
+        api.restore_batch(runner.model, runner.streams, ckpt[ctx.chunks])
         return gx, None
 
 

@@ -17,8 +17,13 @@
 // chunk, only the rows that no later chunk could have touched are cleared.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "../../include/cachedconv.h"
 #include "cc_device.cuh"
@@ -35,26 +40,48 @@ namespace {
 
 using namespace cc;
 
-struct BwdView {
-  Ring r;          // FP32 view geometry (same offsets in both arenas)
-  int64_t t0;      // absolute time of the chunk's first frame at this node
+// Forward values a backward kernel reads: the view the forward computed with.
+// kind 0: FP32 pre-activation values (the consumer's activation is applied on
+// read); 1: low precision as computed; 2: low precision with LeakyReLU
+// applied (what a tensor-core layer multiplied; its sign is the pre-activation's).
+struct ValView {
+  Ring r;
+  int32_t kind, act, lp_bf16;
 };
 
-__device__ __forceinline__ float* adj_ptr(char* adj, int64_t slot_bytes, int32_t slot, const Ring& r,
-                                          int64_t t) {
-  return reinterpret_cast<float*>(adj + (int64_t)slot * slot_bytes + r.off) + ring_row(t, r.rows) * r.chans;
+__device__ __forceinline__ float load_lp(const void* p, bool bf16) {
+  const uint16_t h = *reinterpret_cast<const uint16_t*>(p);
+  return bf16 ? __bfloat162float(__ushort_as_bfloat16(h)) : __half2float(__ushort_as_half(h));
 }
 
-__device__ __forceinline__ const float* fwd_ptr(const Batch& b, int32_t s, const Ring& r, int64_t t) {
-  return reinterpret_cast<const float*>(slot_base(b, s) + r.off) + ring_row(t, r.rows) * r.chans;
+// The value the forward multiplied (activation applied) at time t, channel m.
+__device__ __forceinline__ float val_act(const Batch& b, int32_t s, const ValView& v, int64_t t, int32_t m) {
+  const char* base = slot_base(b, s) + v.r.off;
+  const int64_t row = ring_row(t, v.r.rows);
+  if (v.kind == 0) return activate(reinterpret_cast<const float*>(base)[row * v.r.chans + v.r.choff + m], v.act);
+  return load_lp(base + (row * v.r.chans + m) * 2, v.lp_bf16 != 0);
+}
+
+// The activation's derivative at that point (1 without activation).
+__device__ __forceinline__ float val_deriv(const Batch& b, int32_t s, const ValView& v, int64_t t, int32_t m) {
+  if (v.kind == 1 || (v.kind == 0 && !v.act)) return 1.f;
+  return val_act(b, s, v, t, m) >= 0.f ? 1.f : kLeakySlope;  // LeakyReLU keeps the sign
+}
+
+// Adjoint rows: an FP32 ring per node in the adjoint arena, indexed by the
+// node's absolute time like the forward rings.
+__device__ __forceinline__ float* adj_row(char* adj, int64_t adj_slot_bytes, int32_t slot, const Ring& r, int64_t t) {
+  return reinterpret_cast<float*>(adj + (int64_t)slot * adj_slot_bytes + r.off) + ring_row(t, r.rows) * r.chans;
 }
 
 __device__ __forceinline__ int64_t chunk_t0(const Batch& b, int32_t s, int32_t u, int32_t steps) {
   return (steps_of(b, s) - steps) * (int64_t)u;
 }
 
-// Zero the adjoint rows of times [t0 - keep, t0 + n - keep) for every stream.
-__global__ void k_adj_clear(Batch b, char* adj, Ring r, int32_t keep, int32_t n, int32_t steps) {
+// Zero the adjoint rows of times [t0 - keep, t0 + n - keep) for every stream:
+// the rows no later chunk (processed earlier, in reverse order) could have
+// written; rows [t0 + n - keep, t0 + n) hold the cache adjoint they left.
+__global__ void k_adj_clear(Batch b, char* adj, int64_t adj_slot_bytes, Ring r, int32_t keep, int32_t n, int32_t steps) {
   const int64_t total = (int64_t)b.count * n * r.chans;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = (int32_t)(i % r.chans);
@@ -62,122 +89,198 @@ __global__ void k_adj_clear(Batch b, char* adj, Ring r, int32_t keep, int32_t n,
     const int32_t j = (int32_t)(q % n);
     const int32_t s = (int32_t)(q / n);
     const int64_t t = chunk_t0(b, s, r.u, steps) - keep + j;
-    adj_ptr(adj, b.slot_bytes, b.slots[s], r, t)[c] = 0.f;
+    adj_row(adj, adj_slot_bytes, b.slots[s], r, t)[c] = 0.f;
   }
 }
 
 struct BwdConv {
-  const float* W;   // trained layout: conv [cout][cin][K], convt [cin][cout][K]
+  const float* Wt;  // weights per tap: [K][cout][cin] (what the forward multiplied)
   int32_t op;       // CC_OP_CONV / CC_OP_CONVT
-  int32_t cin, cout, K, S, dil, hist, act;
+  int32_t cin, cout, K, S, dil, hist;
   int32_t n_in, n_out;  // frames of this chunk per stream, input / output rate
-  Ring x;               // forward FP32 view of the input (pre-activation values)
+  ValView x;            // the forward's input values
   int32_t u_in, u_out;
   Ring gy;              // adjoint ring of the output node (rows == 0: gy_ext)
   const float* gy_ext;  // caller's output gradient, stream s at gy_ext + s*gy_stride
   int64_t gy_stride;
-  float* dW;  // trained layout accumulators
+  Ring gx;              // adjoint ring of the input node
+  float* dW;            // trained layout accumulators
   float* db;
   int32_t steps;
   Batch b;
   char* adj;
+  int64_t adj_slot_bytes;
 };
 
-__device__ __forceinline__ float load_gy(const BwdConv& a, int32_t s, int64_t t0_out, int32_t o, int32_t n) {
-  if (a.gy.rows == 0) return a.gy_ext[(int64_t)s * a.gy_stride + (int64_t)o * a.cout + n];
-  return adj_ptr(a.adj, a.b.slot_bytes, a.b.slots[s], a.gy, t0_out + o)[n];
+__device__ __forceinline__ const float* gy_row(const BwdConv& a, int32_t s, int64_t t_local, int64_t t0_out) {
+  if (a.gy.rows == 0) return a.gy_ext + (int64_t)s * a.gy_stride + t_local * a.cout;
+  return adj_row(a.adj, a.adj_slot_bytes, a.b.slots[s], a.gy, t0_out + t_local);
 }
 
-// dL/dx for input frames i in [-hist, n_in) of the chunk (history included),
-// times the LeakyReLU derivative, accumulated into the input's adjoint ring.
-// Only the chunk's own output frames contribute: later outputs were handled
-// by later chunks, which already scattered into these rows.
-__global__ void k_bwd_data(BwdConv a) {
-  const int32_t span = a.hist + a.n_in;
-  const int64_t total = (int64_t)a.b.count * span * a.cin;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t m = (int32_t)(idx % a.cin);
-    const int64_t q = idx / a.cin;
-    const int32_t i = (int32_t)(q % span) - a.hist;
-    const int32_t s = (int32_t)(q / span);
-    const int64_t t0_in = chunk_t0(a.b, s, a.u_in, a.steps), t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
-    float acc = 0.f;
-    if (a.op == CC_OP_CONV) {
-      for (int32_t k = 0; k < a.K; ++k) {
-        const int32_t jj = i + a.hist - k * a.dil;
-        if (jj < 0 || jj % a.S) continue;
-        const int32_t o = jj / a.S;
-        if (o >= a.n_out) continue;
-        for (int32_t n = 0; n < a.cout; ++n)
-          acc = fmaf(a.W[((int64_t)n * a.cin + m) * a.K + k], load_gy(a, s, t0_out, o, n), acc);
-      }
-    } else {
-      const int32_t T = a.K / a.S;
-      for (int32_t jj = 0; jj < T; ++jj) {
-        const int32_t qq = i + jj;  // output block fed by input frame i through tap jj
-        if (qq < 0 || qq >= a.n_in) continue;
-        for (int32_t ph = 0; ph < a.S; ++ph) {
-          const int32_t o = qq * a.S + ph;
-          const float* wrow = a.W + (int64_t)m * a.cout * a.K + ph + jj * a.S;
-          for (int32_t n = 0; n < a.cout; ++n) acc = fmaf(wrow[(int64_t)n * a.K], load_gy(a, s, t0_out, o, n), acc);
-        }
+constexpr int kBT = 64;  // output tile (rows x columns) of the backward GEMMs
+constexpr int kBC = 32;  // reduction chunk
+
+// dL/dW of this chunk as a GEMM per tap k: dW_k[n][m] += sum over columns
+// (stream, output frame) of gy[col][n] * x_k[col][m], x_k the value the
+// forward multiplied by tap k.  A block computes a 64 x 64 tile of one tap
+// over every column; 4 x 4 outputs per thread.  (A transposed convolution's
+// tap kk = ph + jj*S pairs output phase ph with input frame q - jj.)
+__global__ void __launch_bounds__(256) k_bwd_weight(BwdConv a) {
+  __shared__ __align__(16) float Gs[kBC][kBT + 4];
+  __shared__ __align__(16) float Xs[kBC][kBT + 4];
+  __shared__ const float* gp[kBC];
+  __shared__ int32_t xs_s[kBC];
+  __shared__ int64_t xs_t[kBC];
+  const int32_t n0 = blockIdx.x * kBT, m0 = blockIdx.y * kBT, kk = blockIdx.z;
+  const int32_t tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool convt = a.op == CC_OP_CONVT;
+  const int32_t ph = convt ? kk % a.S : 0, jj = convt ? kk / a.S : 0;
+  const int32_t ncol = convt ? a.n_in : a.n_out;
+  const int64_t total = (int64_t)a.b.count * ncol;
+  float acc[4][4] = {};
+  for (int64_t c0 = 0; c0 < total; c0 += kBC) {
+    if (threadIdx.x < kBC) {
+      const int64_t col = c0 + threadIdx.x;
+      gp[threadIdx.x] = nullptr;
+      xs_s[threadIdx.x] = -1;
+      if (col < total) {
+        const int32_t s = (int32_t)(col / ncol), o = (int32_t)(col - (int64_t)s * ncol);
+        const int64_t t0_in = chunk_t0(a.b, s, a.u_in, a.steps), t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
+        gp[threadIdx.x] = gy_row(a, s, convt ? (int64_t)o * a.S + ph : o, t0_out);
+        xs_s[threadIdx.x] = s;
+        xs_t[threadIdx.x] = convt ? t0_in + o - jj : t0_in + (int64_t)o * a.S + (int64_t)kk * a.dil - a.hist;
       }
     }
-    const int64_t t = t0_in + i;
-    if (a.act) {
-      const float xpre = fwd_ptr(a.b, s, a.x, t)[m];
-      acc *= xpre >= 0.f ? 1.f : kLeakySlope;
+    __syncthreads();
+    for (int e = threadIdx.x; e < kBC * kBT; e += 256) {
+      const int c = e / kBT, q = e - c * kBT;
+      float g = 0.f, x = 0.f;
+      if (gp[c]) {
+        if (n0 + q < a.cout) g = gp[c][n0 + q];
+        if (m0 + q < a.cin) x = val_act(a.b, xs_s[c], a.x, xs_t[c], m0 + q);
+      }
+      Gs[c][q] = g;
+      Xs[c][q] = x;
     }
-    adj_ptr(a.adj, a.b.slot_bytes, a.b.slots[s], a.x, t)[m] += acc;
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < kBC; ++c) {
+      const float4 g4 = *reinterpret_cast<const float4*>(&Gs[c][ty * 4]);
+      const float4 x4 = *reinterpret_cast<const float4*>(&Xs[c][tx * 4]);
+      const float g[4] = {g4.x, g4.y, g4.z, g4.w}, x[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) acc[i][j2] = fmaf(g[i], x[j2], acc[i][j2]);
+    }
+    __syncthreads();
   }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) {
+      const int32_t n = n0 + ty * 4 + i, m = m0 + tx * 4 + j2;
+      if (n >= a.cout || m >= a.cin) continue;
+      const int64_t w = convt ? ((int64_t)m * a.cout + n) * a.K + kk : ((int64_t)n * a.cin + m) * a.K + kk;
+      a.dW[w] += acc[i][j2];
+    }
 }
 
-// dL/dW and dL/db of this chunk, added to the accumulators; one thread per
-// weight, reduction over every stream and output frame of the chunk.
-__global__ void k_bwd_weight(BwdConv a) {
-  const int64_t total = (int64_t)a.cout * a.cin * a.K;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    float acc = 0.f, bacc = 0.f;
-    if (a.op == CC_OP_CONV) {
-      // idx -> (n, k, m), m fastest for coalesced input reads
-      const int32_t m = (int32_t)(idx % a.cin);
-      const int64_t r = idx / a.cin;
-      const int32_t k = (int32_t)(r % a.K);
-      const int32_t n = (int32_t)(r / a.K);
-      const bool do_bias = a.db && m == 0 && k == 0;
-      for (int32_t s = 0; s < a.b.count; ++s) {
-        const int64_t t0_in = chunk_t0(a.b, s, a.u_in, a.steps), t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
-        for (int32_t o = 0; o < a.n_out; ++o) {
-          const float g = load_gy(a, s, t0_out, o, n);
-          const float xin = activate(fwd_ptr(a.b, s, a.x, t0_in + (int64_t)o * a.S + k * a.dil - a.hist)[m], a.act);
-          acc = fmaf(g, xin, acc);
-          if (do_bias) bacc += g;
+// dL/db of this chunk: the sum of gy over every output frame, per channel.
+__global__ void __launch_bounds__(256) k_bwd_bias(BwdConv a) {
+  __shared__ float part[4][64];
+  const int32_t n = blockIdx.x * 64 + (threadIdx.x & 63);
+  const int32_t lane4 = threadIdx.x >> 6;
+  const int64_t total = (int64_t)a.b.count * a.n_out;
+  float acc = 0.f;
+  if (n < a.cout)
+    for (int64_t col = lane4; col < total; col += 4) {
+      const int32_t s = (int32_t)(col / a.n_out), o = (int32_t)(col - (int64_t)s * a.n_out);
+      acc += gy_row(a, s, o, chunk_t0(a.b, s, a.u_out, a.steps))[n];
+    }
+  part[lane4][threadIdx.x & 63] = acc;
+  __syncthreads();
+  if (lane4 == 0 && n < a.cout) a.db[n] += part[0][threadIdx.x] + part[1][threadIdx.x] + part[2][threadIdx.x] + part[3][threadIdx.x];
+}
+
+// dL/dx for the chunk's input frames i in [-hist, n_in) (the cached history
+// included), times the activation's derivative, added into the input's
+// adjoint ring: a GEMM over (tap, output channel) per (stream, frame) row.
+// Only this chunk's output frames contribute; later chunks already added
+// theirs into these rows.
+__global__ void __launch_bounds__(256) k_bwd_data(BwdConv a) {
+  __shared__ __align__(16) float Gs[kBC][kBT + 4];  // [n][row]
+  __shared__ __align__(16) float Ws[kBC][kBT + 4];  // [n][m]
+  __shared__ const float* gp[kBT];
+  __shared__ int32_t rs[kBT];
+  __shared__ int32_t ri[kBT];
+  const int32_t span = a.hist + a.n_in;
+  const int64_t rows = (int64_t)a.b.count * span;
+  const int64_t r0 = (int64_t)blockIdx.x * kBT;
+  const int32_t m0 = blockIdx.y * kBT;
+  const int32_t tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const bool convt = a.op == CC_OP_CONVT;
+  if (threadIdx.x < kBT) {
+    const int64_t row = r0 + threadIdx.x;
+    rs[threadIdx.x] = -1;
+    if (row < rows) {
+      rs[threadIdx.x] = (int32_t)(row / span);
+      ri[threadIdx.x] = (int32_t)(row - (int64_t)rs[threadIdx.x] * span) - a.hist;
+    }
+  }
+  float acc[4][4] = {};
+  for (int32_t tap = 0; tap < a.K; ++tap) {
+    __syncthreads();
+    if (threadIdx.x < kBT) {
+      const int32_t s = rs[threadIdx.x], i = ri[threadIdx.x];
+      const float* p = nullptr;
+      if (s >= 0) {
+        const int64_t t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
+        if (!convt) {
+          const int32_t jj2 = i + a.hist - tap * a.dil;
+          if (jj2 >= 0 && jj2 % a.S == 0 && jj2 / a.S < a.n_out) p = gy_row(a, s, jj2 / a.S, t0_out);
+        } else {
+          const int32_t ph = tap % a.S, jj = tap / a.S, qq = i + jj;
+          if (qq >= 0 && qq < a.n_in) p = gy_row(a, s, (int64_t)qq * a.S + ph, t0_out);
         }
       }
-      a.dW[((int64_t)n * a.cin + m) * a.K + k] += acc;
-      if (do_bias) a.db[n] += bacc;
-    } else {
-      // idx -> (n, kk, m): W[m][n][kk], kk = ph + jj*S
-      const int32_t m = (int32_t)(idx % a.cin);
-      const int64_t r = idx / a.cin;
-      const int32_t kk = (int32_t)(r % a.K);
-      const int32_t n = (int32_t)(r / a.K);
-      const int32_t ph = kk % a.S, jj = kk / a.S;
-      const bool do_bias = a.db && m == 0 && kk == 0;
-      for (int32_t s = 0; s < a.b.count; ++s) {
-        const int64_t t0_in = chunk_t0(a.b, s, a.u_in, a.steps), t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
-        for (int32_t qq = 0; qq < a.n_in; ++qq) {
-          const float g = load_gy(a, s, t0_out, qq * a.S + ph, n);
-          const float xin = activate(fwd_ptr(a.b, s, a.x, t0_in + qq - jj)[m], a.act);
-          acc = fmaf(g, xin, acc);
-        }
-        if (do_bias)
-          for (int32_t o = 0; o < a.n_out; ++o) bacc += load_gy(a, s, t0_out, o, n);
+      gp[threadIdx.x] = p;
+    }
+    __syncthreads();
+    const float* wt = a.Wt + (int64_t)tap * a.cout * a.cin;
+    for (int32_t n0 = 0; n0 < a.cout; n0 += kBC) {
+      for (int e = threadIdx.x; e < kBC * kBT; e += 256) {
+        const int c = e / kBT, q = e - c * kBT;
+        const int32_t n = n0 + c;
+        Gs[c][q] = (gp[q] && n < a.cout) ? gp[q][n] : 0.f;
+        Ws[c][q] = (n < a.cout && m0 + q < a.cin) ? wt[(int64_t)n * a.cin + m0 + q] : 0.f;
       }
-      a.dW[((int64_t)m * a.cout + n) * a.K + kk] += acc;
-      if (do_bias) a.db[n] += bacc;
+      __syncthreads();
+#pragma unroll 4
+      for (int c = 0; c < kBC; ++c) {
+        const float4 g4 = *reinterpret_cast<const float4*>(&Gs[c][ty * 4]);
+        const float4 w4 = *reinterpret_cast<const float4*>(&Ws[c][tx * 4]);
+        const float g[4] = {g4.x, g4.y, g4.z, g4.w}, w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int i2 = 0; i2 < 4; ++i2)
+#pragma unroll
+          for (int j2 = 0; j2 < 4; ++j2) acc[i2][j2] = fmaf(g[i2], w[j2], acc[i2][j2]);
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i2 = 0; i2 < 4; ++i2) {
+    const int32_t lr = ty * 4 + i2;
+    const int32_t s = rs[lr];
+    if (s < 0) continue;
+    const int64_t t = chunk_t0(a.b, s, a.u_in, a.steps) + ri[lr];
+    float* out = adj_row(a.adj, a.adj_slot_bytes, a.b.slots[s], a.gx, t);
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) {
+      const int32_t m = m0 + tx * 4 + j2;
+      if (m >= a.cin) continue;
+      out[m] += acc[i2][j2] * val_deriv(a.b, s, a.x, t, m);
     }
   }
 }
@@ -195,7 +298,12 @@ struct BwdMerge {
   int32_t noise;
   Batch b;
   char* adj;
+  int64_t adj_slot_bytes;
 };
+
+__device__ __forceinline__ float fwd_val(const Batch& b, int32_t s, const Ring& r, int64_t t, int32_t c) {
+  return reinterpret_cast<const float*>(slot_base(b, s) + r.off)[ring_row(t, r.rows) * r.chans + r.choff + c];
+}
 
 __global__ void k_bwd_merge(BwdMerge a) {
   const int64_t total = (int64_t)a.b.count * a.n * a.chans;
@@ -206,27 +314,29 @@ __global__ void k_bwd_merge(BwdMerge a) {
     const int32_t j = (int32_t)(q % a.n);
     const int32_t s = (int32_t)(q / a.n);
     const int64_t t = chunk_t0(a.b, s, a.u, a.steps) + j;
-    const float g = a.gy.rows ? adj_ptr(a.adj, a.b.slot_bytes, a.b.slots[s], a.gy, t)[c]
+    const int32_t slot = a.b.slots[s];
+    const float g = a.gy.rows ? adj_row(a.adj, a.adj_slot_bytes, slot, a.gy, t)[c]
                               : a.gy_ext[(int64_t)s * a.gy_stride + (int64_t)j * a.chans + c];
     if (a.op == CC_OP_ADD) {
       for (int k = 0; k < a.nin; ++k)
-        if (a.gin[k].rows) adj_ptr(a.adj, a.b.slot_bytes, a.b.slots[s], a.gin[k], t - a.A[k])[c] += g;
+        if (a.gin[k].rows) adj_row(a.adj, a.adj_slot_bytes, slot, a.gin[k], t - a.A[k])[c] += g;
     } else {
-      const float w = fwd_ptr(a.b, s, a.in[0], t - a.A[0])[c];
-      const float am = fwd_ptr(a.b, s, a.in[1], t - a.A[1])[c];
-      const float nz = fwd_ptr(a.b, s, a.in[2], t - a.A[2])[c];
+      const float w = fwd_val(a.b, s, a.in[0], t - a.A[0], c);
+      const float am = fwd_val(a.b, s, a.in[1], t - a.A[1], c);
+      const float nz = fwd_val(a.b, s, a.in[2], t - a.A[2], c);
       const float th = tanhf(w), sa = 1.f / (1.f + expf(-am)), sn = 1.f / (1.f + expf(-nz));
       float u = 0.f;
-      if (a.noise) u = noise_uniform(a.b.seeds[a.b.slots[s]], t - a.delay, c, a.chans);
+      if (a.noise) u = noise_uniform(a.b.seeds[slot], t - a.delay, c, a.chans);
       const float gw = g * (1.f - th * th) * sa, ga = g * th * sa * (1.f - sa), gn = g * u * sn * (1.f - sn);
       const float gs[3] = {gw, ga, gn};
       for (int k = 0; k < 3; ++k)
-        if (a.gin[k].rows) adj_ptr(a.adj, a.b.slot_bytes, a.b.slots[s], a.gin[k], t - a.A[k])[c] += gs[k];
+        if (a.gin[k].rows) adj_row(a.adj, a.adj_slot_bytes, slot, a.gin[k], t - a.A[k])[c] += gs[k];
     }
   }
 }
 
-__global__ void k_adj_out(Batch b, char* adj, Ring r, int32_t n, int32_t steps, float* gx, int64_t stride) {
+__global__ void k_adj_out(Batch b, char* adj, int64_t adj_slot_bytes, Ring r, int32_t n, int32_t steps, float* gx,
+                          int64_t stride) {
   const int64_t total = (int64_t)b.count * n * r.chans;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = (int32_t)(i % r.chans);
@@ -234,7 +344,7 @@ __global__ void k_adj_out(Batch b, char* adj, Ring r, int32_t n, int32_t steps, 
     const int32_t j = (int32_t)(q % n);
     const int32_t s = (int32_t)(q / n);
     gx[(int64_t)s * stride + (int64_t)j * r.chans + c] =
-        adj_ptr(adj, b.slot_bytes, b.slots[s], r, chunk_t0(b, s, r.u, steps) + j)[c];
+        adj_row(adj, adj_slot_bytes, b.slots[s], r, chunk_t0(b, s, r.u, steps) + j)[c];
   }
 }
 
@@ -248,14 +358,53 @@ int grid_of(int64_t total) {
 // ===========================================================================
 struct cc_grads {
   cc::Model* m = nullptr;
-  char* adj = nullptr;
+  char* adj = nullptr;          // adjoint arena: max_streams slots of adj_slot_bytes
+  int64_t adj_slot_bytes = 0;
+  std::vector<cc::Ring> adj_ring;  // per node: FP32 adjoint ring (rows 0: none)
   std::vector<float*> dW, db;
   std::vector<size_t> nW;
-  std::vector<float*> dW_dev_trained;  // trained-layout FP32 weights per node (for backward data)
+  std::vector<float*> Wt;  // per conv node: the weights the forward multiplied, [K][cout][cin]
   int32_t* d_slots = nullptr;
   int32_t* h_slots = nullptr;
   cudaEvent_t upload_done = nullptr;
 };
+
+namespace {
+
+// The weights a tensor-core layer multiplies: each packed GEMM row (an output
+// channel of a convolution, a (phase, channel) row of a transposed one)
+// scaled to max |w| = 1, rounded to the model's 16-bit type, scaled back.
+void quantize_like_forward(const cc::Model& m, const cc_node_desc& d, std::vector<float>& w) {
+  const bool bf16 = m.lp_dtype == cc::kDtBF16;
+  auto round16 = [&](float x) {
+    return bf16 ? __bfloat162float(__float2bfloat16_rn(x)) : __half2float(__float2half_rn(x));
+  };
+  if (d.op == CC_OP_CONV) {
+    const size_t row = (size_t)d.c_in * d.kernel;
+    for (int o = 0; o < d.c_out; ++o) {
+      float mx = 0.f;
+      for (size_t k = 0; k < row; ++k) mx = std::max(mx, std::fabs(w[o * row + k]));
+      const float sc = mx > 0.f ? mx : 1.f;
+      for (size_t k = 0; k < row; ++k) w[o * row + k] = round16(w[o * row + k] / sc) * sc;
+    }
+  } else {
+    const int S = d.stride, T = d.kernel / S;
+    for (int ph = 0; ph < S; ++ph)
+      for (int o = 0; o < d.c_out; ++o) {
+        float mx = 0.f;
+        for (int c = 0; c < d.c_in; ++c)
+          for (int j = 0; j < T; ++j) mx = std::max(mx, std::fabs(w[((size_t)c * d.c_out + o) * d.kernel + ph + j * S]));
+        const float sc = mx > 0.f ? mx : 1.f;
+        for (int c = 0; c < d.c_in; ++c)
+          for (int j = 0; j < T; ++j) {
+            float& x = w[((size_t)c * d.c_out + o) * d.kernel + ph + j * S];
+            x = round16(x / sc) * sc;
+          }
+      }
+  }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -263,8 +412,11 @@ cc_status cc_grads_create(cc_model* model, const float* const* weights, cc_grads
   using cc::fail;
   if (!model || !out || !weights) return fail(CC_ERR_INVALID_ARG, "null argument");
   auto* m = reinterpret_cast<cc::Model*>(model);
-  if (m->dtype != CC_F32) return fail(CC_ERR_STATE, "the backward pass runs on FP32 models");
   if (m->max_streams == 0) return fail(CC_ERR_STATE, "plan-only model");
+  if (m->dtype != CC_F32 && m->fuse_units)
+    return fail(CC_ERR_STATE,
+                "a low-precision model is differentiable only with CC_FLAG_NO_UNIT_FUSION (a fused residual "
+                "unit keeps its intermediate on chip, and the backward reads it)");
   for (size_t i = 0; i < m->nodes.size(); ++i) {
     const cc_node_desc& d = m->nodes[i].d;
     if ((d.op == CC_OP_CONV || d.op == CC_OP_CONVT) && !weights[i])
@@ -276,13 +428,14 @@ cc_status cc_grads_create(cc_model* model, const float* const* weights, cc_grads
   g->dW.assign(n, nullptr);
   g->db.assign(n, nullptr);
   g->nW.assign(n, 0);
-  g->dW_dev_trained.assign(n, nullptr);
+  g->Wt.assign(n, nullptr);
+  g->adj_ring.assign(n, cc::Ring{});
   auto bad = [&](const char* what) {
     cudaGetLastError();
     for (size_t i = 0; i < n; ++i) {
       if (g->dW[i]) cudaFree(g->dW[i]);
       if (g->db[i]) cudaFree(g->db[i]);
-      if (g->dW_dev_trained[i]) cudaFree(g->dW_dev_trained[i]);
+      if (g->Wt[i]) cudaFree(g->Wt[i]);
     }
     if (g->adj) cudaFree(g->adj);
     if (g->d_slots) cudaFree(g->d_slots);
@@ -290,20 +443,46 @@ cc_status cc_grads_create(cc_model* model, const float* const* weights, cc_grads
     delete g;
     return fail(CC_ERR_NO_MEMORY, "gradient buffers: %s", what);
   };
-  if (cudaMalloc(&g->adj, m->slot_bytes * (size_t)m->max_streams) != cudaSuccess) return bad("adjoint arena");
-  if (cudaMemset(g->adj, 0, m->slot_bytes * (size_t)m->max_streams) != cudaSuccess) return bad("adjoint arena");
+  // adjoint arena: an FP32 ring per node that anything reads (its kept
+  // history plus a call's frames), independent of the forward's views
+  int64_t off = 0;
+  for (size_t i = 0; i < n; ++i) {
+    const cc::NodePlan& p = m->nodes[i];
+    if (p.consumers.empty() && i + 1 != n) continue;
+    cc::Ring r{};
+    r.off = off;
+    r.rows = p.keep + p.u * m->max_steps;
+    r.chans = p.d.c_out;
+    r.u = p.u;
+    r.dtype = cc::kDtF32;
+    g->adj_ring[i] = r;
+    off += ((int64_t)r.rows * r.chans * 4 + 255) / 256 * 256;
+  }
+  g->adj_slot_bytes = std::max<int64_t>(off, 256);
+  if (cudaMalloc(&g->adj, (size_t)g->adj_slot_bytes * m->max_streams) != cudaSuccess) return bad("adjoint arena");
+  if (cudaMemset(g->adj, 0, (size_t)g->adj_slot_bytes * m->max_streams) != cudaSuccess) return bad("adjoint arena");
   if (cudaMalloc(&g->d_slots, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
       cudaMallocHost(&g->h_slots, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
       cudaEventCreateWithFlags(&g->upload_done, cudaEventDisableTiming) != cudaSuccess)
     return bad("batch list");
   for (size_t i = 0; i < n; ++i) {
-    const cc_node_desc& d = m->nodes[i].d;
+    const cc::NodePlan& p = m->nodes[i];
+    const cc_node_desc& d = p.d;
     if (d.op != CC_OP_CONV && d.op != CC_OP_CONVT) continue;
     g->nW[i] = (size_t)d.c_in * d.c_out * d.kernel;
-    if (cudaMalloc(&g->dW[i], g->nW[i] * 4) != cudaSuccess ||
-        cudaMalloc(&g->dW_dev_trained[i], g->nW[i] * 4) != cudaSuccess)
+    std::vector<float> w(weights[i], weights[i] + g->nW[i]);
+    if (p.engine == 1) quantize_like_forward(*m, d, w);
+    // per tap [K][cout][cin]: conv W[n][m][k]; transposed conv W[m][n][k]
+    std::vector<float> wt(g->nW[i]);
+    for (int k = 0; k < d.kernel; ++k)
+      for (int o = 0; o < d.c_out; ++o)
+        for (int c = 0; c < d.c_in; ++c)
+          wt[((size_t)k * d.c_out + o) * d.c_in + c] = d.op == CC_OP_CONV
+                                                            ? w[((size_t)o * d.c_in + c) * d.kernel + k]
+                                                            : w[((size_t)c * d.c_out + o) * d.kernel + k];
+    if (cudaMalloc(&g->dW[i], g->nW[i] * 4) != cudaSuccess || cudaMalloc(&g->Wt[i], g->nW[i] * 4) != cudaSuccess)
       return bad("weight gradient");
-    if (cudaMemcpy(g->dW_dev_trained[i], weights[i], g->nW[i] * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(g->Wt[i], wt.data(), g->nW[i] * 4, cudaMemcpyHostToDevice) != cudaSuccess)
       return bad("weight upload");
     if (d.has_bias && cudaMalloc(&g->db[i], (size_t)d.c_out * 4) != cudaSuccess) return bad("bias gradient");
   }
@@ -317,7 +496,7 @@ cc_status cc_grads_destroy(cc_grads* g) {
   for (size_t i = 0; i < g->dW.size(); ++i) {
     if (g->dW[i]) cudaFree(g->dW[i]);
     if (g->db[i]) cudaFree(g->db[i]);
-    if (g->dW_dev_trained[i]) cudaFree(g->dW_dev_trained[i]);
+    if (g->Wt[i]) cudaFree(g->Wt[i]);
   }
   cudaFree(g->adj);
   cudaFree(g->d_slots);
@@ -358,8 +537,8 @@ cc_status cc_backward_begin(cc_grads* g, cc_stream* const* streams, int32_t coun
     if (!streams[i] || cc::stream_model(streams[i]) != g->m) return cc::fail(CC_ERR_INVALID_ARG, "stream %d", i);
     if (cc::stream_manipulated(streams[i]))
       return cc::fail(CC_ERR_STATE, "stream %d has an input manipulation; the backward does not differentiate it", i);
-    const cudaError_t e = cudaMemsetAsync(g->adj + (size_t)cc::stream_slot(streams[i]) * g->m->slot_bytes, 0,
-                                          g->m->slot_bytes, st);
+    const cudaError_t e = cudaMemsetAsync(g->adj + (size_t)cc::stream_slot(streams[i]) * g->adj_slot_bytes, 0,
+                                          (size_t)g->adj_slot_bytes, st);
     if (e != cudaSuccess) return cc::fail(CC_ERR_CUDA, "adjoint reset: %s", cudaGetErrorString(e));
   }
   return CC_OK;
@@ -406,23 +585,25 @@ cc_status cc_backward_chunk(cc_grads* g, cc_stream* const* streams, int32_t coun
   const int n = (int)m->nodes.size();
   for (int i = 0; i < n; ++i) {
     const cc::NodePlan& p = m->nodes[i];
-    if (!p.view[0].rows) continue;
+    const cc::Ring& r = g->adj_ring[i];
+    if (!r.rows) continue;
     const int32_t nn = p.u * steps;
-    k_adj_clear<<<grid_of((int64_t)count * nn * p.d.c_out), 256, 0, st>>>(b, g->adj, p.view[0], p.keep_view[0], nn,
-                                                                          steps);
+    k_adj_clear<<<grid_of((int64_t)count * nn * r.chans), 256, 0, st>>>(b, g->adj, g->adj_slot_bytes, r, p.keep, nn,
+                                                                       steps);
     BW_CUDA(cudaGetLastError());
   }
   // 3. nodes in reverse order
-  auto gy_ring = [&](int wi) -> cc::Ring { return wi == n - 1 ? cc::Ring{} : m->nodes[wi].view[0]; };
+  auto gy_ring = [&](int wi) -> cc::Ring { return wi == n - 1 ? cc::Ring{} : g->adj_ring[wi]; };
+  const int32_t lp_bf16 = m->lp_dtype == cc::kDtBF16;
   for (int i = n - 1; i >= 1; --i) {
     const cc::NodePlan& p = m->nodes[i];
     const cc_node_desc& d = p.d;
     if (d.op == CC_OP_CONV || d.op == CC_OP_CONVT) {
       const int wi = p.fused_add >= 0 ? p.fused_add : i;
-      if (wi != n - 1 && !m->nodes[wi].view[0].rows) continue;  // dead branch: zero adjoint
+      if (wi != n - 1 && !g->adj_ring[wi].rows) continue;  // dead branch: zero adjoint
       const cc::NodePlan& src = m->nodes[d.inputs[0]];
       BwdConv a{};
-      a.W = g->dW_dev_trained[i];
+      a.Wt = g->Wt[i];
       a.op = d.op;
       a.cin = d.c_in;
       a.cout = d.c_out;
@@ -430,26 +611,43 @@ cc_status cc_backward_chunk(cc_grads* g, cc_stream* const* streams, int32_t coun
       a.S = d.stride;
       a.dil = d.op == CC_OP_CONV ? d.dilation : 1;
       a.hist = p.hist_need;
-      a.act = d.act_in;
       a.n_in = src.u * steps;
       a.n_out = m->nodes[wi].u * steps;
-      a.x = src.view[0];
+      // the values the forward multiplied: the low-precision view a tensor-core
+      // layer read (activation pre-applied), else the FP32 view
+      if (p.engine == 1) {
+        a.x.r = src.view[1 + d.act_in];
+        a.x.kind = 1 + d.act_in;
+      } else {
+        a.x.r = src.view[0];
+        a.x.kind = 0;
+      }
+      a.x.act = d.act_in;
+      a.x.lp_bf16 = lp_bf16;
       a.u_in = src.u;
       a.u_out = m->nodes[wi].u;
       a.gy = gy_ring(wi);
       a.gy_ext = grad_y;
       a.gy_stride = gy_stride;
+      a.gx = g->adj_ring[d.inputs[0]];
       a.dW = g->dW[i];
       a.db = g->db[i];
       a.steps = steps;
       a.b = b;
       a.adj = g->adj;
-      k_bwd_data<<<grid_of((int64_t)count * (a.hist + a.n_in) * a.cin), 256, 0, st>>>(a);
+      a.adj_slot_bytes = g->adj_slot_bytes;
+      const int64_t rows = (int64_t)count * (a.hist + a.n_in);
+      k_bwd_data<<<dim3((unsigned)((rows + kBT - 1) / kBT), (unsigned)((a.cin + kBT - 1) / kBT)), 256, 0, st>>>(a);
       BW_CUDA(cudaGetLastError());
-      k_bwd_weight<<<grid_of((int64_t)a.cout * a.cin * a.K), 256, 0, st>>>(a);
+      k_bwd_weight<<<dim3((unsigned)((a.cout + kBT - 1) / kBT), (unsigned)((a.cin + kBT - 1) / kBT), (unsigned)a.K), 256,
+                     0, st>>>(a);
       BW_CUDA(cudaGetLastError());
+      if (a.db) {
+        k_bwd_bias<<<(a.cout + 63) / 64, 256, 0, st>>>(a);
+        BW_CUDA(cudaGetLastError());
+      }
     } else if (d.op == CC_OP_ADD || d.op == CC_OP_HEADS) {
-      if (i != n - 1 && !p.view[0].rows) continue;  // dead branch
+      if (i != n - 1 && !g->adj_ring[i].rows) continue;  // dead branch
       BwdMerge a{};
       a.op = d.op;
       a.chans = d.c_out;
@@ -465,13 +663,14 @@ cc_status cc_backward_chunk(cc_grads* g, cc_stream* const* streams, int32_t coun
         a.in[k] = m->nodes[src].view[0];
         // a fused add's conv reads the add's adjoint directly
         const bool into_conv = p.fused && m->nodes[src].fused_add == i;
-        a.gin[k] = into_conv ? cc::Ring{} : m->nodes[src].view[0];
+        a.gin[k] = into_conv ? cc::Ring{} : g->adj_ring[src];
         a.A[k] = p.A[k];
       }
       a.delay = p.D;
       a.noise = m->noise;
       a.b = b;
       a.adj = g->adj;
+      a.adj_slot_bytes = g->adj_slot_bytes;
       k_bwd_merge<<<grid_of((int64_t)count * a.n * a.chans), 256, 0, st>>>(a);
       BW_CUDA(cudaGetLastError());
     }
@@ -479,43 +678,131 @@ cc_status cc_backward_chunk(cc_grads* g, cc_stream* const* streams, int32_t coun
   // 4. the input adjoint of this chunk's frames
   if (grad_x) {
     const cc::NodePlan& p0 = m->nodes[0];
-    k_adj_out<<<grid_of((int64_t)count * p0.u * steps * p0.d.c_out), 256, 0, st>>>(b, g->adj, p0.view[0],
-                                                                                   p0.u * steps, steps, grad_x,
-                                                                                   gx_stride);
+    k_adj_out<<<grid_of((int64_t)count * p0.u * steps * p0.d.c_out), 256, 0, st>>>(
+        b, g->adj, g->adj_slot_bytes, g->adj_ring[0], p0.u * steps, steps, grad_x, gx_stride);
     BW_CUDA(cudaGetLastError());
   }
 #undef BW_CUDA
   return CC_OK;
 }
 
-cc_status cc_stream_snapshot(cc_stream* s, void* dev, size_t bytes, void* cuda_stream) {
-  if (!s || !dev) return cc::fail(CC_ERR_INVALID_ARG, "null argument");
-  cc::Model* m = cc::stream_model(s);
-  if (bytes != m->slot_bytes + 16) return cc::fail(CC_ERR_INVALID_ARG, "snapshot size must be %zu", m->slot_bytes + 16);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-  const int32_t slot = cc::stream_slot(s);
-  char* d = static_cast<char*>(dev);
-  if (cudaMemcpyAsync(d, m->counters + slot, 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d + 8, m->seeds + slot, 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(d + 16, m->arena + (size_t)slot * m->slot_bytes, m->slot_bytes, cudaMemcpyDeviceToDevice, st) !=
-          cudaSuccess)
-    return cc::fail(CC_ERR_CUDA, "snapshot copy failed");
+cc_status cc_model_snapshot_bytes(const cc_model* model, size_t* bytes) {
+  if (!model || !bytes) return cc::fail(CC_ERR_INVALID_ARG, "null argument");
+  *bytes = reinterpret_cast<const cc::Model*>(model)->snapshot_bytes;
   return CC_OK;
 }
 
-cc_status cc_stream_restore(cc_stream* s, const void* dev, size_t bytes, void* cuda_stream) {
-  if (!s || !dev) return cc::fail(CC_ERR_INVALID_ARG, "null argument");
-  cc::Model* m = cc::stream_model(s);
-  if (bytes != m->slot_bytes + 16) return cc::fail(CC_ERR_INVALID_ARG, "snapshot size must be %zu", m->slot_bytes + 16);
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-  const int32_t slot = cc::stream_slot(s);
-  const char* d = static_cast<const char*>(dev);
-  if (cudaMemcpyAsync(m->counters + slot, d, 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(m->seeds + slot, d + 8, 8, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(m->arena + (size_t)slot * m->slot_bytes, d + 16, m->slot_bytes, cudaMemcpyDeviceToDevice, st) !=
-          cudaSuccess)
-    return cc::fail(CC_ERR_CUDA, "restore copy failed");
+}  // extern "C"
+
+namespace {
+
+// Copies the cached state of `count` streams between their arena slots and a
+// compact buffer (stream i at buf + i * snap_bytes: step counter, noise seed,
+// then each region's kept rows, oldest first), four bytes per thread.
+// Restoring also rewrites the mirrored copy of a low-precision view's tail.
+__global__ void k_state_copy(cc::Batch b, const cc::Model::StateRegion* regs, int32_t n_regs, char* buf,
+                             int64_t snap_bytes, int32_t to_slots) {
+  const int64_t words = snap_bytes / 4;
+  const int64_t per = n_regs ? words : 4;  // no regions: the counter and seed words only
+  const int64_t total = (int64_t)b.count * per;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = (int32_t)(i / per);
+    int64_t w = i - (int64_t)s * per;
+    const int32_t slot = b.slots[s];
+    uint32_t* bw = reinterpret_cast<uint32_t*>(buf + (int64_t)s * snap_bytes) + w;
+    if (w < 4) {  // counter, seed
+      uint32_t* src = w < 2 ? reinterpret_cast<uint32_t*>(const_cast<int64_t*>(b.counters) + slot) + w
+                            : reinterpret_cast<uint32_t*>(const_cast<uint64_t*>(b.seeds) + slot) + (w - 2);
+      if (to_slots)
+        *src = *bw;
+      else
+        *bw = *src;
+      continue;
+    }
+    w -= 4;
+    int32_t k = 0;
+    for (; k < n_regs; ++k) {
+      const int64_t rw = (int64_t)regs[k].keep * regs[k].row_bytes / 4;
+      if (w < rw) break;
+      w -= rw;
+    }
+    if (k >= n_regs) continue;
+    const cc::Model::StateRegion& g = regs[k];
+    const int32_t per_row = g.row_bytes / 4;
+    const int32_t q = (int32_t)(w / per_row), c = (int32_t)(w - (int64_t)q * per_row);
+    // the step counter in the buffer is the state's: at restore it is the one
+    // being written (read it from the buffer), at snapshot the slot's
+    const int64_t steps = *reinterpret_cast<const int64_t*>(buf + (int64_t)s * snap_bytes);
+    const int64_t t = steps * g.u - g.keep + q;
+    const int64_t row = ring_row(t, g.rows);
+    uint32_t* slot_word = reinterpret_cast<uint32_t*>(b.arena + (int64_t)slot * b.slot_bytes + g.off + row * g.row_bytes) + c;
+    if (to_slots) {
+      *slot_word = *bw;
+      if (g.pre && row >= g.rows - g.pre)
+        *reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(slot_word) - (int64_t)g.rows * g.row_bytes) = *bw;
+    } else {
+      *bw = *slot_word;
+    }
+  }
+}
+
+cc_status state_copy(cc::Model* m, cc_stream* const* streams, int32_t count, void* buf, size_t bytes, int32_t to_slots,
+                     cudaStream_t st) {
+  using cc::fail;
+  if (!streams || !buf || count <= 0) return fail(CC_ERR_INVALID_ARG, "null argument or empty batch");
+  if (count > m->max_streams) return fail(CC_ERR_INVALID_ARG, "batch larger than max_streams");
+  if (bytes != (size_t)count * m->snapshot_bytes)
+    return fail(CC_ERR_INVALID_ARG, "snapshot buffer must hold %d x %zu bytes", count, m->snapshot_bytes);
+  if (reinterpret_cast<uintptr_t>(buf) % 8) return fail(CC_ERR_INVALID_ARG, "snapshot buffer must be 8-byte aligned");
+  std::vector<int32_t> slots(count);
+  for (int32_t i = 0; i < count; ++i) {
+    if (!streams[i] || cc::stream_model(streams[i]) != m) return fail(CC_ERR_INVALID_ARG, "stream %d not of this model", i);
+    slots[i] = cc::stream_slot(streams[i]);
+  }
+  const int32_t* d_list = nullptr;
+  cc_status r = cc::upload_slot_list(m, slots, st, &d_list);
+  if (r) return r;
+  const cc::Batch b = m->batch_for(d_list, count);
+  if (!to_slots) {
+    // the counters first (every state row's time depends on them), then the rows
+    k_state_copy<<<(count * 4 + 255) / 256, 256, 0, st>>>(b, m->d_state_regions, 0, static_cast<char*>(buf),
+                                                        (int64_t)m->snapshot_bytes, 0);
+    if (cudaGetLastError() != cudaSuccess) return fail(CC_ERR_CUDA, "snapshot launch failed");
+  }
+  k_state_copy<<<grid_of((int64_t)count * m->snapshot_bytes / 4), 256, 0, st>>>(
+      b, m->d_state_regions, (int32_t)m->state_regions.size(), static_cast<char*>(buf), (int64_t)m->snapshot_bytes,
+      to_slots);
+  if (cudaGetLastError() != cudaSuccess) return fail(CC_ERR_CUDA, "state copy launch failed");
   return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cc_status cc_snapshot_batch(cc_model* model, cc_stream* const* streams, int32_t count, void* dev_buf, size_t bytes,
+                            void* cuda_stream) {
+  if (!model) return cc::fail(CC_ERR_INVALID_ARG, "null model");
+  return state_copy(reinterpret_cast<cc::Model*>(model), streams, count, dev_buf, bytes, 0,
+                    reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+cc_status cc_restore_batch(cc_model* model, cc_stream* const* streams, int32_t count, const void* dev_buf, size_t bytes,
+                           void* cuda_stream) {
+  if (!model) return cc::fail(CC_ERR_INVALID_ARG, "null model");
+  return state_copy(reinterpret_cast<cc::Model*>(model), streams, count, const_cast<void*>(dev_buf), bytes, 1,
+                    reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+cc_status cc_stream_snapshot(cc_stream* s, void* dev, size_t bytes, void* cuda_stream) {
+  if (!s) return cc::fail(CC_ERR_INVALID_ARG, "null stream");
+  return state_copy(cc::stream_model(s), &s, 1, dev, bytes, 0, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+cc_status cc_stream_restore(cc_stream* s, const void* dev, size_t bytes, void* cuda_stream) {
+  if (!s) return cc::fail(CC_ERR_INVALID_ARG, "null stream");
+  return state_copy(cc::stream_model(s), &s, 1, const_cast<void*>(dev), bytes, 1,
+                    reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
 }  // extern "C"

@@ -269,6 +269,40 @@ static void plan_ksplit(Model& m) {
   }
 }
 
+// The cached state as ring regions: every view's kept rows (one region per
+// ring: a sibling group's shared FP32 ring keeps its members' largest history).
+static cc_status plan_state(Model& m) {
+  m.state_regions.clear();
+  std::map<int64_t, size_t> by_off;
+  for (const NodePlan& p : m.nodes) {
+    if (!p.has_ring) continue;
+    for (int v = 0; v < 3; ++v) {
+      const Ring& r = p.view[v];
+      if (!r.rows || !p.keep_view[v]) continue;
+      const int32_t elem = v == 0 ? 4 : 2;
+      auto it = by_off.find(r.off);
+      if (it != by_off.end()) {
+        m.state_regions[it->second].keep = std::max(m.state_regions[it->second].keep, p.keep_view[v]);
+        continue;
+      }
+      Model::StateRegion g{};
+      g.off = r.off;
+      g.rows = r.rows;
+      g.pre = r.pre;
+      g.row_bytes = r.chans * elem;
+      g.keep = p.keep_view[v];
+      g.u = r.u;
+      if (g.row_bytes % 4) return fail(CC_ERR_STATE, "state row of %d bytes is not a multiple of 4", g.row_bytes);
+      by_off[r.off] = m.state_regions.size();
+      m.state_regions.push_back(g);
+    }
+  }
+  m.snapshot_bytes = 16;
+  for (const auto& g : m.state_regions) m.snapshot_bytes += (size_t)g.keep * g.row_bytes;
+  m.snapshot_bytes = align_up(m.snapshot_bytes, 16);  // every stream's record 16-byte aligned in a batch buffer
+  return CC_OK;
+}
+
 static size_t lcm_size(size_t a, size_t b) {
   size_t x = a, y = b;
   while (y) {
@@ -934,6 +968,7 @@ Model::~Model() {
   }
   if (stage_in) cudaFree(stage_in);
   if (stage_out) cudaFree(stage_out);
+  if (d_state_regions) cudaFree(d_state_regions);
   if (rag_in) cudaFree(rag_in);
   if (rag_out) cudaFree(rag_out);
   for (auto e : event_pool) cudaEventDestroy(e);
@@ -1059,6 +1094,15 @@ cc_status cc_model_create(const cc_node_desc* nodes, int32_t n_nodes, const floa
     }
   }
   if (!s) s = cc::encode_gather_maps(*m);
+  if (!s) s = cc::plan_state(*m);
+  if (!s && !m->state_regions.empty()) {
+    const size_t nb = sizeof(cc::Model::StateRegion) * m->state_regions.size();
+    if (cudaMalloc(&m->d_state_regions, nb) != cudaSuccess ||
+        cudaMemcpy(m->d_state_regions, m->state_regions.data(), nb, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      s = fail(CC_ERR_NO_MEMORY, "state map");
+    }
+  }
   const size_t manip_floats = (size_t)3 * m->nodes.front().d.c_out * m->max_streams;
   if (!s && (cudaMalloc(&m->counters, sizeof(int64_t) * m->max_streams) != cudaSuccess ||
              cudaMalloc(&m->seeds, sizeof(uint64_t) * m->max_streams) != cudaSuccess ||

@@ -114,6 +114,17 @@ struct Model {
 
   int32_t force_tile_n = 0;  // autotuning: every tensor-core layer uses this N tile
   int32_t last_chain_launches = 0;  // kernels the most recent launch chain enqueued
+  // the cached state as ring regions (a stream's snapshot copies only these rows)
+  struct StateRegion {
+    int64_t off;        // byte offset of ring row 0 in a slot
+    int32_t rows, pre;  // ring rows R; mirrored rows before row 0 (low-precision views)
+    int32_t row_bytes;  // bytes per row (a multiple of 4)
+    int32_t keep;       // rows of history kept: times t0 - keep .. t0 - 1
+    int32_t u;          // frames per model step of the ring
+  };
+  std::vector<StateRegion> state_regions;
+  StateRegion* d_state_regions = nullptr;  // device copy
+  size_t snapshot_bytes = 0;               // 16 (counter, seed) + every region's kept rows
 
   ~Model();
   int32_t tile_n_for(const NodePlan& p, int64_t n_cols) const;

@@ -138,3 +138,174 @@ def test_backward_restores_forward_state(cclib, cuda):
     model.process_batch([b], nxt, yb2)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(ya.cpu().numpy(), yb2.cpu().numpy())
+
+
+def bf16_decoder(seed=0):
+    """A decoder wide enough for the tensor cores (256 -> 128 -> 64 channels),
+    with the FP32 tail (narrow heads and inverse PQMF)."""
+    nodes = W.rave_decoder(latent=16, capacity=64, ratios=(2, 2), dilations=(1, 3), bands=4, pqmf_taps=16)
+    p = W.init_params(nodes, seed)
+    _, g, _, _ = pqmf.design(4, 16, 5.0)
+    p[W.pqmf_node_index(nodes)] = (pqmf.synthesis_weights(g), None)
+    return nodes, p
+
+
+def _tc_layers(nodes, fmt):
+    """The layers the BF16/FP16 modes run on the tensor cores (the rule the
+    library documents: a conv or convT with c_in % 64 == 0 and c_out % 8 == 0)."""
+    return {i: fmt for i, nd in enumerate(nodes)
+            if nd["op"] in ("conv", "convt") and nd["c_in"] % 64 == 0 and nd["c_out"] % 8 == 0}
+
+
+def shallow_tc_stack(seed):
+    """Every tensor-core layer kind in a few layers: LeakyReLU -> convT (K=4,
+    S=2), a dilated k=3 conv and a 1x1 conv (both on LeakyReLU views), a
+    residual add, and a k=3 conv on the add's plain low-precision view."""
+    n = W._node
+    nodes = [W.input_node(64),
+             n("convt", [0], 64, 64, k=4, stride=2, crop=1, act_in="leaky", name="up"),
+             n("conv", [1], 64, 64, k=3, dilation=3, pad_left=3, pad_right=3, act_in="leaky", name="a"),
+             n("conv", [2], 64, 64, k=1, act_in="leaky", name="b"),
+             n("add", [1, 3], 64, 64, bias=False, name="add"),
+             n("conv", [4], 64, 64, k=3, pad_left=1, pad_right=1, act_in=None, name="c")]
+    return nodes, W.init_params(nodes, seed)
+
+
+def _streamed_gradients(cuda, nodes, p, dtype, xs, seeds, chunk, r_seed=12):
+    import torch
+
+    model = api.Model(nodes, p, dtype=dtype, max_streams=len(xs), max_steps_per_call=chunk, fuse_units=False)
+    runner = AG.StreamedRunner(model, p, [model.stream(seed=s) for s in seeds], chunk)
+    x = torch.tensor(np.stack(xs), dtype=torch.float32, device=cuda, requires_grad=True)
+    y = AG.streamed(x, runner)
+    r = np.random.default_rng(r_seed).standard_normal(tuple(y.shape))
+    y.backward(torch.tensor(r, dtype=torch.float32, device=cuda))
+    torch.cuda.synchronize()
+    assert model.device_status() == 0
+    grads = {i: runner.grads.read(i) for i in p}
+    return x.grad.cpu().numpy(), grads, r
+
+
+def _oracle_sums(nodes, p, xs, seeds, r, rounded):
+    gx, gw = [], {}
+    for k in range(len(xs)):
+        _, gxr, gwr = AD.gradients(nodes, p, xs[k], r[k], seed=seeds[k], rounded=rounded)
+        gx.append(gxr)
+        for i, (dw, db) in gwr.items():
+            a = gw.get(i)
+            gw[i] = (dw, db) if a is None else (a[0] + dw, None if db is None else a[1] + db)
+    return gx, gw
+
+
+def _snr(g, ref):
+    g = np.asarray(g, np.float64).ravel()
+    ref = np.asarray(ref, np.float64).ravel()
+    return 10 * np.log10(np.sum(ref ** 2) / max(np.sum((g - ref) ** 2), 1e-300))
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("pseed", [2, 3, 4])
+def test_lowp_gradient_is_the_rounded_models(cclib, cuda, dtype, pseed):
+    """Differentiation with a BF16 (FP16) forward on the tensor cores: the
+    backward multiplies the rounded weights and activations the forward
+    multiplied, so dL/dx and every dL/dw, dL/db equal the oracle's FP64
+    gradients of the model with those operands rounded (activated inputs to
+    nearest, weights row by row after scaling to max |w| = 1), over chunks
+    whose cache adjoints carry from chunk to chunk: >= 70 dB and max-abs <=
+    1e-3 x peak per tensor.  The model is shallow on purpose: the GPU sums in
+    FP32 and the oracle in FP64, and once a value lands on the other side of a
+    rounding boundary the two forwards part and the gap grows layer by layer
+    (faster in FP16, whose grid is 8x finer), so only a few layers compare
+    exactly; the deep decoder is checked below for what rounding costs."""
+    nodes, p = shallow_tc_stack(pseed)
+    frames, chunk = 6, 2
+    xs = [W.signal(60 + k, frames, 64) for k in range(2)]
+    seeds = [7, 8]
+    gx, grads, r = _streamed_gradients(cuda, nodes, p, dtype, xs, seeds, chunk)
+    gxr, gwr = _oracle_sums(nodes, p, xs, seeds, r, _tc_layers(nodes, dtype))
+
+    def close(g, ref, what):
+        snr = _snr(g, ref)
+        rel = np.abs(np.asarray(g, np.float64) - ref).max() / max(np.abs(ref).max(), 1e-30)
+        assert snr >= 70.0 and rel <= 1e-3, f"{dtype} {what}: SNR {snr:.1f} dB, max-abs/peak {rel:.2e}"
+
+    for k in range(2):
+        close(gx[k], gxr[k], f"dL/dx stream {k}")
+    for i, (dw, db) in grads.items():
+        close(dw, gwr[i][0], f"dL/dw {nodes[i]['name']}")
+        if db is not None:
+            close(db, gwr[i][1], f"dL/db {nodes[i]['name']}")
+
+
+@pytest.mark.parametrize("dtype,min_cos", [("bf16", 0.98), ("f16", 0.995)])
+def test_lowp_decoder_gradient_direction(cclib, cuda, dtype, min_cos):
+    """What rounding costs a decoder's gradient: against the FP64 gradient of
+    the exact model, every gradient tensor of the BF16 (FP16) decoder points
+    the same way (cosine >= 0.98 / 0.995).  The error is mostly LeakyReLU
+    derivatives taken on the other side of zero where rounding moved a value
+    across it (a 0.2 vs 1 slope at that element), summed over the layers."""
+    nodes, p = bf16_decoder(2)
+    frames, chunk = 6, 2
+    xs = [W.signal(60 + k, frames, 16) for k in range(2)]
+    seeds = [7, 8]
+    gx, grads, r = _streamed_gradients(cuda, nodes, p, dtype, xs, seeds, chunk)
+    gxr, gwr = _oracle_sums(nodes, p, xs, seeds, r, None)
+
+    def cos(g, ref, what):
+        g = np.asarray(g, np.float64).ravel()
+        ref = np.asarray(ref, np.float64).ravel()
+        c = float(g @ ref / (np.linalg.norm(g) * np.linalg.norm(ref)))
+        assert c >= min_cos, f"{dtype} {what}: cosine {c:.4f}"
+
+    for k in range(2):
+        cos(gx[k], gxr[k], f"dL/dz stream {k}")
+    for i, (dw, db) in grads.items():
+        cos(dw, gwr[i][0], f"dL/dw {nodes[i]['name']}")
+        if db is not None:
+            cos(db, gwr[i][1], f"dL/db {nodes[i]['name']}")
+
+
+def test_lowp_gradients_need_unfused_units(cclib, cuda):
+    nodes, p = bf16_decoder(2)
+    model = api.Model(nodes, p, dtype="bf16", max_streams=1, max_steps_per_call=1)
+    with pytest.raises(api.CCError) as e:
+        api.Grads(model, p)
+    assert e.value.status == -7
+
+
+def test_compact_checkpoint_restores_the_stream(cclib, cuda):
+    """A checkpoint holds the step counter, the seed and the cached rows only
+    (about a tenth of the arena slot for the decoder); restoring it into a
+    stream that ran further makes that stream continue exactly as the
+    original, in BF16 (mirrored low-precision rows included) and FP32."""
+    import torch
+
+    dec = W.rave_decoder()
+    p = W.init_params(dec, 1)
+    _, g, _, _ = pqmf.design(16, 64)
+    p[W.pqmf_node_index(dec)] = (pqmf.synthesis_weights(g), None)
+    for dtype in ("bf16", "f32"):
+        model = api.Model(dec, p, dtype=dtype, max_streams=3, max_steps_per_call=1)
+        a, b, c = model.stream(seed=1), model.stream(seed=1), model.stream(seed=2)
+        nb = api.snapshot_bytes(model)
+        assert nb < model.state_bytes[1] / 4
+        z = torch.tensor(W.signal(3, 40, 128)[:, None, :], dtype=torch.float32, device=cuda)
+        y = torch.empty((1, 2048, 1), device=cuda)
+        for t in range(13):
+            model.process_batch([a, b], torch.stack([z[t], z[t]]), torch.empty((2, 2048, 1), device=cuda))
+        buf = torch.empty(2 * nb, dtype=torch.uint8, device=cuda)
+        api.snapshot_batch(model, [a, b], buf)
+        for t in range(13, 31):  # b runs on: every ring wraps past the checkpoint's rows
+            model.process_batch([b], z[t:t + 1], y)
+        api.restore_batch(model, [c, b], buf)  # c takes a's state, b returns to it
+        ya = torch.empty((1, 2048, 1), device=cuda)
+        yb = torch.empty_like(ya)
+        yc = torch.empty_like(ya)
+        for t in range(13, 20):
+            model.process_batch([a], z[t:t + 1], ya)
+            model.process_batch([b], z[t:t + 1], yb)
+            model.process_batch([c], z[t:t + 1], yc)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(yb.cpu().numpy(), ya.cpu().numpy())
+            np.testing.assert_array_equal(yc.cpu().numpy(), ya.cpu().numpy())
+        model.close()

@@ -167,13 +167,39 @@ def build_decoder(dtype, streams, seed=1, kind="decoder"):
     return nodes, params, model
 
 
+def autoencoder(dtype, streams, seed=4, steps_per_call=1):
+    """The encoder feeding the decoder (audio -> audio), random weights, the
+    16-band PQMF pair; a low-precision model is built without fused residual
+    units (the backward needs each convolution's output)."""
+    from paper_2204_07064_gb300 import api
+    from paper_2204_07064_gb300 import workloads as W
+
+    nodes = W.chain(W.rave_encoder(), W.rave_decoder())
+    params = W.init_params(nodes, seed)
+    analysis, synthesis = api.pqmf_layer_weights(16, 64, 5.0)
+    for i, nd in enumerate(nodes):
+        if nd["name"] == "pqmf":
+            params[i] = (analysis, None)
+        if nd["name"] == "ipqmf":
+            params[i] = (synthesis, None)
+    model = api.Model(nodes, params, dtype=dtype, max_streams=streams, max_steps_per_call=steps_per_call,
+                      fuse_units=dtype == "f32")
+    return nodes, params, model
+
+
 def run_differentiate(args):
-    """Differentiation form: the encoder + decoder (audio -> audio, FP32),
+    """Differentiation form: the encoder + decoder (audio -> audio) with a BF16
+    forward on the tensor cores (--diff-dtype f32: FFMA) and FP32 gradients,
     --diff-streams streams of --diff-chunks 2048-sample chunks of N(0, 0.1^2)
-    audio, streamed through torch.autograd with one device checkpoint per chunk,
-    then the hand-written chunked backward (loss = sum(r * y), r seeded).
-    Reports audio seconds differentiated per second (forward + backward, CUDA
-    events) and the checkpoint memory."""
+    audio (60 s at 48 kHz = 1407 chunks), streamed through torch.autograd with
+    one compact state checkpoint per chunk, then the chunked backward (loss =
+    sum(r * y), r ~ N(0, 1) seeded; gradients of every weight and bias and of
+    the input audio).  The forward and the backward are timed with CUDA
+    events; audio seconds differentiated per second = streams x chunks x 2048
+    / 48000 / (forward + backward seconds).  A second, shorter pass with every
+    backward kernel bracketed by events gives the kernels' shares, the nodes
+    that cost most, and the roofline of the dominant class (FP32 FFMA:
+    ALU-bound)."""
     import torch
 
     import __graft_entry__
@@ -181,57 +207,117 @@ def run_differentiate(args):
     __graft_entry__.build()
     from paper_2204_07064_gb300 import api
     from paper_2204_07064_gb300 import autograd as AG
-    from paper_2204_07064_gb300 import workloads as W
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    enc = W.rave_encoder()
-    dec = W.rave_decoder()
-    nodes = W.chain(enc, dec)
-    params = W.init_params(nodes, 4)
-    analysis, synthesis = api.pqmf_layer_weights(16, 64, 5.0)
-    for i, nd in enumerate(nodes):
-        if nd["name"] == "pqmf":
-            params[i] = (analysis, None)
-        if nd["name"] == "ipqmf":
-            params[i] = (synthesis, None)
-    count, chunks = args.diff_streams, args.diff_chunks
-    model = api.Model(nodes, params, dtype="f32", max_streams=count, max_steps_per_call=1)
-    streams = [model.stream(seed=s) for s in W.stream_seeds(4, count)]
-    runner = AG.StreamedRunner(model, params, streams, 1)
+    dtype = args.diff_dtype
+    count, chunks, cs = args.diff_streams, args.diff_chunks, args.diff_chunk_steps
+    if chunks % cs:
+        raise SystemExit("--diff-chunks must be a multiple of --diff-chunk-steps")
+    nodes, params, model = autoencoder(dtype, count, steps_per_call=cs)
+    streams = [model.stream(seed=1000 + s) for s in range(count)]
+    runner = AG.StreamedRunner(model, params, streams, cs)
     n = chunks * 2048
     rng = np.random.default_rng(4)
-    x = torch.tensor(rng.standard_normal((count, n, 1)) * 0.1, dtype=torch.float32, device=dev, requires_grad=True)
+    x = torch.tensor(rng.standard_normal((count, n, 1)) * 0.1, dtype=torch.float32, device=dev)
     r = torch.tensor(rng.standard_normal((count, n, 1)), dtype=torch.float32, device=dev)
+    free0 = device_free_bytes(dev)
 
-    def once():
-        x.grad = None
+    def one_pass(xx, rr, events=None):
+        xx = xx.detach().requires_grad_(True)
         runner.grads.zero()
-        y = AG.streamed(x, runner)
-        (y * r).sum().backward()
+        for s in streams:
+            s.reset()
+        if events:
+            events[0].record()
+        y = AG.streamed(xx, runner)
+        if events:
+            events[1].record()
+        (y * rr).sum().backward()
+        if events:
+            events[2].record()
+        return xx.grad
 
+    warm = min(chunks, 8 * cs)
     for _ in range(max(1, args.warmup // 3)):
-        once()
+        one_pass(x[:, :warm * 2048], r[:, :warm * 2048])
     torch.cuda.synchronize()
     model.device_status()
-    reps = max(1, args.steps // 10)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        once()
-    e1.record()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.time()
+    gx = one_pass(x, r, ev)
     torch.cuda.synchronize()
+    t1 = time.time()
+    clk = clocks.stop(window=(t0, t1))
     model.device_status()
-    ms = e0.elapsed_time(e1) / reps
+    fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    free1 = device_free_bytes(dev)
+    assert torch.isfinite(gx).all()
     audio_s = count * n / SR
-    ckpt_bytes = (chunks + 1) * count * api.snapshot_bytes(model)
-    print(json.dumps({
-        "metric": "streamed forward + backward, audio seconds per second", "value": audio_s / (ms / 1000.0),
-        "unit": "audio s / s", "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-        "ms_per_pass": ms, "repeats": reps,
-        "config": {"workload": f"autoencoder-f32-diff-{count}x{chunks}", "streams": count, "chunks": chunks,
-                   "chunk_samples": 2048, "checkpoint_bytes": ckpt_bytes,
-                   "loss": "sum(r * y), r ~ N(0,1) seeded"}}))
+    snap = api.snapshot_bytes(model)
+    slot = model.state_bytes[1]
+
+    # kernel classes of the backward over a window of chunks (events around
+    # every launch; the absolute times include that overhead, the shares are
+    # what the roofline uses)
+    win = min(chunks, 32 * cs)
+    runner.grads.timing(True)
+    one_pass(x[:, :win * 2048], r[:, :win * 2048])
+    torch.cuda.synchronize()
+    classes = runner.grads.timing_read()
+    per_node = runner.grads.timing_read_nodes()
+    runner.grads.timing(False)
+    ev_total = sum(v[0] for v in classes.values())
+    info_u = [model.node_info(i)["frames_per_step"] for i in range(len(nodes))]
+    conv_flops = sum(node_flops(nd, info_u[i]) for i, nd in enumerate(nodes) if nd["op"] in ("conv", "convt"))
+    # dL/dW and dL/dx each cost the forward's multiply-adds: per stream-step
+    per_class_flops = {"weight": conv_flops, "data": conv_flops}
+    pk, pk_kind = peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    kernels = {}
+    for c, (ms, cnt) in classes.items():
+        e = {"launches": cnt, "event_ms": ms, "share": ms / ev_total if ev_total else None}
+        if c in per_class_flops and cnt:
+            # the class's share of the event pass, applied to the timed backward
+            e["achieved_tflops"] = per_class_flops[c] * count * chunks / (bwd_ms / 1000.0 * e["share"]) / 1e12
+        kernels[c] = e
+    top = []
+    for i, c, ms, cnt in sorted(per_node, key=lambda e: -e[2])[:10]:
+        e = {"node": nodes[i]["name"] or nodes[i]["op"], "class": c, "us_per_chunk": 1000.0 * ms / win,
+             "share": ms / ev_total if ev_total else None}
+        if c in ("weight", "data"):
+            e["event_tflops"] = node_flops(nodes[i], info_u[i]) * count * win / (ms / 1000.0) / 1e12
+        top.append(e)
+    dom = max(("weight", "data"), key=lambda c: classes[c][0])
+    achieved = kernels[dom]["achieved_tflops"]
+    line = {
+        "metric": "streamed forward + backward, audio seconds differentiated per second",
+        "value": audio_s / ((fwd_ms + bwd_ms) / 1000.0),
+        "unit": "audio s / s", "higher_is_better": True, "dtype": f"{dtype} forward, f32 gradients",
+        "data": "synthetic", "n_gpus": 1,
+        "ms": {"forward_with_checkpoints": fwd_ms, "backward": bwd_ms},
+        "config": {"workload": f"autoencoder-{dtype}-diff-{count}x{chunks}", "streams": count, "chunks": chunks,
+                   "chunk_samples": 2048 * cs, "audio_seconds_per_stream": n / SR,
+                   "loss": "sum(r * y), r ~ N(0,1) seeded", "input": "N(0, 0.1^2) audio, seed 4",
+                   "gradients": "every weight and bias, and the input audio"},
+        "checkpoints": {"bytes_per_stream_per_chunk": snap, "arena_slot_bytes": slot,
+                        "total_bytes": (chunks // cs + 1) * count * snap},
+        "device_memory_used_bytes": free0 - free1 if free0 and free1 else None,
+        "backward_kernels": {"window_chunks": win, "classes": kernels, "top_nodes": top,
+                             "note": "event-bracketed pass over the first window_chunks chunks; shares of its "
+                                     "summed event times"},
+        "roofline": {"bound": "alu", "kernel": f"k_bwd_{dom} (FP32 FFMA, 64x64 tiles)", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "achieved_from": "the class's algorithmic FLOPs over the whole pass / (timed backward x its "
+                                      "share of the event pass)",
+                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
+        "clocks": clk,
+    }
+    print(json.dumps(line))
     model.close()
 
 
@@ -603,7 +689,9 @@ def main():
     ap.add_argument("--differentiate", action="store_true",
                     help="time the streamed forward + hand-written backward of the encoder + decoder")
     ap.add_argument("--diff-streams", type=int, default=32)
-    ap.add_argument("--diff-chunks", type=int, default=32)
+    ap.add_argument("--diff-chunks", type=int, default=1407, help="2048-sample chunks per stream (1407 = 60 s)")
+    ap.add_argument("--diff-chunk-steps", type=int, default=1, help="model steps per checkpointed chunk")
+    ap.add_argument("--diff-dtype", default="bf16", choices=["bf16", "f16", "f32"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -328,7 +328,10 @@ cc_status cc_model_timing_read(cc_model* model, double* ms_per_node, int64_t* la
  * multiplied (a rounding's derivative taken as 1).  All signal pointers are device memory:
  * x [n_in][in_channels], grad_y [n_out][out_channels], grad_x (may be NULL)
  * [n_in][in_channels], stream i at base + i*stride.  n_in is a whole number
- * of model steps, at most max_steps_per_call. */
+ * of model steps, at most max_steps_per_call.  With grad_x NULL the adjoint
+ * of the model input is not computed at all (weights only): pass grad_x for
+ * every chunk of a backward pass or for none, since a chunk's input adjoint
+ * includes what the later chunks carried back. */
 typedef struct cc_grads cc_grads;
 /* weights: the trained-layout float32 host weights the model was created with. */
 cc_status cc_grads_create(cc_model* model, const float* const* weights, cc_grads** out);
@@ -340,6 +343,30 @@ cc_status cc_backward_begin(cc_grads* grads, cc_stream* const* streams, int32_t 
 cc_status cc_backward_chunk(cc_grads* grads, cc_stream* const* streams, int32_t count, const float* x,
                             int64_t x_stride, int64_t n_in, const float* grad_y, int64_t gy_stride,
                             int64_t n_out, float* grad_x, int64_t gx_stride, void* cuda_stream);
+
+/* Device time of the backward's kernels by class, for measurement (no
+ * counterpart in the paper): with timing enabled every kernel of
+ * cc_backward_chunk is bracketed by CUDA events on the launching stream (it
+ * adds a few microseconds per launch; keep it off when timing the whole pass).
+ * cc_grads_timing(enable) synchronizes the device and clears what was
+ * recorded; cc_grads_timing_read waits for the recorded kernels and returns,
+ * per class, the summed milliseconds and the number of launches (arrays of
+ * CC_BWD_CLASSES entries; either may be NULL). */
+enum {
+  CC_BWD_RECOMPUTE = 0, /* the chunk's forward, recomputed from the restored state */
+  CC_BWD_CLEAR = 1,     /* zeroing adjoint rows no later chunk wrote (one launch)  */
+  CC_BWD_DATA = 2,      /* dL/dx of a convolution (history rows included)          */
+  CC_BWD_WEIGHT = 3,    /* dL/dW and dL/db of a convolution                        */
+  CC_BWD_MERGE = 4,     /* residual adds and the heads                             */
+  CC_BWD_INPUT = 5,     /* copy of the input adjoint out to grad_x                 */
+  CC_BWD_CLASSES = 6
+};
+cc_status cc_grads_timing(cc_grads* grads, int32_t enable);
+cc_status cc_grads_timing_read(cc_grads* grads, double* ms, int64_t* launches, int32_t n_classes);
+/* The same per node: ms and launches are [n_nodes][CC_BWD_CLASSES] (the
+ * recompute and the clear, which span every node, are left out). */
+cc_status cc_grads_timing_read_nodes(cc_grads* grads, int32_t n_nodes, double* ms, int64_t* launches);
+
 /* Device-side copies of streams' state for per-chunk checkpoints: the step
  * counter, the noise seed and the cached padding itself -- every ring's kept
  * rows (section 2.2's cache; section 4.1 measures it as the method's only

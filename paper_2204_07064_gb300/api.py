@@ -93,6 +93,9 @@ _SIGNATURES = {
     "cc_grads_read": [_P, _I32, _P, _P],
     "cc_backward_begin": [_P, _P, _I32, _P],
     "cc_backward_chunk": [_P, _P, _I32, _P, _I64, _I64, _P, _I64, _I64, _P, _I64, _P],
+    "cc_grads_timing": [_P, _I32],
+    "cc_grads_timing_read": [_P, C.POINTER(_DBL), C.POINTER(_I64), _I32],
+    "cc_grads_timing_read_nodes": [_P, _I32, C.POINTER(_DBL), C.POINTER(_I64)],
     "cc_model_snapshot_bytes": [_P, C.POINTER(_SZ)],
     "cc_snapshot_batch": [_P, C.POINTER(_P), _I32, _P, _SZ, _P],
     "cc_restore_batch": [_P, C.POINTER(_P), _I32, _P, _SZ, _P],
@@ -571,6 +574,27 @@ class Grads:
                                        x.shape[1], _ptr(gy), int(np.prod(gy.shape[1:])), gy.shape[1],
                                        None if gx is None else _ptr(gx),
                                        int(np.prod(x.shape[1:])), _cuda_stream(cuda_stream)))
+
+    BWD_CLASSES = ("recompute", "clear", "data", "weight", "merge", "input")
+
+    def timing(self, enable):
+        """Bracket every backward kernel with CUDA events (cc_grads_timing)."""
+        _check(lib().cc_grads_timing(self.handle, int(bool(enable))))
+
+    def timing_read(self):
+        """{class: (milliseconds, launches)} recorded since timing(True)."""
+        n = len(self.BWD_CLASSES)
+        ms, cnt = (_DBL * n)(), (_I64 * n)()
+        _check(lib().cc_grads_timing_read(self.handle, ms, cnt, n))
+        return {c: (ms[i], cnt[i]) for i, c in enumerate(self.BWD_CLASSES)}
+
+    def timing_read_nodes(self):
+        """[(node, class, milliseconds, launches)] with launches > 0."""
+        n, k = len(self.model.nodes), len(self.BWD_CLASSES)
+        ms, cnt = (_DBL * (n * k))(), (_I64 * (n * k))()
+        _check(lib().cc_grads_timing_read_nodes(self.handle, n, ms, cnt))
+        return [(i, c, ms[i * k + j], cnt[i * k + j]) for i in range(n) for j, c in enumerate(self.BWD_CLASSES)
+                if cnt[i * k + j]]
 
     def close(self):
         if getattr(self, "handle", None) and getattr(self.model, "handle", None):

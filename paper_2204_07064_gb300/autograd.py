@@ -8,7 +8,8 @@ of chunks times the per-stream cache, not with the signal's activations.
 Backward: the checkpoints are restored in reverse order and the library's
 hand-written backward (cc_backward_chunk) recomputes each chunk and
 propagates the adjoints, carrying the cache adjoint from chunk to chunk;
-weight and bias gradients accumulate in a Grads object.  After the backward
+weight and bias gradients accumulate in a Grads object (the input's gradient
+is computed only when the input requires it).  After the backward
 the streams are back in the state the forward left them in.
 """
 from __future__ import annotations
@@ -31,11 +32,20 @@ class StreamedRunner:
         self.in_chunk = chunk_steps * io["in_per_step"]
         self.out_chunk = chunk_steps * io["out_per_step"]
         self.io = io
+        self.anchor = None
+
+    def weights_anchor(self, device):
+        """A zero-size tensor that requires a gradient and stands for the
+        model's weights in the autograd graph (their gradients land in
+        self.grads), so that the backward runs when only they need one."""
+        if self.anchor is None or self.anchor.device != device:
+            self.anchor = torch.zeros(0, device=device, requires_grad=True)
+        return self.anchor
 
 
 class _Streamed(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, runner):
+    def forward(ctx, x, anchor, runner):
         count, n_in, cin = x.shape
         io = runner.io
         if n_in % runner.in_chunk:
@@ -63,20 +73,23 @@ class _Streamed(torch.autograd.Function):
         xs, ckpt = ctx.saved_tensors
         runner = ctx.runner
         gy = gy.contiguous()
-        gx = torch.zeros_like(xs)
+        want_gx = ctx.needs_input_grad[0]
+        gx = torch.zeros_like(xs) if want_gx else None
         runner.grads.begin(runner.streams)
         for c in reversed(range(ctx.chunks)):
             api.restore_batch(runner.model, runner.streams, ckpt[c])
             xc = xs[:, c * runner.in_chunk:(c + 1) * runner.in_chunk].contiguous()
             gyc = gy[:, c * runner.out_chunk:(c + 1) * runner.out_chunk].contiguous()
-            gxc = torch.empty_like(xc)
+            gxc = torch.empty_like(xc) if want_gx else None
             runner.grads.chunk(runner.streams, xc, gyc, gxc)
-            gx[:, c * runner.in_chunk:(c + 1) * runner.in_chunk] = gxc
+            if want_gx:
+                gx[:, c * runner.in_chunk:(c + 1) * runner.in_chunk] = gxc
         api.restore_batch(runner.model, runner.streams, ckpt[ctx.chunks])
-        return gx, None
+        return gx, None, None
 
 
 def streamed(x, runner):
-    """y = the streamed model applied to x [count][n_in][C_in] (differentiable in x;
-    weight gradients accumulate in runner.grads)."""
-    return _Streamed.apply(x, runner)
+    """y = the streamed model applied to x [count][n_in][C_in]; y.backward()
+    accumulates the weight and bias gradients in runner.grads, and x's
+    gradient when x requires one."""
+    return _Streamed.apply(x, runner.weights_anchor(x.device), runner)

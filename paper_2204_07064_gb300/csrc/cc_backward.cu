@@ -54,18 +54,24 @@ __device__ __forceinline__ float load_lp(const void* p, bool bf16) {
   return bf16 ? __bfloat162float(__ushort_as_bfloat16(h)) : __half2float(__ushort_as_half(h));
 }
 
-// The value the forward multiplied (activation applied) at time t, channel m.
-__device__ __forceinline__ float val_act(const Batch& b, int32_t s, const ValView& v, int64_t t, int32_t m) {
+// Start of the row the forward wrote at time t (FP32 views: at the node's
+// channel offset; low-precision views: 2 bytes per channel).
+__device__ __forceinline__ const char* val_row(const Batch& b, int32_t s, const ValView& v, int64_t t) {
   const char* base = slot_base(b, s) + v.r.off;
   const int64_t row = ring_row(t, v.r.rows);
-  if (v.kind == 0) return activate(reinterpret_cast<const float*>(base)[row * v.r.chans + v.r.choff + m], v.act);
-  return load_lp(base + (row * v.r.chans + m) * 2, v.lp_bf16 != 0);
+  return v.kind == 0 ? base + (row * v.r.chans + v.r.choff) * 4 : base + row * v.r.chans * 2;
 }
 
-// The activation's derivative at that point (1 without activation).
-__device__ __forceinline__ float val_deriv(const Batch& b, int32_t s, const ValView& v, int64_t t, int32_t m) {
+// The value the forward multiplied (activation applied), channel m of a row.
+__device__ __forceinline__ float val_at(const char* row, const ValView& v, int32_t m) {
+  if (v.kind == 0) return activate(reinterpret_cast<const float*>(row)[m], v.act);
+  return load_lp(row + m * 2, v.lp_bf16 != 0);
+}
+
+// The activation's derivative there (1 without activation).
+__device__ __forceinline__ float deriv_at(const char* row, const ValView& v, int32_t m) {
   if (v.kind == 1 || (v.kind == 0 && !v.act)) return 1.f;
-  return val_act(b, s, v, t, m) >= 0.f ? 1.f : kLeakySlope;  // LeakyReLU keeps the sign
+  return val_at(row, v, m) >= 0.f ? 1.f : kLeakySlope;  // LeakyReLU keeps the sign
 }
 
 // Adjoint rows: an FP32 ring per node in the adjoint arena, indexed by the
@@ -78,17 +84,33 @@ __device__ __forceinline__ int64_t chunk_t0(const Batch& b, int32_t s, int32_t u
   return (steps_of(b, s) - steps) * (int64_t)u;
 }
 
-// Zero the adjoint rows of times [t0 - keep, t0 + n - keep) for every stream:
-// the rows no later chunk (processed earlier, in reverse order) could have
-// written; rows [t0 + n - keep, t0 + n) hold the cache adjoint they left.
-__global__ void k_adj_clear(Batch b, char* adj, int64_t adj_slot_bytes, Ring r, int32_t keep, int32_t n, int32_t steps) {
-  const int64_t total = (int64_t)b.count * n * r.chans;
+// Zero the adjoint rows of times [t0 - keep, t0 + n - keep) for every stream
+// and every listed ring: the rows no later chunk (processed earlier, in
+// reverse order) could have written; rows [t0 + n - keep, t0 + n) hold the
+// cache adjoint they left.  One launch covers up to kClearMax rings; entry k
+// owns elements [start[k], start[k + 1]) of the flattened (stream, row,
+// channel) space.
+constexpr int kClearMax = 48;
+struct ClearList {
+  int32_t count;
+  Ring r[kClearMax];
+  int32_t keep[kClearMax], n[kClearMax];
+  int64_t start[kClearMax + 1];
+};
+
+__global__ void k_adj_clear(Batch b, char* adj, int64_t adj_slot_bytes, const __grid_constant__ ClearList L,
+                            int32_t steps) {
+  const int64_t total = L.start[L.count];
+  int32_t k = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t c = (int32_t)(i % r.chans);
-    const int64_t q = i / r.chans;
-    const int32_t j = (int32_t)(q % n);
-    const int32_t s = (int32_t)(q / n);
-    const int64_t t = chunk_t0(b, s, r.u, steps) - keep + j;
+    while (i >= L.start[k + 1]) ++k;  // i only grows within a thread
+    const Ring& r = L.r[k];
+    const int64_t e = i - L.start[k];
+    const int32_t c = (int32_t)(e % r.chans);
+    const int64_t q = e / r.chans;
+    const int32_t j = (int32_t)(q % L.n[k]);
+    const int32_t s = (int32_t)(q / L.n[k]);
+    const int64_t t = chunk_t0(b, s, r.u, steps) - L.keep[k] + j;
     adj_row(adj, adj_slot_bytes, b.slots[s], r, t)[c] = 0.f;
   }
 }
@@ -104,12 +126,21 @@ struct BwdConv {
   const float* gy_ext;  // caller's output gradient, stream s at gy_ext + s*gy_stride
   int64_t gy_stride;
   Ring gx;              // adjoint ring of the input node
-  float* dW;            // trained layout accumulators
+  float* dW;            // accumulators, tap-major [K][cout][cin]
   float* db;
   int32_t steps;
   Batch b;
   char* adj;
   int64_t adj_slot_bytes;
+  // split reductions: blockIdx.z = (tap or 0) * splits + split; with splits >
+  // 1 every split writes a 64 x 64 partial of its tile and the tile's last
+  // block to arrive adds them, in split order, into the destination
+  int32_t splits;
+  int32_t res;         // dX rows residue by residue (strided convolution, dilation 1)
+  int64_t per_split;   // reduction steps per split: columns (dW), (tap, 32-channel chunk) pairs (dX)
+  float* part;         // [tile][split][64 * 64]
+  float* bpart;        // [n tile][phase][split][64] bias partials (dW)
+  uint32_t* counters;  // per tile arrivals, then per n tile bias arrivals; left at 0
 };
 
 __device__ __forceinline__ const float* gy_row(const BwdConv& a, int32_t s, int64_t t_local, int64_t t0_out) {
@@ -119,37 +150,98 @@ __device__ __forceinline__ const float* gy_row(const BwdConv& a, int32_t s, int6
 
 constexpr int kBT = 64;  // output tile (rows x columns) of the backward GEMMs
 constexpr int kBC = 32;  // reduction chunk
+// split reductions aim at 4 blocks per SM; the partial buffer holds twice
+// that many 64 x 64 tiles, and the bias arrival counters sit after the tiles'
+constexpr int64_t kTargetBlocks = 4 * 152;
+constexpr int64_t kPartTiles = 2 * kTargetBlocks;
+
+// Split reductions: a block's 4 x 4 accumulators (rows ty*4+i, columns
+// tx*4+j of its 64 x 64 tile) go straight to `apply` when the reduction is not
+// split; otherwise into the tile's partial for this split, and the last split
+// to arrive sums the tile's partials in split order (deterministic) and
+// applies the sum.  Returns whether this block applied the tile.
+template <typename Apply>
+__device__ __forceinline__ bool finish_tile(const BwdConv& a, float (&acc)[4][4], int64_t tile, int32_t split,
+                                            Apply apply) {
+  const int32_t tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (a.splits == 1) {
+    apply(acc);
+    return true;
+  }
+  __shared__ bool last;
+  float* mine = a.part + (tile * a.splits + split) * (kBT * kBT);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    *reinterpret_cast<float4*>(mine + (ty * 4 + i) * kBT + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t prev = atomicAdd(a.counters + tile, 1u);
+    last = prev == (uint32_t)a.splits - 1;
+    if (last) a.counters[tile] = 0;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  float sum[4][4] = {};
+#pragma unroll 4
+  for (int32_t q = 0; q < a.splits; ++q) {
+    const float* p = a.part + (tile * a.splits + q) * (kBT * kBT);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(p + (ty * 4 + i) * kBT + tx * 4));
+      sum[i][0] += v.x;
+      sum[i][1] += v.y;
+      sum[i][2] += v.z;
+      sum[i][3] += v.w;
+    }
+  }
+  apply(sum);
+  return true;
+}
 
 // dL/dW of this chunk as a GEMM per tap k: dW_k[n][m] += sum over columns
 // (stream, output frame) of gy[col][n] * x_k[col][m], x_k the value the
 // forward multiplied by tap k.  A block computes a 64 x 64 tile of one tap
-// over every column; 4 x 4 outputs per thread.  (A transposed convolution's
-// tap kk = ph + jj*S pairs output phase ph with input frame q - jj.)
+// over one split of the columns; 4 x 4 outputs per thread.  (A transposed
+// convolution's tap kk = ph + jj*S pairs output phase ph with input frame
+// q - jj.)  dL/db, the sum of gy over every output frame, rides along in the
+// blocks of the first input-channel tile: tap 0 of a convolution, taps
+// 0..S-1 (one per output phase) of a transposed one; with more than one such
+// block per output-channel tile, the last to arrive sums their partials in
+// (phase, split) order.
 __global__ void __launch_bounds__(256) k_bwd_weight(BwdConv a) {
   __shared__ __align__(16) float Gs[kBC][kBT + 4];
   __shared__ __align__(16) float Xs[kBC][kBT + 4];
   __shared__ const float* gp[kBC];
-  __shared__ int32_t xs_s[kBC];
-  __shared__ int64_t xs_t[kBC];
-  const int32_t n0 = blockIdx.x * kBT, m0 = blockIdx.y * kBT, kk = blockIdx.z;
+  __shared__ const char* xp[kBC];
+  __shared__ bool blast;
+  const int32_t n0 = blockIdx.x * kBT, m0 = blockIdx.y * kBT;
+  const int32_t kk = blockIdx.z / a.splits, split = blockIdx.z - kk * a.splits;
   const int32_t tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool convt = a.op == CC_OP_CONVT;
   const int32_t ph = convt ? kk % a.S : 0, jj = convt ? kk / a.S : 0;
   const int32_t ncol = convt ? a.n_in : a.n_out;
   const int64_t total = (int64_t)a.b.count * ncol;
+  const int64_t c_begin = (int64_t)split * a.per_split;
+  const int64_t c_end = c_begin + a.per_split < total ? c_begin + a.per_split : total;
+  const bool bias = a.db && blockIdx.y == 0 && (convt ? kk < a.S : kk == 0);
+  const int32_t nph = convt ? a.S : 1;
   float acc[4][4] = {};
-  for (int64_t c0 = 0; c0 < total; c0 += kBC) {
+  float bacc = 0.f;
+  for (int64_t c0 = c_begin; c0 < c_end; c0 += kBC) {
     if (threadIdx.x < kBC) {
       const int64_t col = c0 + threadIdx.x;
-      gp[threadIdx.x] = nullptr;
-      xs_s[threadIdx.x] = -1;
-      if (col < total) {
+      const float* g = nullptr;
+      const char* xr = nullptr;
+      if (col < c_end) {
         const int32_t s = (int32_t)(col / ncol), o = (int32_t)(col - (int64_t)s * ncol);
         const int64_t t0_in = chunk_t0(a.b, s, a.u_in, a.steps), t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
-        gp[threadIdx.x] = gy_row(a, s, convt ? (int64_t)o * a.S + ph : o, t0_out);
-        xs_s[threadIdx.x] = s;
-        xs_t[threadIdx.x] = convt ? t0_in + o - jj : t0_in + (int64_t)o * a.S + (int64_t)kk * a.dil - a.hist;
+        g = gy_row(a, s, convt ? (int64_t)o * a.S + ph : o, t0_out);
+        xr = val_row(a.b, s, a.x, convt ? t0_in + o - jj : t0_in + (int64_t)o * a.S + (int64_t)kk * a.dil - a.hist);
       }
+      gp[threadIdx.x] = g;
+      xp[threadIdx.x] = xr;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < kBC * kBT; e += 256) {
@@ -157,12 +249,14 @@ __global__ void __launch_bounds__(256) k_bwd_weight(BwdConv a) {
       float g = 0.f, x = 0.f;
       if (gp[c]) {
         if (n0 + q < a.cout) g = gp[c][n0 + q];
-        if (m0 + q < a.cin) x = val_act(a.b, xs_s[c], a.x, xs_t[c], m0 + q);
+        if (m0 + q < a.cin) x = val_at(xp[c], a.x, m0 + q);
       }
       Gs[c][q] = g;
       Xs[c][q] = x;
     }
     __syncthreads();
+    if (bias && threadIdx.x < kBT)
+      for (int c = 0; c < kBC; ++c) bacc += Gs[c][threadIdx.x];
 #pragma unroll 4
     for (int c = 0; c < kBC; ++c) {
       const float4 g4 = *reinterpret_cast<const float4*>(&Gs[c][ty * 4]);
@@ -175,39 +269,65 @@ __global__ void __launch_bounds__(256) k_bwd_weight(BwdConv a) {
     }
     __syncthreads();
   }
+  const int64_t tile = ((int64_t)kk * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  // dW accumulates tap-major, [K][cout][cin] like Wt: a thread's 4 input
+  // channels are one 16-byte word when cin allows
+  const bool vec = (a.cin & 3) == 0;
+  finish_tile(a, acc, tile, split, [&](float (&v)[4][4]) {
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j2 = 0; j2 < 4; ++j2) {
-      const int32_t n = n0 + ty * 4 + i, m = m0 + tx * 4 + j2;
+    for (int i = 0; i < 4; ++i) {
+      const int32_t n = n0 + ty * 4 + i, m = m0 + tx * 4;
       if (n >= a.cout || m >= a.cin) continue;
-      const int64_t w = convt ? ((int64_t)m * a.cout + n) * a.K + kk : ((int64_t)n * a.cin + m) * a.K + kk;
-      a.dW[w] += acc[i][j2];
+      float* w = a.dW + ((int64_t)kk * a.cout + n) * a.cin + m;
+      if (vec) {
+        float4 t = *reinterpret_cast<float4*>(w);
+        t.x += v[i][0];
+        t.y += v[i][1];
+        t.z += v[i][2];
+        t.w += v[i][3];
+        *reinterpret_cast<float4*>(w) = t;
+      } else {
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2)
+          if (m + j2 < a.cin) w[j2] += v[i][j2];
+      }
     }
-}
-
-// dL/db of this chunk: the sum of gy over every output frame, per channel.
-__global__ void __launch_bounds__(256) k_bwd_bias(BwdConv a) {
-  __shared__ float part[4][64];
-  const int32_t n = blockIdx.x * 64 + (threadIdx.x & 63);
-  const int32_t lane4 = threadIdx.x >> 6;
-  const int64_t total = (int64_t)a.b.count * a.n_out;
-  float acc = 0.f;
-  if (n < a.cout)
-    for (int64_t col = lane4; col < total; col += 4) {
-      const int32_t s = (int32_t)(col / a.n_out), o = (int32_t)(col - (int64_t)s * a.n_out);
-      acc += gy_row(a, s, o, chunk_t0(a.b, s, a.u_out, a.steps))[n];
-    }
-  part[lane4][threadIdx.x & 63] = acc;
+  });
+  if (!bias) return;
+  const int32_t contributors = nph * a.splits;
+  if (contributors == 1) {
+    if (threadIdx.x < kBT && n0 + (int32_t)threadIdx.x < a.cout) a.db[n0 + threadIdx.x] += bacc;
+    return;
+  }
+  if (threadIdx.x < kBT) a.bpart[(((int64_t)blockIdx.x * nph + ph) * a.splits + split) * kBT + threadIdx.x] = bacc;
+  __threadfence();
   __syncthreads();
-  if (lane4 == 0 && n < a.cout) a.db[n] += part[0][threadIdx.x] + part[1][threadIdx.x] + part[2][threadIdx.x] + part[3][threadIdx.x];
+  if (threadIdx.x == 0) {
+    uint32_t* cnt = a.counters + kPartTiles + blockIdx.x;
+    const uint32_t prev = atomicAdd(cnt, 1u);
+    blast = prev == (uint32_t)contributors - 1;
+    if (blast) *cnt = 0;
+  }
+  __syncthreads();
+  if (!blast) return;
+  __threadfence();
+  if (threadIdx.x < kBT && n0 + (int32_t)threadIdx.x < a.cout) {
+    float sb = 0.f;
+    for (int32_t q = 0; q < contributors; ++q)
+      sb += __ldcg(a.bpart + ((int64_t)blockIdx.x * contributors + q) * kBT + threadIdx.x);
+    a.db[n0 + threadIdx.x] += sb;
+  }
 }
 
 // dL/dx for the chunk's input frames i in [-hist, n_in) (the cached history
 // included), times the activation's derivative, added into the input's
-// adjoint ring: a GEMM over (tap, output channel) per (stream, frame) row.
-// Only this chunk's output frames contribute; later chunks already added
-// theirs into these rows.
+// adjoint ring: a GEMM over (tap, output channel) per (stream, frame) row,
+// the (tap, 32-channel chunk) steps of the reduction split across
+// blockIdx.z.  Only this chunk's output frames contribute; later chunks
+// already added theirs into these rows.  For a strided convolution of
+// dilation 1 (a.res) the rows are taken residue by residue: frame e = i +
+// hist only meets taps k = e mod S + S*jt, so a block holds rows of one
+// residue and runs only those ceil(K/S) taps.
 __global__ void __launch_bounds__(256) k_bwd_data(BwdConv a) {
   __shared__ __align__(16) float Gs[kBC][kBT + 4];  // [n][row]
   __shared__ __align__(16) float Ws[kBC][kBT + 4];  // [n][m]
@@ -218,70 +338,189 @@ __global__ void __launch_bounds__(256) k_bwd_data(BwdConv a) {
   const int64_t rows = (int64_t)a.b.count * span;
   const int64_t r0 = (int64_t)blockIdx.x * kBT;
   const int32_t m0 = blockIdx.y * kBT;
+  const int32_t split = blockIdx.z;
   const int32_t tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const bool convt = a.op == CC_OP_CONVT;
+  // residue mode: this block's residue and its first row within it
+  int32_t res = 0, nj = span;
+  int64_t rbase = r0;
+  if (a.res) {
+    int64_t bx = blockIdx.x;
+    for (res = 0; res < a.S; ++res) {
+      nj = (span - res + a.S - 1) / a.S;
+      const int64_t t = ((int64_t)a.b.count * nj + kBT - 1) / kBT;
+      if (bx < t) break;
+      bx -= t;
+    }
+    rbase = bx * kBT;
+  }
   if (threadIdx.x < kBT) {
-    const int64_t row = r0 + threadIdx.x;
+    const int64_t row = rbase + threadIdx.x;
     rs[threadIdx.x] = -1;
-    if (row < rows) {
+    ri[threadIdx.x] = 0;
+    if (a.res) {
+      if (row < (int64_t)a.b.count * nj) {
+        rs[threadIdx.x] = (int32_t)(row / nj);
+        ri[threadIdx.x] = res + a.S * (int32_t)(row - (int64_t)rs[threadIdx.x] * nj) - a.hist;
+      }
+    } else if (row < rows) {
       rs[threadIdx.x] = (int32_t)(row / span);
       ri[threadIdx.x] = (int32_t)(row - (int64_t)rs[threadIdx.x] * span) - a.hist;
     }
   }
+  const int32_t nch = (a.cout + kBC - 1) / kBC;
+  const int32_t ntaps = a.res ? (a.K > res ? (a.K - res + a.S - 1) / a.S : 0) : a.K;
+  const int64_t steps_total = (int64_t)ntaps * nch;
+  const int64_t it_begin = (int64_t)split * a.per_split;
+  const int64_t it_end = it_begin + a.per_split < steps_total ? it_begin + a.per_split : steps_total;
   float acc[4][4] = {};
-  for (int32_t tap = 0; tap < a.K; ++tap) {
-    __syncthreads();
-    if (threadIdx.x < kBT) {
-      const int32_t s = rs[threadIdx.x], i = ri[threadIdx.x];
-      const float* p = nullptr;
-      if (s >= 0) {
-        const int64_t t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
-        if (!convt) {
-          const int32_t jj2 = i + a.hist - tap * a.dil;
-          if (jj2 >= 0 && jj2 % a.S == 0 && jj2 / a.S < a.n_out) p = gy_row(a, s, jj2 / a.S, t0_out);
-        } else {
-          const int32_t ph = tap % a.S, jj = tap / a.S, qq = i + jj;
-          if (qq >= 0 && qq < a.n_in) p = gy_row(a, s, (int64_t)qq * a.S + ph, t0_out);
+  int32_t cur_tap = -1;
+  for (int64_t it = it_begin; it < it_end; ++it) {
+    const int32_t jt = (int32_t)(it / nch), n0 = (int32_t)(it - (int64_t)jt * nch) * kBC;
+    const int32_t tap = a.res ? res + a.S * jt : jt;
+    if (tap != cur_tap) {
+      __syncthreads();
+      if (threadIdx.x < kBT) {
+        const int32_t s = rs[threadIdx.x], i = ri[threadIdx.x];
+        const float* p = nullptr;
+        if (s >= 0) {
+          const int64_t t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
+          if (!convt) {
+            const int32_t jj2 = i + a.hist - tap * a.dil;
+            if (jj2 >= 0 && jj2 % a.S == 0 && jj2 / a.S < a.n_out) p = gy_row(a, s, jj2 / a.S, t0_out);
+          } else {
+            const int32_t ph = tap % a.S, jj = tap / a.S, qq = i + jj;
+            if (qq >= 0 && qq < a.n_in) p = gy_row(a, s, (int64_t)qq * a.S + ph, t0_out);
+          }
         }
+        gp[threadIdx.x] = p;
       }
-      gp[threadIdx.x] = p;
+      cur_tap = tap;
+      __syncthreads();
+    }
+    const float* wt = a.Wt + (int64_t)tap * a.cout * a.cin;
+    for (int e = threadIdx.x; e < kBC * kBT; e += 256) {
+      const int c = e / kBT, q = e - c * kBT;
+      const int32_t n = n0 + c;
+      Gs[c][q] = (gp[q] && n < a.cout) ? gp[q][n] : 0.f;
+      Ws[c][q] = (n < a.cout && m0 + q < a.cin) ? wt[(int64_t)n * a.cin + m0 + q] : 0.f;
     }
     __syncthreads();
-    const float* wt = a.Wt + (int64_t)tap * a.cout * a.cin;
-    for (int32_t n0 = 0; n0 < a.cout; n0 += kBC) {
-      for (int e = threadIdx.x; e < kBC * kBT; e += 256) {
-        const int c = e / kBT, q = e - c * kBT;
-        const int32_t n = n0 + c;
-        Gs[c][q] = (gp[q] && n < a.cout) ? gp[q][n] : 0.f;
-        Ws[c][q] = (n < a.cout && m0 + q < a.cin) ? wt[(int64_t)n * a.cin + m0 + q] : 0.f;
-      }
-      __syncthreads();
 #pragma unroll 4
-      for (int c = 0; c < kBC; ++c) {
-        const float4 g4 = *reinterpret_cast<const float4*>(&Gs[c][ty * 4]);
-        const float4 w4 = *reinterpret_cast<const float4*>(&Ws[c][tx * 4]);
-        const float g[4] = {g4.x, g4.y, g4.z, g4.w}, w[4] = {w4.x, w4.y, w4.z, w4.w};
+    for (int c = 0; c < kBC; ++c) {
+      const float4 g4 = *reinterpret_cast<const float4*>(&Gs[c][ty * 4]);
+      const float4 w4 = *reinterpret_cast<const float4*>(&Ws[c][tx * 4]);
+      const float g[4] = {g4.x, g4.y, g4.z, g4.w}, w[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-        for (int i2 = 0; i2 < 4; ++i2)
+      for (int i2 = 0; i2 < 4; ++i2)
 #pragma unroll
-          for (int j2 = 0; j2 < 4; ++j2) acc[i2][j2] = fmaf(g[i2], w[j2], acc[i2][j2]);
+        for (int j2 = 0; j2 < 4; ++j2) acc[i2][j2] = fmaf(g[i2], w[j2], acc[i2][j2]);
+    }
+    __syncthreads();
+  }
+  const int64_t tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+  finish_tile(a, acc, tile, split, [&](float (&v)[4][4]) {
+#pragma unroll
+    for (int i2 = 0; i2 < 4; ++i2) {
+      const int32_t lr = ty * 4 + i2;
+      const int32_t s = rs[lr];
+      if (s < 0) continue;
+      const int64_t t = chunk_t0(a.b, s, a.u_in, a.steps) + ri[lr];
+      float* out = adj_row(a.adj, a.adj_slot_bytes, a.b.slots[s], a.gx, t);
+      const char* xr = val_row(a.b, s, a.x, t);
+#pragma unroll
+      for (int j2 = 0; j2 < 4; ++j2) {
+        const int32_t m = m0 + tx * 4 + j2;
+        if (m >= a.cin) continue;
+        out[m] += v[i2][j2] * deriv_at(xr, a.x, m);
       }
-      __syncthreads();
+    }
+  });
+}
+
+// Layers with fewer than 16 input or output channels (the PQMF filterbanks)
+// would leave most of a 64 x 64 tile idle; their gradients are a few million
+// multiply-adds, computed directly.
+
+// dL/dW (and dL/db) of a narrow layer: one block per weight (tap-major index
+// ((kk * cout + n) * cin + m)), its threads striding over the columns, summed
+// in a fixed order.
+__global__ void __launch_bounds__(256) k_bwd_weight_narrow(BwdConv a) {
+  __shared__ float red[2][8];
+  const int64_t o = blockIdx.x;
+  const int32_t m = (int32_t)(o % a.cin);
+  const int64_t r = o / a.cin;
+  const int32_t n = (int32_t)(r % a.cout), kk = (int32_t)(r / a.cout);
+  const bool convt = a.op == CC_OP_CONVT;
+  const int32_t ph = convt ? kk % a.S : 0, jj = convt ? kk / a.S : 0;
+  const int32_t ncol = convt ? a.n_in : a.n_out;
+  const int64_t total = (int64_t)a.b.count * ncol;
+  const bool bias = a.db && m == 0 && kk == 0;
+  float acc = 0.f, bacc = 0.f;
+  for (int64_t col = threadIdx.x; col < total; col += blockDim.x) {
+    const int32_t s = (int32_t)(col / ncol), q = (int32_t)(col - (int64_t)s * ncol);
+    const int64_t t0_in = chunk_t0(a.b, s, a.u_in, a.steps), t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
+    const float g = gy_row(a, s, convt ? (int64_t)q * a.S + ph : q, t0_out)[n];
+    const int64_t t = convt ? t0_in + q - jj : t0_in + (int64_t)q * a.S + (int64_t)kk * a.dil - a.hist;
+    acc = fmaf(g, val_at(val_row(a.b, s, a.x, t), a.x, m), acc);
+    if (bias) {
+      if (!convt) {
+        bacc += g;
+      } else {
+        for (int32_t p = 0; p < a.S; ++p) bacc += gy_row(a, s, (int64_t)q * a.S + p, t0_out)[n];
+      }
     }
   }
 #pragma unroll
-  for (int i2 = 0; i2 < 4; ++i2) {
-    const int32_t lr = ty * 4 + i2;
-    const int32_t s = rs[lr];
-    if (s < 0) continue;
-    const int64_t t = chunk_t0(a.b, s, a.u_in, a.steps) + ri[lr];
-    float* out = adj_row(a.adj, a.adj_slot_bytes, a.b.slots[s], a.gx, t);
-#pragma unroll
-    for (int j2 = 0; j2 < 4; ++j2) {
-      const int32_t m = m0 + tx * 4 + j2;
-      if (m >= a.cin) continue;
-      out[m] += acc[i2][j2] * val_deriv(a.b, s, a.x, t, m);
+  for (int d = 16; d > 0; d >>= 1) {
+    acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    bacc += __shfl_xor_sync(0xffffffffu, bacc, d);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = acc;
+    red[1][w] = bacc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sw = 0.f, sb = 0.f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      sw += red[0][k];
+      sb += red[1][k];
     }
+    a.dW[o] += sw;
+    if (bias) a.db[n] += sb;
+  }
+}
+
+// dL/dx of a narrow layer: one thread per (stream, frame, input channel),
+// history frames included, summing its taps' output channels directly.
+__global__ void __launch_bounds__(256) k_bwd_data_narrow(BwdConv a) {
+  const int32_t span = a.hist + a.n_in;
+  const int64_t total = (int64_t)a.b.count * span * a.cin;
+  const bool convt = a.op == CC_OP_CONVT;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t m = (int32_t)(idx % a.cin);
+    const int64_t row = idx / a.cin;
+    const int32_t s = (int32_t)(row / span), i = (int32_t)(row - (int64_t)s * span) - a.hist;
+    const int64_t t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
+    float acc = 0.f;
+    for (int32_t tap = 0; tap < a.K; ++tap) {
+      const float* g = nullptr;
+      if (!convt) {
+        const int32_t jj2 = i + a.hist - tap * a.dil;
+        if (jj2 >= 0 && jj2 % a.S == 0 && jj2 / a.S < a.n_out) g = gy_row(a, s, jj2 / a.S, t0_out);
+      } else {
+        const int32_t ph = tap % a.S, jj = tap / a.S, qq = i + jj;
+        if (qq >= 0 && qq < a.n_in) g = gy_row(a, s, (int64_t)qq * a.S + ph, t0_out);
+      }
+      if (!g) continue;
+      const float* w = a.Wt + (int64_t)tap * a.cout * a.cin + m;
+      for (int32_t n = 0; n < a.cout; ++n) acc = fmaf(g[n], w[(int64_t)n * a.cin], acc);
+    }
+    const int64_t t = chunk_t0(a.b, s, a.u_in, a.steps) + i;
+    adj_row(a.adj, a.adj_slot_bytes, a.b.slots[s], a.gx, t)[m] += acc * deriv_at(val_row(a.b, s, a.x, t), a.x, m);
   }
 }
 
@@ -353,6 +592,22 @@ int grid_of(int64_t total) {
   return (int)(g < 1 ? 1 : (g > 152 * 32 ? 152 * 32 : g));
 }
 
+// Splits of a reduction of `steps` steps over `tiles` output tiles, at least
+// `min_steps` steps each, within the partial buffer; per_split is set to the
+// steps of one split (a multiple of `align`).
+int32_t pick_splits(int64_t tiles, int64_t steps, int64_t min_steps, int64_t align, int64_t* per_split) {
+  int64_t sp = 1;
+  if (tiles < kTargetBlocks) {
+    sp = (kTargetBlocks + tiles - 1) / tiles;
+    sp = std::min(sp, std::max<int64_t>(1, steps / min_steps));
+    sp = std::min(sp, std::max<int64_t>(1, kPartTiles / tiles));
+  }
+  int64_t per = (steps + sp - 1) / sp;
+  per = (per + align - 1) / align * align;
+  *per_split = std::max<int64_t>(per, align);
+  return (int32_t)std::max<int64_t>(1, (steps + *per_split - 1) / *per_split);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -367,6 +622,31 @@ struct cc_grads {
   int32_t* d_slots = nullptr;
   int32_t* h_slots = nullptr;
   cudaEvent_t upload_done = nullptr;
+  std::vector<int32_t> uploaded;  // the slot list d_slots holds
+  // split-reduction scratch of the GEMM kernels (shared by their launches,
+  // which run in order on the caller's stream)
+  float* part = nullptr;
+  float* bpart = nullptr;
+  uint32_t* counters = nullptr;
+  // measurement (cc_grads_timing): device time per kernel class and node
+  struct TimingRec {
+    int32_t cls, node;
+    cudaEvent_t start, stop;
+  };
+  bool timing_on = false;
+  std::vector<TimingRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  cudaError_t take_event(cudaEvent_t* e) {
+    if (pool_used == pool.size()) {
+      cudaEvent_t n = nullptr;
+      const cudaError_t r = cudaEventCreate(&n);
+      if (r != cudaSuccess) return r;
+      pool.push_back(n);
+    }
+    *e = pool[pool_used++];
+    return cudaSuccess;
+  }
 };
 
 namespace {
@@ -438,6 +718,9 @@ cc_status cc_grads_create(cc_model* model, const float* const* weights, cc_grads
       if (g->Wt[i]) cudaFree(g->Wt[i]);
     }
     if (g->adj) cudaFree(g->adj);
+    if (g->part) cudaFree(g->part);
+    if (g->bpart) cudaFree(g->bpart);
+    if (g->counters) cudaFree(g->counters);
     if (g->d_slots) cudaFree(g->d_slots);
     if (g->h_slots) cudaFreeHost(g->h_slots);
     delete g;
@@ -459,6 +742,11 @@ cc_status cc_grads_create(cc_model* model, const float* const* weights, cc_grads
     off += ((int64_t)r.rows * r.chans * 4 + 255) / 256 * 256;
   }
   g->adj_slot_bytes = std::max<int64_t>(off, 256);
+  if (cudaMalloc(&g->part, (size_t)kPartTiles * kBT * kBT * 4) != cudaSuccess ||
+      cudaMalloc(&g->bpart, (size_t)kPartTiles * kBT * 4) != cudaSuccess ||
+      cudaMalloc(&g->counters, (size_t)2 * kPartTiles * 4) != cudaSuccess ||
+      cudaMemset(g->counters, 0, (size_t)2 * kPartTiles * 4) != cudaSuccess)
+    return bad("split-reduction scratch");
   if (cudaMalloc(&g->adj, (size_t)g->adj_slot_bytes * m->max_streams) != cudaSuccess) return bad("adjoint arena");
   if (cudaMemset(g->adj, 0, (size_t)g->adj_slot_bytes * m->max_streams) != cudaSuccess) return bad("adjoint arena");
   if (cudaMalloc(&g->d_slots, sizeof(int32_t) * m->max_streams) != cudaSuccess ||
@@ -499,10 +787,59 @@ cc_status cc_grads_destroy(cc_grads* g) {
     if (g->Wt[i]) cudaFree(g->Wt[i]);
   }
   cudaFree(g->adj);
+  cudaFree(g->part);
+  cudaFree(g->bpart);
+  cudaFree(g->counters);
   cudaFree(g->d_slots);
   cudaFreeHost(g->h_slots);
   cudaEventDestroy(g->upload_done);
+  for (cudaEvent_t e : g->pool) cudaEventDestroy(e);
   delete g;
+  return CC_OK;
+}
+
+cc_status cc_grads_timing(cc_grads* g, int32_t enable) {
+  if (!g) return cc::fail(CC_ERR_INVALID_ARG, "null gradients");
+  if (cudaDeviceSynchronize() != cudaSuccess) return cc::fail(CC_ERR_CUDA, "synchronize failed");
+  g->timing_on = enable != 0;
+  g->recs.clear();
+  g->pool_used = 0;
+  return CC_OK;
+}
+
+cc_status cc_grads_timing_read(cc_grads* g, double* ms, int64_t* launches, int32_t n_classes) {
+  if (!g) return cc::fail(CC_ERR_INVALID_ARG, "null gradients");
+  if (n_classes != CC_BWD_CLASSES) return cc::fail(CC_ERR_INVALID_ARG, "n_classes must be %d", CC_BWD_CLASSES);
+  for (int i = 0; i < n_classes; ++i) {
+    if (ms) ms[i] = 0.0;
+    if (launches) launches[i] = 0;
+  }
+  for (auto& r : g->recs) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.stop) != cudaSuccess || cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess)
+      return cc::fail(CC_ERR_CUDA, "timing read failed");
+    if (ms) ms[r.cls] += t;
+    if (launches) launches[r.cls] += 1;
+  }
+  return CC_OK;
+}
+
+cc_status cc_grads_timing_read_nodes(cc_grads* g, int32_t n_nodes, double* ms, int64_t* launches) {
+  if (!g) return cc::fail(CC_ERR_INVALID_ARG, "null gradients");
+  if (n_nodes != (int32_t)g->m->nodes.size()) return cc::fail(CC_ERR_INVALID_ARG, "n_nodes mismatch");
+  const size_t total = (size_t)n_nodes * CC_BWD_CLASSES;
+  for (size_t i = 0; i < total; ++i) {
+    if (ms) ms[i] = 0.0;
+    if (launches) launches[i] = 0;
+  }
+  for (auto& r : g->recs) {
+    if (r.node < 0) continue;
+    float t = 0.f;
+    if (cudaEventSynchronize(r.stop) != cudaSuccess || cudaEventElapsedTime(&t, r.start, r.stop) != cudaSuccess)
+      return cc::fail(CC_ERR_CUDA, "timing read failed");
+    if (ms) ms[(size_t)r.node * CC_BWD_CLASSES + r.cls] += t;
+    if (launches) launches[(size_t)r.node * CC_BWD_CLASSES + r.cls] += 1;
+  }
   return CC_OK;
 }
 
@@ -522,8 +859,19 @@ cc_status cc_grads_read(cc_grads* g, int32_t node, float* dw, float* db) {
   if (node < 0 || node >= (int32_t)g->dW.size() || !g->dW[node])
     return cc::fail(CC_ERR_INVALID_ARG, "node %d has no weights", node);
   if (cudaDeviceSynchronize() != cudaSuccess) return cc::fail(CC_ERR_CUDA, "synchronize failed");
-  if (dw && cudaMemcpy(dw, g->dW[node], g->nW[node] * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return cc::fail(CC_ERR_CUDA, "copy failed");
+  if (dw) {
+    // accumulated tap-major [K][cout][cin]; the trained layout is [cout][cin][K]
+    // (conv) or [cin][cout][K] (transposed conv)
+    const cc_node_desc& d = g->m->nodes[node].d;
+    std::vector<float> t(g->nW[node]);
+    if (cudaMemcpy(t.data(), g->dW[node], g->nW[node] * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cc::fail(CC_ERR_CUDA, "copy failed");
+    for (int k = 0; k < d.kernel; ++k)
+      for (int o = 0; o < d.c_out; ++o)
+        for (int c = 0; c < d.c_in; ++c)
+          dw[d.op == CC_OP_CONV ? ((size_t)o * d.c_in + c) * d.kernel + k : ((size_t)c * d.c_out + o) * d.kernel + k] =
+              t[((size_t)k * d.c_out + o) * d.c_in + c];
+  }
   if (db && g->db[node] &&
       cudaMemcpy(db, g->db[node], (size_t)g->m->nodes[node].d.c_out * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
     return cc::fail(CC_ERR_CUDA, "copy failed");
@@ -562,35 +910,72 @@ cc_status cc_backward_chunk(cc_grads* g, cc_stream* const* streams, int32_t coun
     cudaError_t e_ = (call);                                                                   \
     if (e_ != cudaSuccess) return fail(CC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
-  // batch list (the pinned staging may still feed the previous upload)
-  BW_CUDA(cudaEventSynchronize(g->upload_done));
+  // batch list: uploaded again only when it changed (the pinned staging may
+  // still feed the previous upload)
+  std::vector<int32_t> slots(count);
   for (int32_t i = 0; i < count; ++i) {
     if (!streams[i] || cc::stream_model(streams[i]) != m) return fail(CC_ERR_INVALID_ARG, "stream %d", i);
     if (cc::stream_manipulated(streams[i]))
       return fail(CC_ERR_STATE, "stream %d has an input manipulation; the backward does not differentiate it", i);
-    g->h_slots[i] = cc::stream_slot(streams[i]);
+    slots[i] = cc::stream_slot(streams[i]);
   }
-  BW_CUDA(cudaMemcpyAsync(g->d_slots, g->h_slots, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
-  BW_CUDA(cudaEventRecord(g->upload_done, st));
+  if (slots != g->uploaded) {
+    BW_CUDA(cudaEventSynchronize(g->upload_done));
+    std::memcpy(g->h_slots, slots.data(), sizeof(int32_t) * count);
+    BW_CUDA(cudaMemcpyAsync(g->d_slots, g->h_slots, sizeof(int32_t) * count, cudaMemcpyHostToDevice, st));
+    BW_CUDA(cudaEventRecord(g->upload_done, st));
+    g->uploaded = slots;
+  }
   const cc::Batch b = m->batch_for(g->d_slots, count);
+  auto t_begin = [&](int32_t cls, int32_t node) -> cudaError_t {
+    if (!g->timing_on) return cudaSuccess;
+    cc_grads::TimingRec r{cls, node, nullptr, nullptr};
+    cudaError_t e = g->take_event(&r.start);
+    if (e == cudaSuccess) e = g->take_event(&r.stop);
+    if (e == cudaSuccess) e = cudaEventRecord(r.start, st);
+    if (e == cudaSuccess) g->recs.push_back(r);
+    return e;
+  };
+  auto t_end = [&]() -> cudaError_t {
+    return g->timing_on ? cudaEventRecord(g->recs.back().stop, st) : cudaSuccess;
+  };
   // 1. recompute this chunk's forward from the restored state; its output is
   //    not needed (grad_x doubles as scratch only if the shapes agree, so use
   //    the model's staging buffers)
   cc_status s = m->ensure_staging(count);
   if (s) return s;
+  BW_CUDA(t_begin(CC_BWD_RECOMPUTE, -1));
   s = m->run_chain(b, x, x_stride, m->stage_out, (int64_t)steps * m->nodes.back().u * m->nodes.back().d.c_out,
                    steps, st);
   if (s) return s;
-  // 2. clear the adjoint rows no later chunk could have written
+  BW_CUDA(t_end());
+  // 2. clear the adjoint rows no later chunk could have written (the model
+  //    input's only when its adjoint is wanted)
   const int n = (int)m->nodes.size();
-  for (int i = 0; i < n; ++i) {
-    const cc::NodePlan& p = m->nodes[i];
-    const cc::Ring& r = g->adj_ring[i];
-    if (!r.rows) continue;
-    const int32_t nn = p.u * steps;
-    k_adj_clear<<<grid_of((int64_t)count * nn * r.chans), 256, 0, st>>>(b, g->adj, g->adj_slot_bytes, r, p.keep, nn,
-                                                                       steps);
-    BW_CUDA(cudaGetLastError());
+  {
+    ClearList L{};
+    auto flush = [&]() -> cudaError_t {
+      if (!L.count) return cudaSuccess;
+      cudaError_t e = t_begin(CC_BWD_CLEAR, -1);
+      if (e != cudaSuccess) return e;
+      k_adj_clear<<<grid_of(L.start[L.count]), 256, 0, st>>>(b, g->adj, g->adj_slot_bytes, L, steps);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = t_end();
+      L.count = 0;
+      return e;
+    };
+    for (int i = 0; i < n; ++i) {
+      const cc::NodePlan& p = m->nodes[i];
+      const cc::Ring& r = g->adj_ring[i];
+      if (!r.rows || (i == 0 && !grad_x)) continue;
+      const int32_t k = L.count;
+      L.r[k] = r;
+      L.keep[k] = p.keep;
+      L.n[k] = p.u * steps;
+      L.start[k + 1] = L.start[k] + (int64_t)count * L.n[k] * r.chans;
+      if (++L.count == kClearMax) BW_CUDA(flush());
+    }
+    BW_CUDA(flush());
   }
   // 3. nodes in reverse order
   auto gy_ring = [&](int wi) -> cc::Ring { return wi == n - 1 ? cc::Ring{} : g->adj_ring[wi]; };
@@ -636,16 +1021,55 @@ cc_status cc_backward_chunk(cc_grads* g, cc_stream* const* streams, int32_t coun
       a.b = b;
       a.adj = g->adj;
       a.adj_slot_bytes = g->adj_slot_bytes;
-      const int64_t rows = (int64_t)count * (a.hist + a.n_in);
-      k_bwd_data<<<dim3((unsigned)((rows + kBT - 1) / kBT), (unsigned)((a.cin + kBT - 1) / kBT)), 256, 0, st>>>(a);
-      BW_CUDA(cudaGetLastError());
-      k_bwd_weight<<<dim3((unsigned)((a.cout + kBT - 1) / kBT), (unsigned)((a.cin + kBT - 1) / kBT), (unsigned)a.K), 256,
-                     0, st>>>(a);
-      BW_CUDA(cudaGetLastError());
-      if (a.db) {
-        k_bwd_bias<<<(a.cout + 63) / 64, 256, 0, st>>>(a);
+      a.part = g->part;
+      a.bpart = g->bpart;
+      a.counters = g->counters;
+      const int64_t tm = (a.cin + kBT - 1) / kBT, tn = (a.cout + kBT - 1) / kBT;
+      const bool narrow = a.cin < 16 || a.cout < 16;
+      // dL/dx (not needed for the model input when the caller wants no grad_x)
+      if (grad_x || d.inputs[0] != 0) {
+        BW_CUDA(t_begin(CC_BWD_DATA, i));
+        if (narrow) {
+          k_bwd_data_narrow<<<grid_of((int64_t)count * (a.hist + a.n_in) * a.cin), 256, 0, st>>>(a);
+        } else {
+          // (stream, frame) row tiles x input-channel tiles, the (tap,
+          // 32-channel chunk) reduction split
+          const int64_t span = a.hist + a.n_in;
+          int64_t rt = ((int64_t)count * span + kBT - 1) / kBT, taps = a.K;
+          a.res = d.op == CC_OP_CONV && a.S > 1 && a.dil == 1;
+          if (a.res) {
+            rt = 0;
+            for (int32_t r = 0; r < a.S; ++r) rt += ((int64_t)count * ((span - r + a.S - 1) / a.S) + kBT - 1) / kBT;
+            taps = (a.K + a.S - 1) / a.S;
+          }
+          a.splits = pick_splits(rt * tm, taps * ((a.cout + kBC - 1) / kBC), 4, 1, &a.per_split);
+          k_bwd_data<<<dim3((unsigned)rt, (unsigned)tm, (unsigned)a.splits), 256, 0, st>>>(a);
+        }
         BW_CUDA(cudaGetLastError());
+        BW_CUDA(t_end());
       }
+      // dL/dW (and dL/db)
+      BW_CUDA(t_begin(CC_BWD_WEIGHT, i));
+      if (narrow) {
+        k_bwd_weight_narrow<<<(unsigned)((int64_t)a.cout * a.cin * a.K), 256, 0, st>>>(a);
+      } else {
+        // output-channel x input-channel x tap tiles, the (stream, frame)
+        // columns split
+        const int64_t cols = (int64_t)count * (d.op == CC_OP_CONVT ? a.n_in : a.n_out);
+        a.splits = pick_splits(tn * tm * a.K, cols, 2 * kBC, kBC, &a.per_split);
+        // bias partials: (output-channel tile, phase, split) within the buffer
+        const int64_t nph = d.op == CC_OP_CONVT ? a.S : 1;
+        if (a.db && tn * nph * a.splits > kPartTiles) {
+          if (tn * nph > kPartTiles)
+            return fail(CC_ERR_INVALID_ARG, "node %d: too many output channels x phases for the bias reduction", i);
+          a.splits = (int32_t)(kPartTiles / (tn * nph));
+          a.per_split = ((cols + a.splits - 1) / a.splits + kBC - 1) / kBC * kBC;
+          a.splits = (int32_t)((cols + a.per_split - 1) / a.per_split);
+        }
+        k_bwd_weight<<<dim3((unsigned)tn, (unsigned)tm, (unsigned)(a.K * a.splits)), 256, 0, st>>>(a);
+      }
+      BW_CUDA(cudaGetLastError());
+      BW_CUDA(t_end());
     } else if (d.op == CC_OP_ADD || d.op == CC_OP_HEADS) {
       if (i != n - 1 && !g->adj_ring[i].rows) continue;  // dead branch
       BwdMerge a{};
@@ -671,16 +1095,20 @@ cc_status cc_backward_chunk(cc_grads* g, cc_stream* const* streams, int32_t coun
       a.b = b;
       a.adj = g->adj;
       a.adj_slot_bytes = g->adj_slot_bytes;
+      BW_CUDA(t_begin(CC_BWD_MERGE, i));
       k_bwd_merge<<<grid_of((int64_t)count * a.n * a.chans), 256, 0, st>>>(a);
       BW_CUDA(cudaGetLastError());
+      BW_CUDA(t_end());
     }
   }
   // 4. the input adjoint of this chunk's frames
   if (grad_x) {
     const cc::NodePlan& p0 = m->nodes[0];
+    BW_CUDA(t_begin(CC_BWD_INPUT, 0));
     k_adj_out<<<grid_of((int64_t)count * p0.u * steps * p0.d.c_out), 256, 0, st>>>(
         b, g->adj, g->adj_slot_bytes, g->adj_ring[0], p0.u * steps, steps, grad_x, gx_stride);
     BW_CUDA(cudaGetLastError());
+    BW_CUDA(t_end());
   }
 #undef BW_CUDA
   return CC_OK;

@@ -87,6 +87,71 @@ def test_backward_matches_oracle_gradient(cclib, cuda, builder, frames, chunk):
             _close(grads[i][1], gw_ref[i][1], f"dL/db node {i} {nodes[i]['name']}")
 
 
+def wide_strided_stack(seed=0):
+    """Layers wide enough for the tiled backward kernels, with the strides of
+    the encoder and decoder: a stride-4 conv (K=8) and a stride-2 conv (K=5,
+    so residues meet different tap counts), a stride-4 transposed conv, a
+    dilated conv and a residual add."""
+    n = W._node
+    nodes = [W.input_node(32),
+             n("conv", [0], 32, 64, k=8, stride=4, pad_left=2, pad_right=2, act_in=None, name="down4"),
+             n("conv", [1], 64, 96, k=5, stride=2, pad_left=2, pad_right=2, act_in="leaky", name="down2"),
+             n("convt", [2], 96, 64, k=8, stride=4, crop=2, act_in="leaky", name="up4"),
+             n("conv", [3], 64, 64, k=3, dilation=3, pad_left=3, pad_right=3, act_in="leaky", name="dil"),
+             n("add", [3, 4], 64, 64, bias=False, name="add"),
+             n("conv", [5], 64, 48, k=3, pad_left=1, pad_right=1, act_in="leaky", name="out")]
+    return nodes, W.init_params(nodes, seed)
+
+
+def test_backward_wide_strided_layers(cclib, cuda):
+    """FP32 parity of the tiled dW / dX kernels (split reductions, residue-
+    ordered rows of strided convolutions, phases of a transposed one) against
+    the oracle's gradient, over chunks of 3 steps with the cache adjoint
+    carried."""
+    import torch
+
+    nodes, p = wide_strided_stack(3)
+    info = M.analyze(nodes)
+    xs = [W.signal(50 + k, 12 * info["in_per_step"], 32) for k in range(3)]
+    seeds = [1, 2, 3]
+    y, gx, grads, r, _, _ = _run(nodes, p, xs, seeds, 3, torch, cuda)
+    gw_ref = {}
+    for k in range(3):
+        _, gxr, gwr = AD.gradients(nodes, p, xs[k], r[k], seed=seeds[k])
+        _close(gx[k], gxr, f"dL/dx stream {k}")
+        for i, (dw, db) in gwr.items():
+            a = gw_ref.get(i)
+            gw_ref[i] = (dw, db) if a is None else (a[0] + dw, None if db is None else a[1] + db)
+    for i, (dw, db) in grads.items():
+        _close(dw, gw_ref[i][0], f"dL/dw {nodes[i]['name']}")
+        if db is not None:
+            _close(db, gw_ref[i][1], f"dL/db {nodes[i]['name']}")
+
+
+def test_weight_gradients_without_input_gradient(cclib, cuda):
+    """An input that does not require a gradient: the backward still runs
+    (the runner's weights anchor), skips the model input's adjoint (grad_x
+    NULL), and every weight and bias gradient is the same, bit for bit."""
+    import torch
+
+    nodes, p = small_autoencoder()
+    xs = [W.signal(40 + k, 96, 1) for k in range(2)]
+    _, _, g_all, r, _, _ = _run(nodes, p, xs, [3, 4], 2, torch, cuda)
+    model = api.Model(nodes, p, dtype="f32", max_streams=2, max_steps_per_call=2)
+    runner = AG.StreamedRunner(model, p, [model.stream(seed=s) for s in (3, 4)], 2)
+    x = torch.tensor(np.stack(xs), dtype=torch.float32, device=cuda)
+    y = AG.streamed(x, runner)
+    assert y.requires_grad and not x.requires_grad
+    y.backward(torch.tensor(r, dtype=torch.float32, device=cuda))
+    torch.cuda.synchronize()
+    assert x.grad is None
+    for i in p:
+        dw, db = runner.grads.read(i)
+        np.testing.assert_array_equal(dw, g_all[i][0])
+        if db is not None:
+            np.testing.assert_array_equal(db, g_all[i][1])
+
+
 def test_gradient_independent_of_chunking(cclib, cuda):
     import torch
 

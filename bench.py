@@ -518,30 +518,39 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_serving(args):
-    """Serving run through the library's scheduler (cc_server_*): streams
-    arrive Poisson(lambda), live U[5, 60] s, draw a buffer size from
-    {512, 1024, 2048, 4096} and submit one request per buffer period, paced in
-    wall-clock time; admission by arena slots (cap concurrent streams).  With
-    --serve-fixed N, N streams of 2048-sample buffers run for the whole time.
-    Latency = submit -> output ready, per request; deadline = buffer duration."""
-    import torch
-
-    import __graft_entry__
-
-    __graft_entry__.build()
+def serve_once(args, kind, cap, fixed, run_s, warm_s, prepare=True):
+    """One serving run through the library's scheduler (cc_server_*), BF16.
+    kind "decoder": latent frames in, audio out; streams arrive Poisson(200/s),
+    live U[5, 60] s and draw a buffer size from {512, 1024, 2048, 4096}.
+    kind "autoencoder": the encoder feeding the decoder, 2048-sample audio
+    buffers in and out.  fixed > 0: that many streams of 2048-sample buffers
+    for the whole run instead of arrivals.  Each stream submits one request
+    per buffer period, paced in wall-clock time, at most 4 in flight.
+    Latency = submit -> output ready; deadline = the buffer's duration."""
     from paper_2204_07064_gb300 import api
 
-    torch.cuda.set_device(0)
-    cap = args.serve_cap if not args.serve_fixed else args.serve_fixed
-    nodes, params, model = build_decoder("bf16", cap + 1)
-    server = api.Server(model, max_batch=cap, bucket=32, use_graphs=True, autotune=True)
+    if kind == "decoder":
+        nodes, params, model = build_decoder("bf16", cap + 1)
+    else:
+        nodes, params, model = build_decoder("bf16", cap + 1, kind="autoencoder")
+    io = model.io
+    cin = io["in_channels"]
+    bucket = max(32, -(-cap // 64))
+    server = api.Server(model, max_batch=cap, bucket=bucket, use_graphs=True, autotune=True)
+    t_prep = time.perf_counter()
+    if prepare:
+        server.prepare(cap)
+    t_prep = time.perf_counter() - t_prep
     rng = np.random.default_rng(3)
     lam = 200.0
-    sizes = np.array([512, 1024, 2048, 4096])
+    sizes = np.array([512, 1024, 2048, 4096]) if (kind == "decoder" and not fixed) else np.array([2048])
+    bmax = int(sizes.max())
     ring = 4  # output buffers per stream (requests in flight per stream)
-    pool = rng.standard_normal((4096, 128)).astype(np.float32)
-    outs = np.zeros((cap, ring, 4096), np.float32)
+    pool_frames = 4096
+    pool = rng.standard_normal((pool_frames * (2048 if kind != "decoder" else 1), cin)).astype(np.float32)
+    if kind != "decoder":
+        pool *= 0.1
+    outs = np.zeros((cap, ring, bmax), np.float32)
     pool_base, out_base = pool.ctypes.data, outs.ctypes.data
     active = np.zeros(cap, bool)
     handles = [None] * cap
@@ -554,21 +563,31 @@ def run_serving(args):
     nreq = np.zeros(cap, np.int64)
     outstanding = np.zeros(cap, np.int64)
     gen = np.zeros(cap, np.int64)
-    warm_s, run_s = args.serve_warmup, args.serve_seconds
     t_start = time.perf_counter_ns()
     t_meas = t_start + int(warm_s * 1e9)
     t_end = t_meas + int(run_s * 1e9)
-    lat, lat_b, conc = [], [], []
+    # results in preallocated arrays (the client must keep up with ~0.5 M
+    # requests/s at 24 k streams: no per-request Python objects, no GC pauses)
+    expect = int((run_s + 2.0) * cap * SR / int(sizes.min()) * 1.2) + 1024
+    res = np.zeros((4, expect), np.float32)  # latency, wait, step (ms), buffer size
+    nres = 0
+    import gc
+    gc_was = gc.isenabled()
+    gc.disable()
     rejected = admitted = 0
     delivered = 0
+    conc = []
     clocks = ClockSampler(0)
     sampled = False
+    wall_meas = None
+    st0 = None
     last = t_start
-    if args.serve_fixed:
+    if fixed:
         for i in range(cap):
             handles[i] = model.stream(seed=i)
             hptr[i] = handles[i].handle.value
-            active[i], B[i], next_due[i], end_ns[i] = True, 2048, t_start + int(rng.uniform(0, 2048 / SR) * 1e9), 1 << 62
+            active[i], B[i], end_ns[i] = True, 2048, 1 << 62
+            next_due[i] = t_start + int(rng.uniform(0, 2048 / SR) * 1e9)
     while True:
         now = time.perf_counter_ns()
         if now >= t_end:
@@ -577,9 +596,10 @@ def run_serving(args):
             clocks.start()
             sampled = True
             wall_meas = time.time()
+            st0 = server.stats()
         dt = (now - last) / 1e9
         last = now
-        if not args.serve_fixed:
+        if not fixed:
             # departures (once nothing is in flight), then Poisson arrivals
             gone = np.nonzero(active & (end_ns <= now) & (outstanding == 0))[0]
             for i in gone:
@@ -608,62 +628,130 @@ def run_serving(args):
         due = np.nonzero(active & (next_due <= now) & (outstanding < ring))[0]
         if len(due):
             b = B[due]
-            asked[due] += b
-            need = -(-asked[due] // 2048)
-            n_in = need - sent[due]
-            sent[due] = need
-            frame = (due * 61 + nreq[due] * 3) % (4096 - 2)
-            in_ptr = (pool_base + frame * 128 * 4).astype(np.uint64)
-            out_ptr = (out_base + ((due * ring + nreq[due] % ring) * 4096) * 4).astype(np.uint64)
+            if kind == "decoder":
+                # latent frames as soon as the output they make is asked for
+                asked[due] += b
+                need = -(-asked[due] // 2048)
+                n_in = need - sent[due]
+                sent[due] = need
+                frame = (due * 61 + nreq[due] * 3) % (pool_frames - 2)
+                in_ptr = (pool_base + frame * cin * 4).astype(np.uint64)
+            else:
+                n_in = b
+                frame = (due * 61 + nreq[due] * 3) % (pool_frames - 2)
+                in_ptr = (pool_base + frame * 2048 * 4).astype(np.uint64)
+            out_ptr = (out_base + ((due * ring + nreq[due] % ring) * bmax) * 4).astype(np.uint64)
             tags = ((gen[due] << 40) | (due << 24) | (nreq[due] & 0xFFFFFF)).astype(np.uint64)
-            server.submit_raw(len(due), np.ascontiguousarray(hptr[due]), in_ptr, n_in.astype(np.int64),
+            server.submit_raw(len(due), np.ascontiguousarray(hptr[due]), in_ptr, np.asarray(n_in, np.int64),
                               out_ptr, b.astype(np.int64), tags)
             nreq[due] += 1
             outstanding[due] += 1
             next_due[due] += (b * 1e9 / SR).astype(np.int64)
-        tags, sub, fin = server.poll()
+        tags, sub, step, fin = server.poll(detail=True)
         if len(tags):
             idx = ((tags >> 24) & 0xFFFF).astype(np.int64)
             g = (tags >> 40).astype(np.int64)
             live = g == gen[idx]
-            np.subtract.at(outstanding, idx[live], 1)
+            outstanding -= np.bincount(idx[live], minlength=cap)
             if now >= t_meas:
-                lat.extend(((fin - sub) / 1e6).tolist())
-                lat_b.extend(B[idx].tolist())
+                k = min(len(tags), expect - nres)
+                res[0, nres:nres + k] = (fin[:k] - sub[:k]) / 1e6
+                res[1, nres:nres + k] = (step[:k] - sub[:k]) / 1e6
+                res[2, nres:nres + k] = (fin[:k] - step[:k]) / 1e6
+                res[3, nres:nres + k] = B[idx[:k]]
+                nres += k
                 delivered += int(B[idx].sum())
         if now >= t_meas:
             conc.append(int(active.sum()))
         time.sleep(0.0005)
     clk = clocks.stop((wall_meas, time.time())) if sampled else None
+    if gc_was:
+        gc.enable()
     st = server.stats()
     server.close()
-    lat = np.asarray(lat)
-    lat_b = np.asarray(lat_b)
+    model.close()
+    lat, wait, stepd, lat_b = res[0, :nres], res[1, :nres], res[2, :nres], res[3, :nres]
     per_b = {}
     for b in sizes:
         m = lat_b == b
         if m.any():
-            per_b[str(int(b))] = {"p50_ms": float(np.percentile(lat[m], 50)),
-                                  "p99_ms": float(np.percentile(lat[m], 99)),
-                                  "deadline_ms": 1000.0 * b / SR,
-                                  "met": float(np.mean(lat[m] < 1000.0 * b / SR)), "requests": int(m.sum())}
-    line = {
-        "metric": METRIC, "value": delivered / run_s / SR, "unit": "streams", "n_gpus": 1,
-        "steps": int(st["batches"]), "warmup": warm_s, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": "serving-bf16" if not args.serve_fixed else f"serving-bf16-fixed{cap}",
-                   "arrivals_per_s": 0 if args.serve_fixed else lam, "cap_streams": cap,
-                   "buffer_samples": "2048" if args.serve_fixed else "U{512,1024,2048,4096}",
-                   "lifetime_s": None if args.serve_fixed else "U[5,60]", "seconds": run_s},
+            dl = 1000.0 * b / SR
+            miss = m & (lat >= dl)
+            e = {"p50_ms": float(np.percentile(lat[m], 50)), "p99_ms": float(np.percentile(lat[m], 99)),
+                 "max_ms": float(lat[m].max()), "deadline_ms": dl, "met": float(np.mean(lat[m] < dl)),
+                 "requests": int(m.sum())}
+            if miss.any():
+                # where a missed request's time went: waiting for its step to
+                # start (queue, the previous batch, the host) vs the step itself
+                e["missed"] = {"count": int(miss.sum()), "wait_p50_ms": float(np.median(wait[miss])),
+                               "step_p50_ms": float(np.median(stepd[miss])),
+                               "wait_max_ms": float(wait[miss].max()), "step_max_ms": float(stepd[miss].max())}
+            per_b[str(int(b))] = e
+    meas = {k: st[k] - (st0 or {}).get(k, 0) for k in ("batches", "stream_steps", "gpu_ns", "setups", "setup_ns")}
+    return {
+        "value": delivered / run_s / SR, "cap": cap, "fixed": fixed,
         "latency_ms": {"p50": float(np.percentile(lat, 50)) if len(lat) else None,
-                       "p99": float(np.percentile(lat, 99)) if len(lat) else None, "per_buffer": per_b,
+                       "p99": float(np.percentile(lat, 99)) if len(lat) else None,
+                       "max": float(lat.max()) if len(lat) else None,
+                       "wait_p50": float(np.percentile(wait, 50)) if len(wait) else None,
+                       "step_p50": float(np.percentile(stepd, 50)) if len(stepd) else None,
+                       "per_buffer": per_b,
                        "met_deadline": float(np.mean([v["met"] for v in per_b.values()])) if per_b else None},
         "streams": {"mean_concurrent": float(np.mean(conc)) if conc else 0, "max_concurrent": int(max(conc or [0])),
                     "admitted": admitted, "rejected": rejected},
-        "server": {"batches": st["batches"], "stream_steps": st["stream_steps"], "max_batch": st["max_batch"],
-                   "gpu_busy": st["gpu_ns"] / ((warm_s + run_s) * 1e9)},
+        "server": {"bucket": bucket, "prepare_s": t_prep if prepare else None,
+                   "batches": meas["batches"], "stream_steps": meas["stream_steps"],
+                   "mean_batch": meas["stream_steps"] / max(1, meas["batches"]), "max_batch": st["max_batch"],
+                   "gpu_busy": meas["gpu_ns"] / (run_s * 1e9), "setups_while_serving": meas["setups"],
+                   "setup_ms_while_serving": meas["setup_ns"] / 1e6},
         "clocks": clk,
     }
+
+
+def run_serving(args):
+    """Serving form through the library's scheduler.  Without --serve-sweep:
+    one run (Poisson arrivals, or --serve-fixed N streams).  With
+    --serve-sweep N1,N2,..: fixed-N runs of 2048-sample buffers at growing N
+    (the capacity sweep), stopping after the first N whose p99 latency reaches
+    the buffer duration.  Every bucket is tuned and captured before the
+    measured region (cc_server_prepare) unless --serve-no-prepare."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    kind = args.serve_model
+    prepare = not args.serve_no_prepare
+    base = {"metric": METRIC, "unit": "streams", "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic"}
+    if args.serve_sweep:
+        points = []
+        for n in [int(v) for v in args.serve_sweep.split(",")]:
+            r = serve_once(args, kind, n, n, args.serve_seconds, args.serve_warmup, prepare)
+            points.append(r)
+            print(json.dumps({"sweep_point": n, "value": r["value"], "p99_ms": r["latency_ms"]["p99"],
+                              "max_ms": r["latency_ms"]["max"], "gpu_busy": r["server"]["gpu_busy"]}),
+                  file=sys.stderr, flush=True)
+            if r["latency_ms"]["p99"] is None or r["latency_ms"]["p99"] >= 2048 / SR * 1000.0:
+                break
+        ok = [p for p in points if p["latency_ms"]["p99"] is not None and p["latency_ms"]["p99"] < 2048 / SR * 1000.0]
+        line = dict(base, value=max([p["value"] for p in ok], default=0.0),
+                    config={"workload": f"serving-sweep-{kind}-bf16", "buffer_samples": 2048,
+                            "seconds_per_point": args.serve_seconds, "warmup_s": args.serve_warmup,
+                            "prepared": prepare},
+                    sweep=points,
+                    note="value: the largest N whose p99 stayed under the 42.7 ms buffer")
+    else:
+        fixed = args.serve_fixed
+        cap = fixed if fixed else args.serve_cap
+        r = serve_once(args, kind, cap, fixed, args.serve_seconds, args.serve_warmup, prepare)
+        line = dict(base, **{k: v for k, v in r.items() if k not in ("cap", "fixed")})
+        line["config"] = {"workload": f"serving-{kind}-bf16" + (f"-fixed{cap}" if fixed else ""),
+                          "arrivals_per_s": 0 if fixed else 200.0, "cap_streams": cap,
+                          "buffer_samples": "2048" if (fixed or kind != "decoder") else "U{512,1024,2048,4096}",
+                          "lifetime_s": None if fixed else "U[5,60]", "seconds": args.serve_seconds,
+                          "prepared": prepare}
     print(json.dumps(line))
 
 
@@ -686,6 +774,9 @@ def main():
     ap.add_argument("--serve-warmup", type=float, default=10.0)
     ap.add_argument("--serve-cap", type=int, default=2048)
     ap.add_argument("--serve-fixed", type=int, default=0, help="N fixed streams of 2048-sample buffers")
+    ap.add_argument("--serve-model", default="decoder", choices=["decoder", "autoencoder"])
+    ap.add_argument("--serve-sweep", default="", help="comma-separated fixed stream counts (capacity sweep)")
+    ap.add_argument("--serve-no-prepare", action="store_true", help="set buckets up lazily while serving")
     ap.add_argument("--differentiate", action="store_true",
                     help="time the streamed forward + hand-written backward of the encoder + decoder")
     ap.add_argument("--diff-streams", type=int, default=32)

@@ -420,15 +420,25 @@ cc_status cc_server_destroy(cc_server* server);
 cc_status cc_server_submit(cc_server* server, int32_t count, cc_stream* const* streams,
                            const float* const* in, const int64_t* n_in, float* const* out,
                            const int64_t* n_out, const uint64_t* tags);
-/* Up to max completed requests: tag, submit and completion times (ns,
- * steady clock).  Returns the scheduler's error if it stopped on one. */
+/* Up to max completed requests: tag, submit time, start of the GPU step that
+ * completed the request (its submit time when the stream's FIFO already held
+ * the output) and completion time (ns, steady clock; every array may be
+ * NULL).  Returns the scheduler's error if it stopped on one. */
 cc_status cc_server_poll(cc_server* server, int32_t max, uint64_t* tags, int64_t* submit_ns,
-                         int64_t* done_ns, int32_t* got);
+                         int64_t* step_ns, int64_t* done_ns, int32_t* got);
 /* Forgets a stream (its pending requests are dropped) once it is not in the
  * batch on the GPU; call before cc_stream_destroy of a served stream. */
 cc_status cc_server_remove(cc_server* server, cc_stream* stream);
+/* Batches run, stream-steps, time in GPU steps (ns), the largest batch, and
+ * the first batches of a bucket (tuning, warm-up and graph capture: their
+ * number and time, cc_server_prepare's included); any may be NULL. */
 cc_status cc_server_stats(cc_server* server, int64_t* batches, int64_t* stream_steps,
-                          int64_t* gpu_ns, int64_t* max_batch);
+                          int64_t* gpu_ns, int64_t* max_batch, int64_t* setups, int64_t* setup_ns);
+/* Tunes, warms up and captures every bucket of batches up to max_count
+ * streams now, so that no request later waits behind that set-up (it takes a
+ * few milliseconds per bucket).  Waits for the batch on the GPU, holds the
+ * scheduler off meanwhile; requests submitted during the call wait for it. */
+cc_status cc_server_prepare(cc_server* server, int32_t max_count);
 
 /* Host utility: a cosine-modulated pseudo-QMF bank (bands x taps) with a
  * Kaiser(beta) prototype whose cutoff minimises the prototype autocorrelation

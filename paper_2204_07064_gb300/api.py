@@ -84,9 +84,11 @@ _SIGNATURES = {
     "cc_server_create": [_P, C.c_void_p, C.POINTER(_P)],
     "cc_server_destroy": [_P],
     "cc_server_submit": [_P, _I32, _P, _P, _P, _P, _P, _P],
-    "cc_server_poll": [_P, _I32, _P, _P, _P, C.POINTER(_I32)],
+    "cc_server_poll": [_P, _I32, _P, _P, _P, _P, C.POINTER(_I32)],
+    "cc_server_prepare": [_P, _I32],
     "cc_server_remove": [_P, _P],
-    "cc_server_stats": [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
+    "cc_server_stats": [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64),
+                        C.POINTER(_I64)],
     "cc_grads_create": [_P, C.POINTER(_P), C.POINTER(_P)],
     "cc_grads_destroy": [_P],
     "cc_grads_zero": [_P],
@@ -482,23 +484,33 @@ class Server:
                                           n_in.ctypes.data, out_ptrs.ctypes.data, n_out.ctypes.data,
                                           tags.ctypes.data))
 
-    def poll(self, max_items=65536):
+    def poll(self, max_items=65536, detail=False):
+        """(tags, submit_ns, done_ns) of completed requests; with detail=True
+        also the start of the GPU step that completed each (before done_ns)."""
         tags = np.empty(max_items, np.uint64)
         sub = np.empty(max_items, np.int64)
+        step = np.empty(max_items, np.int64)
         done = np.empty(max_items, np.int64)
         got = _I32()
-        _check(lib().cc_server_poll(self.handle, max_items, tags.ctypes.data, sub.ctypes.data, done.ctypes.data,
-                                    C.byref(got)))
+        _check(lib().cc_server_poll(self.handle, max_items, tags.ctypes.data, sub.ctypes.data, step.ctypes.data,
+                                    done.ctypes.data, C.byref(got)))
         n = got.value
+        if detail:
+            return tags[:n], sub[:n], step[:n], done[:n]
         return tags[:n], sub[:n], done[:n]
+
+    def prepare(self, max_count):
+        """Tune and capture every batch bucket up to max_count streams now."""
+        _check(lib().cc_server_prepare(self.handle, int(max_count)))
 
     def remove(self, stream):
         _check(lib().cc_server_remove(self.handle, stream.handle))
 
     def stats(self):
-        v = [_I64() for _ in range(4)]
+        v = [_I64() for _ in range(6)]
         _check(lib().cc_server_stats(self.handle, *[C.byref(x) for x in v]))
-        return dict(batches=v[0].value, stream_steps=v[1].value, gpu_ns=v[2].value, max_batch=v[3].value)
+        return dict(batches=v[0].value, stream_steps=v[1].value, gpu_ns=v[2].value, max_batch=v[3].value,
+                    setups=v[4].value, setup_ns=v[5].value)
 
     def close(self):
         if getattr(self, "handle", None):

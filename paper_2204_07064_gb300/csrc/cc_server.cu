@@ -11,7 +11,10 @@
 // step (e.g. 512-sample buffers of a decoder that emits 2048 samples per
 // step) are served from the FIFO.  Each batch size is padded to a bucket with
 // a scratch slot and its launch chain is replayed from a CUDA graph; the tile
-// shapes of each bucket come from the model's autotuner.
+// shapes of each bucket come from the model's autotuner.  For large batches
+// the per-stream host work (gathering inputs, handing outputs to requests) is
+// split across worker threads, and an output goes straight into the waiting
+// request's buffer when the stream's FIFO is empty.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,7 +22,9 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -44,6 +49,11 @@ int64_t now_ns() {
              std::chrono::steady_clock::now().time_since_epoch())
       .count();
 }
+
+// batches of at least kParallelMin streams split their host work across up
+// to kWorkers threads
+constexpr int32_t kParallelMin = 1024;
+constexpr int32_t kWorkers = 8;
 
 struct Request {
   float* out;
@@ -72,7 +82,66 @@ struct FloatFifo {
   }
 };
 
+// Worker threads kept for the life of a server: run(fn) calls fn(k) on
+// worker k = 1..size()-1 and on the caller as worker 0, and returns when all
+// are done.
+class Pool {
+ public:
+  explicit Pool(int32_t n) {
+    for (int32_t k = 1; k < n; ++k) th_.emplace_back([this, k] { work(k); });
+  }
+  ~Pool() {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      quit_ = true;
+      ++gen_;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  int32_t size() const { return (int32_t)th_.size() + 1; }
+  void run(const std::function<void(int32_t)>& fn) {
+    {
+      std::lock_guard<std::mutex> g(m_);
+      fn_ = &fn;
+      pending_ = (int32_t)th_.size();
+      ++gen_;
+    }
+    cv_.notify_all();
+    fn(0);
+    std::unique_lock<std::mutex> lk(m_);
+    done_.wait(lk, [&] { return pending_ == 0; });
+    fn_ = nullptr;
+  }
+
+ private:
+  void work(int32_t k) {
+    uint64_t seen = 0;
+    for (;;) {
+      const std::function<void(int32_t)>* f = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(m_);
+        cv_.wait(lk, [&] { return gen_ != seen; });
+        seen = gen_;
+        if (quit_) return;
+        f = fn_;
+      }
+      (*f)(k);
+      std::lock_guard<std::mutex> g(m_);
+      if (--pending_ == 0) done_.notify_one();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex m_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int32_t)>* fn_ = nullptr;
+  int32_t pending_ = 0;
+  uint64_t gen_ = 0;
+  bool quit_ = false;
+};
+
 struct StreamQueue {
+  bool queued = false;  // listed in the server's ready list
   FloatFifo in;   // buffered input (interleaved frames)
   FloatFifo out;  // produced, not yet delivered output
   std::deque<Request> reqs;
@@ -81,7 +150,7 @@ struct StreamQueue {
 
 struct Completion {
   uint64_t tag;
-  int64_t submit_ns, done_ns;
+  int64_t submit_ns, step_ns, done_ns;  // step_ns: start of the GPU step that completed it
 };
 
 }  // namespace
@@ -110,8 +179,17 @@ struct cc_server {
   cc_status error = CC_OK;
   std::string error_msg;
   std::thread th;
+  bool preparing = false;  // cc_server_prepare owns the GPU side
+  std::vector<StreamQueue*> sq_ptr;                   // the batch's queues
+  // streams that may need a step (submitted to, or served, since they were
+  // last batched); an entry counts only while its queue's `queued` is set,
+  // so removed or re-listed streams are skipped
+  std::vector<cc_stream*> ready_list, cand;
+  std::unique_ptr<Pool> pool;
+  std::vector<Completion> part_done[kWorkers];        // completions found by workers 1..
   // statistics
   int64_t batches = 0, stream_steps = 0, gpu_ns = 0, max_batch_seen = 0;
+  int64_t setups = 0, setup_ns = 0;  // first batches of a bucket: tuning, warm-up, graph capture
 
   int32_t bucket(int32_t count) const {
     const int32_t g = cfg.bucket > 0 ? cfg.bucket : 32;
@@ -121,7 +199,29 @@ struct cc_server {
   bool needs_step(const StreamQueue& s) const {
     return s.owed * cout > (int64_t)s.out.size() && (int64_t)s.in.size() >= (int64_t)in_step * cin;
   }
-  void serve_fifo(StreamQueue& s, int64_t t) {
+  void mark(cc_stream* st, StreamQueue& s) {
+    if (!s.queued && needs_step(s)) {
+      s.queued = true;
+      ready_list.push_back(st);
+    }
+  }
+  // fn(begin, end, worker) over [0, n) in contiguous parts, on the pool's
+  // threads from kParallelMin items on
+  template <typename F>
+  void parallel_parts(int32_t n, F fn) {
+    const int32_t w = (n < kParallelMin || !pool) ? 1 : pool->size();
+    if (w == 1) {
+      fn(0, n, 0);
+      return;
+    }
+    const int32_t per = (n + w - 1) / w;
+    pool->run([&](int32_t k) {
+      const int32_t a = k * per, b = std::min(n, a + per);
+      if (a < b) fn(a, b, k);
+    });
+  }
+  void serve_fifo(StreamQueue& s, int64_t t, int64_t t_step) { serve_fifo(s, t, t_step, done); }
+  void serve_fifo(StreamQueue& s, int64_t t, int64_t t_step, std::vector<Completion>& out_done) {
     while (!s.reqs.empty()) {
       Request& r = s.reqs.front();
       const int64_t avail = (int64_t)s.out.size() / cout;
@@ -130,10 +230,34 @@ struct cc_server {
       r.done_frames += take;
       s.owed -= take;
       if (r.done_frames < r.n_out) break;
-      done.push_back(Completion{r.tag, r.submit_ns, t});
+      out_done.push_back(Completion{r.tag, r.submit_ns, t_step, t});
       s.reqs.pop_front();
     }
   }
+  // A step's output of one stream: straight into the waiting requests'
+  // buffers while the FIFO is empty, the rest into the FIFO.
+  void deliver(StreamQueue& s, const float* src, size_t n, int64_t t, int64_t t_step, std::vector<Completion>& out_done) {
+    size_t off = 0;
+    if (s.out.size() == 0) {
+      while (off < n && !s.reqs.empty()) {
+        Request& r = s.reqs.front();
+        const int64_t take = std::min<int64_t>((int64_t)((n - off) / cout), r.n_out - r.done_frames);
+        if (take > 0) std::memcpy(r.out + r.done_frames * cout, src + off, (size_t)take * cout * sizeof(float));
+        off += (size_t)take * cout;
+        r.done_frames += take;
+        s.owed -= take;
+        if (r.done_frames < r.n_out) break;
+        out_done.push_back(Completion{r.tag, r.submit_ns, t_step, t});
+        s.reqs.pop_front();
+      }
+    }
+    if (off < n) s.out.push(src + off, n - off);
+    serve_fifo(s, t, t_step, out_done);
+  }
+  bool ready(int32_t padded) const {
+    return (!cfg.autotune || tuned.count(padded)) && (!cfg.use_graphs || graphs.count(padded));
+  }
+  cc_status setup(int32_t padded);
   cc_status gpu_step(int32_t count, int32_t padded);
   void loop();
 };
@@ -148,11 +272,12 @@ namespace {
 
 }  // namespace
 
-cc_status cc_server::gpu_step(int32_t count, int32_t padded) {
+// First batch of a bucket: tune tile shapes and warm the kernels up on a batch
+// made of the scratch slot only (its rings are never read back), then capture
+// the bucket's launch chain.
+cc_status cc_server::setup(int32_t padded) {
   const int64_t is = (int64_t)in_step * cin, os = (int64_t)out_step * cout;
-  if ((cfg.autotune && !tuned.count(padded)) || (cfg.use_graphs && !graphs.count(padded))) {
-    // First batch of this bucket: tune tile shapes and warm the kernels up on
-    // a batch made of the scratch slot only (its rings are never read back).
+  {
     const cc::Batch scratch_batch = m->batch_for(d_scratch_slots, padded);
     if (cfg.autotune && !tuned.count(padded)) {
       cc_status s = m->autotune(d_scratch_slots, padded, d_in, is, d_out, os, st);
@@ -181,6 +306,11 @@ cc_status cc_server::gpu_step(int32_t count, int32_t padded) {
       graphs.emplace(padded, ge);
     }
   }
+  return CC_OK;
+}
+
+cc_status cc_server::gpu_step(int32_t count, int32_t padded) {
+  const int64_t is = (int64_t)in_step * cin, os = (int64_t)out_step * cout;
   SRV_CUDA(cudaMemcpyAsync(d_slots, h_slots, sizeof(int32_t) * padded, cudaMemcpyHostToDevice, st));
   SRV_CUDA(cudaMemcpyAsync(d_in, h_in, sizeof(float) * (size_t)padded * is, cudaMemcpyHostToDevice, st));
   if (cfg.use_graphs) {
@@ -195,18 +325,38 @@ cc_status cc_server::gpu_step(int32_t count, int32_t padded) {
 }
 
 void cc_server::loop() {
+  {
+    const int32_t hw = (int32_t)std::max(1u, std::thread::hardware_concurrency());
+    const int32_t w = std::min(kWorkers, std::max(1, hw / 2));
+    if (w > 1) pool.reset(new Pool(w));
+  }
   std::vector<cc_stream*> batch;
   std::unique_lock<std::mutex> lk(mu);
   while (!stop) {
-    // every stream with a request waiting and a step of input, oldest request first
+    if (preparing) {
+      cv.wait_for(lk, std::chrono::milliseconds(2));
+      continue;
+    }
+    // every stream with a request waiting and a step of input (from the
+    // ready list), oldest request first
     batch.clear();
-    for (auto& kv : q)
-      if (needs_step(kv.second)) batch.push_back(kv.first);
+    cand.swap(ready_list);
+    for (cc_stream* st : cand) {
+      auto it = q.find(st);
+      if (it == q.end() || !it->second.queued) continue;
+      it->second.queued = false;
+      if (needs_step(it->second)) batch.push_back(st);
+    }
+    cand.clear();
     if ((int32_t)batch.size() > cfg.max_batch) {
       std::nth_element(batch.begin(), batch.begin() + cfg.max_batch, batch.end(),
                        [&](cc_stream* x, cc_stream* y) {
                          return q[x].reqs.front().submit_ns < q[y].reqs.front().submit_ns;
                        });
+      for (size_t k = cfg.max_batch; k < batch.size(); ++k) {
+        q[batch[k]].queued = true;
+        ready_list.push_back(batch[k]);
+      }
       batch.resize(cfg.max_batch);
     }
     if (batch.empty()) {
@@ -216,20 +366,33 @@ void cc_server::loop() {
     const int32_t count = (int32_t)batch.size();
     const int32_t padded = bucket(count);
     const size_t step_in = (size_t)in_step * cin;
+    // (the scheduler holds the lock: nothing else touches the queues)
+    sq_ptr.resize(count);
     for (int32_t i = 0; i < count; ++i) {
-      StreamQueue& s = q[batch[i]];
-      h_slots[i] = cc::stream_slot(batch[i]);
-      s.in.pop(h_in + i * step_in, step_in);
+      sq_ptr[i] = &q[batch[i]];
       in_flight.insert(batch[i]);
     }
+    parallel_parts(count, [&](int32_t a, int32_t b, int32_t) {
+      for (int32_t i = a; i < b; ++i) {
+        h_slots[i] = cc::stream_slot(batch[i]);
+        sq_ptr[i]->in.pop(h_in + i * step_in, step_in);
+      }
+    });
     const int32_t sslot = cc::stream_slot(scratch);
     for (int32_t i = count; i < padded; ++i) {
       h_slots[i] = sslot;
       std::memset(h_in + i * step_in, 0, step_in * sizeof(float));
     }
     lk.unlock();
+    int64_t t_setup = 0;
+    cc_status s = CC_OK;
+    if (!ready(padded)) {
+      const int64_t a = now_ns();
+      s = setup(padded);
+      t_setup = now_ns() - a;
+    }
     const int64_t t0 = now_ns();
-    cc_status s = gpu_step(count, padded);
+    if (!s) s = gpu_step(count, padded);
     const int64_t t1 = now_ns();
     lk.lock();
     if (s) {
@@ -243,15 +406,22 @@ void cc_server::loop() {
     ++batches;
     stream_steps += count;
     gpu_ns += t1 - t0;
+    if (t_setup) {
+      ++setups;
+      setup_ns += t_setup;
+    }
     max_batch_seen = std::max<int64_t>(max_batch_seen, count);
     const size_t step_out = (size_t)out_step * cout;
-    for (int32_t i = 0; i < count; ++i) {
-      auto it = q.find(batch[i]);
-      if (it == q.end()) continue;
-      StreamQueue& sq = it->second;
-      sq.out.push(h_out + i * step_out, step_out);
-      serve_fifo(sq, t1);
+    // (streams removed meanwhile waited for this batch: every queue is there)
+    parallel_parts(count, [&](int32_t a, int32_t b, int32_t w) {
+      std::vector<Completion>& mine = w == 0 ? done : part_done[w];
+      for (int32_t i = a; i < b; ++i) deliver(*sq_ptr[i], h_out + i * step_out, step_out, t1, t0, mine);
+    });
+    for (int32_t w = 1; w < kWorkers; ++w) {
+      done.insert(done.end(), part_done[w].begin(), part_done[w].end());
+      part_done[w].clear();
     }
+    for (int32_t i = 0; i < count; ++i) mark(batch[i], *sq_ptr[i]);
     in_flight.clear();
     idle_cv.notify_all();
   }
@@ -366,20 +536,22 @@ cc_status cc_server_submit(cc_server* s, int32_t count, cc_stream* const* stream
     if (n_in[i]) q.in.push(in[i], (size_t)(n_in[i] * s->cin));
     q.owed += n_out[i];
     q.reqs.push_back(Request{n_out[i] ? out[i] : nullptr, n_out[i], 0, tags[i], t});
-    s->serve_fifo(q, t);
+    s->serve_fifo(q, t, t);
+    s->mark(streams[i], q);
   }
   s->cv.notify_one();
   return CC_OK;
 }
 
-cc_status cc_server_poll(cc_server* s, int32_t max, uint64_t* tags, int64_t* submit_ns, int64_t* done_ns,
-                         int32_t* got) {
+cc_status cc_server_poll(cc_server* s, int32_t max, uint64_t* tags, int64_t* submit_ns, int64_t* step_ns,
+                         int64_t* done_ns, int32_t* got) {
   if (!s || !got || max < 0) return cc::fail(CC_ERR_INVALID_ARG, "null argument");
   std::lock_guard<std::mutex> g(s->mu);
   const int32_t n = std::min<int32_t>(max, (int32_t)s->done.size());
   for (int32_t i = 0; i < n; ++i) {
     if (tags) tags[i] = s->done[i].tag;
     if (submit_ns) submit_ns[i] = s->done[i].submit_ns;
+    if (step_ns) step_ns[i] = s->done[i].step_ns;
     if (done_ns) done_ns[i] = s->done[i].done_ns;
   }
   s->done.erase(s->done.begin(), s->done.begin() + n);
@@ -397,14 +569,47 @@ cc_status cc_server_remove(cc_server* s, cc_stream* stream) {
 }
 
 cc_status cc_server_stats(cc_server* s, int64_t* batches, int64_t* stream_steps, int64_t* gpu_ns,
-                          int64_t* max_batch) {
+                          int64_t* max_batch, int64_t* setups, int64_t* setup_ns) {
   if (!s) return cc::fail(CC_ERR_INVALID_ARG, "null server");
   std::lock_guard<std::mutex> g(s->mu);
   if (batches) *batches = s->batches;
   if (stream_steps) *stream_steps = s->stream_steps;
   if (gpu_ns) *gpu_ns = s->gpu_ns;
   if (max_batch) *max_batch = s->max_batch_seen;
+  if (setups) *setups = s->setups;
+  if (setup_ns) *setup_ns = s->setup_ns;
   return CC_OK;
+}
+
+cc_status cc_server_prepare(cc_server* s, int32_t max_count) {
+  if (!s) return cc::fail(CC_ERR_INVALID_ARG, "null server");
+  if (max_count < 1 || max_count > s->cfg.max_batch)
+    return cc::fail(CC_ERR_INVALID_ARG, "max_count must be in [1, max_batch]");
+  std::unique_lock<std::mutex> lk(s->mu);
+  // wait for the batch on the GPU, then hold the scheduler off
+  s->idle_cv.wait(lk, [&] { return s->in_flight.empty() || s->stop; });
+  if (s->error) return cc::fail(s->error, "server stopped: %s", s->error_msg.c_str());
+  s->preparing = true;
+  lk.unlock();
+  cc_status r = CC_OK;
+  int64_t n = 0, ns = 0;
+  for (int32_t c = 1; c <= max_count && r == CC_OK;) {
+    const int32_t padded = s->bucket(c);
+    if (!s->ready(padded)) {
+      const int64_t a = now_ns();
+      r = s->setup(padded);
+      ns += now_ns() - a;
+      ++n;
+    }
+    if (padded >= s->cap) break;
+    c = padded + 1;
+  }
+  lk.lock();
+  s->preparing = false;
+  s->setups += n;
+  s->setup_ns += ns;
+  s->cv.notify_one();
+  return r;
 }
 
 }  // extern "C"

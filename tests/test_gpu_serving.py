@@ -133,3 +133,52 @@ def test_admission_by_arena_slots(cclib, cuda):
     done = _drain(server, [4_000_007])
     assert done[4_000_007][1] >= done[4_000_007][0]
     server.close()
+
+
+def test_prepare_sets_every_bucket_up_front(cclib, cuda):
+    """cc_server_prepare tunes and captures each bucket before serving: the
+    later batches need no set-up, every request reports the start of the GPU
+    step that completed it (submit <= step start <= done), and the outputs are
+    those of an unprepared server."""
+    dec, p = _decoder(5)
+    z = W.signal(6, 3, 128)
+    outs = {}
+    for prepared in (False, True):
+        model = api.Model(dec, p, dtype="bf16", max_streams=10, max_steps_per_call=1)
+        server = api.Server(model, max_batch=8, bucket=4)
+        if prepared:
+            server.prepare(8)
+            st = server.stats()
+            assert st["setups"] == 2 and st["batches"] == 0 and st["setup_ns"] > 0  # buckets of 4 and 8
+        streams = [model.stream(seed=20 + k) for k in range(6)]
+        ys = [[] for _ in streams]
+        for t in range(3):
+            frames = np.ascontiguousarray(z[t:t + 1], dtype=np.float32)
+            bufs = [np.zeros((2048, 1), np.float32) for _ in streams]
+            tags = [7_000_000 + 1000 * prepared + 10 * t + k for k in range(len(streams))]
+            server.submit(streams, [frames] * len(streams), [1] * len(streams), bufs, [2048] * len(streams), tags)
+            got = {}
+            t0 = time.time()
+            while len(got) < len(tags) and time.time() - t0 < 30:
+                tg, sub, step, fin = server.poll(detail=True)
+                for a, b, c, d in zip(tg, sub, step, fin):
+                    got[int(a)] = (int(b), int(c), int(d))
+                time.sleep(0.001)
+            assert len(got) == len(tags)
+            for tag in tags:
+                sub, step, fin = got[tag]
+                assert sub <= step <= fin
+            for k, b in enumerate(bufs):
+                ys[k].append(b[:, 0].copy())
+        st = server.stats()
+        if prepared:
+            assert st["setups"] == 2  # nothing set up while serving
+        else:
+            assert st["setups"] >= 1
+        outs[prepared] = [np.concatenate(y) for y in ys]
+        server.close()
+        model.close()
+    # the autotuner may pick other tile shapes for the same bucket (timing):
+    # same result within the FP32 bar
+    for a, b in zip(outs[False], outs[True]):
+        np.testing.assert_allclose(b, a, rtol=0, atol=1e-5 * np.sqrt(np.mean(a ** 2)))

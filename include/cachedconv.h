@@ -399,7 +399,7 @@ cc_status cc_stream_restore(cc_stream* stream, const void* dev_buf, size_t bytes
  * launch chain of each bucket is replayed from a CUDA graph (use_graphs) and
  * its tile shapes come from the model's autotuner (autotune: each
  * tensor-core layer is timed with 128- and 256-column tiles on the scratch
- * slot and the faster is kept). */
+ * slot, three rounds alternating the two, and the smaller minimum is kept). */
 typedef struct cc_server cc_server;
 typedef struct {
   int32_t max_batch;  /* streams per launch chain, <= the model's max_streams - 1 */

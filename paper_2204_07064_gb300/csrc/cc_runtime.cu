@@ -813,40 +813,43 @@ int32_t Model::tile_n_for(const NodePlan& p, int64_t n_cols) const {
 // launch), and keeps the faster shape per layer for this launch width.  The
 // chain runs on the given slots, whose rings and step counters it advances:
 // callers pass scratch slots.
+// Tile width per tensor-core layer for one launch width: each candidate (128
+// and 256 columns) is warmed up, then timed per layer in kTuneRounds rounds
+// that alternate the candidates (so a clock or occupancy drift does not favour
+// one), and each layer keeps the candidate with the smaller per-round minimum.
 cc_status Model::autotune(const int32_t* d_slots, int32_t count, const float* in, int64_t in_stride,
                           float* out, int64_t out_stride, cudaStream_t st) {
+  constexpr int kTuneRounds = 3;
   const int n = (int)nodes.size();
-  std::vector<double> best(n, 1e30);
-  std::vector<int32_t> pick(n, 0);
+  const int32_t cands[2] = {128, 256};
+  std::vector<double> best_ms[2] = {std::vector<double>(n, 1e30), std::vector<double>(n, 1e30)};
   const Batch b = batch_for(d_slots, count);
-  for (const int32_t cand : {128, 256}) {
-    force_tile_n = cand;
-    cc_status s = run_chain(b, in, in_stride, out, out_stride, 1, st);  // warm (kernel attributes)
-    if (s) {
-      force_tile_n = 0;
-      return s;
-    }
-    CC_CUDA(cudaStreamSynchronize(st));
-    timing_on = true;
-    timing_recs.clear();
-    event_pool_used = 0;
-    s = run_chain(b, in, in_stride, out, out_stride, 1, st);
-    timing_on = false;
+  for (int c = 0; c < 2; ++c) {  // warm up (kernel attributes, caches)
+    force_tile_n = cands[c];
+    cc_status s = run_chain(b, in, in_stride, out, out_stride, 1, st);
     force_tile_n = 0;
     if (s) return s;
-    CC_CUDA(cudaStreamSynchronize(st));
-    std::vector<double> ms(n, 0.0);
-    for (auto& rec : timing_recs) {
-      float t = 0.f;
-      CC_CUDA(cudaEventElapsedTime(&t, rec.start, rec.stop));
-      ms[rec.node] += t;
-    }
-    for (int i = 0; i < n; ++i)
-      if (nodes[i].engine == 1 && ms[i] < best[i]) {
-        best[i] = ms[i];
-        pick[i] = cand;
-      }
   }
+  CC_CUDA(cudaStreamSynchronize(st));
+  for (int round = 0; round < kTuneRounds; ++round)
+    for (int c = 0; c < 2; ++c) {
+      force_tile_n = cands[c];
+      timing_on = true;
+      timing_recs.clear();
+      event_pool_used = 0;
+      cc_status s = run_chain(b, in, in_stride, out, out_stride, 1, st);
+      timing_on = false;
+      force_tile_n = 0;
+      if (s) return s;
+      CC_CUDA(cudaStreamSynchronize(st));
+      std::vector<double> ms(n, 0.0);
+      for (auto& rec : timing_recs) {
+        float t = 0.f;
+        CC_CUDA(cudaEventElapsedTime(&t, rec.start, rec.stop));
+        ms[rec.node] += t;
+      }
+      for (int i = 0; i < n; ++i) best_ms[c][i] = std::min(best_ms[c][i], ms[i]);
+    }
   timing_recs.clear();
   event_pool_used = 0;
   for (int i = 0; i < n; ++i) {
@@ -854,7 +857,7 @@ cc_status Model::autotune(const int32_t* d_slots, int32_t count, const float* in
     if (p.engine != 1) continue;
     const NodePlan& src = nodes[p.d.inputs[0]];
     const int64_t cols = (int64_t)count * (p.d.op == CC_OP_CONVT ? src.u : p.u);
-    p.tile_n[cols] = pick[i];
+    p.tile_n[cols] = best_ms[1][i] < best_ms[0][i] ? cands[1] : cands[0];
   }
   return CC_OK;
 }

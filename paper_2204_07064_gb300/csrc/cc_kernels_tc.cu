@@ -72,7 +72,7 @@ constexpr int kBM = 128;
 // SM, whose epilogues overlap each other's main loops and other chains'
 // kernels).  Split layers run 4 stages with a receive buffer; fused units 4
 // or 2 stages with the second operand; 256-column tiles 4 stages.
-template <int BN, int STAGES, bool FUSE, int EW, bool SPLIT = false>
+template <int BN, int STAGES, bool FUSE, int EW, bool SPLIT = false, int MT = 1>
 struct TcLayout {
   static constexpr int kThreads = 64 + 32 * EW;
   static constexpr int kStages = STAGES;
@@ -84,7 +84,9 @@ struct TcLayout {
   // the mirror row's offset (low-precision views); the caller-buffer offset
   static constexpr int kCols = BN * (4 * 4 + 4 * 4 + 2 * 4 + 8);
   static constexpr int kTurn = EW * 32 * 8 * 4;  // per epilogue warp: 32 rows x 8 columns of FP32
-  static constexpr int kB2 = FUSE ? 2 * BN * 128 : 0;  // fused unit: BN x 128 channels, 2 K slices
+  // fused unit: the 1x1 conv's operand, BN columns x 128 * MT channels (2 * MT
+  // K slices; MT > 1: the unit's channels span MT M tiles of a cluster)
+  static constexpr int kB2 = FUSE ? 2 * MT * BN * 128 : 0;
   static constexpr int kBars2 = FUSE ? 16 : 0;          // b2ready, tfull2
   // split-K receive buffer: the other CTAs' partials of this CTA's columns
   // ([ksplit-1][BN/ksplit][128] FP32: at most 3 x 32 or 1 x 64 columns)
@@ -103,12 +105,12 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi, bool bf16) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-template <int BN, int STAGES, bool FUSE, int EW, bool SPLIT>
-__global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThreads,
-                                  TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kMinBlocks)
+template <int BN, int STAGES, bool FUSE, int EW, bool SPLIT, int MT>
+__global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kThreads,
+                                  TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kMinBlocks)
     k_conv_tc(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmB,
               const TcArgs a) {
-  using L = TcLayout<BN, STAGES, FUSE, EW, SPLIT>;
+  using L = TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>;
   constexpr int kEpi = 32 * EW;  // epilogue threads
   constexpr int kParts = EW / 4;  // epilogue warps per TMEM lane quarter
   constexpr int kStages = L::kStages;
@@ -163,6 +165,10 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tbase;
+  // a cluster-fused unit writes into its peers' shared memory: every thread
+  // arrives here, and each waits on this phase (every CTA of the cluster has
+  // started) before its part in the operand exchange
+  if (FUSE && MT > 1) cluster_arrive();
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
     }
     if (FUSE && ok) {
       // fused unit: the 1x1 conv's weight slices through the same stages
-      const uint8_t* a2tile = static_cast<const uint8_t*>(a.A2_tiled);
+      const uint8_t* a2tile = static_cast<const uint8_t*>(a.A2_tiled) + (size_t)blockIdx.y * a.k2 * L::kA;
       for (int j = 0; j < a.k2; ++j) {
         const int i = nks + j;
         const int st = i % kStages;
@@ -295,13 +301,20 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
       drained = mbar_wait(full + i % kStages, (i / kStages) & 1, a.wait_ns) && drained;
     if ((!ok || !drained) && lane == 0) atomicOr(a.err, 1);
     if (KS > 1) cluster_sync();  // the epilogue's partial exchange
+    if (FUSE && MT > 1) {
+      // the first epilogue's operand exchange: this warp takes no part but
+      // must arrive (every thread of the cluster does)
+      cluster_wait();
+      cluster_arrive();
+      cluster_wait();
+    }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     pdl_wait();
     pdl_release();
+    const uint32_t idesc = idesc_f16(kBM, BN, a.in.dtype == kDtBF16);
+    bool ok = true;
     if (lane == 0) {
-      const uint32_t idesc = idesc_f16(kBM, BN, a.in.dtype == kDtBF16);
-      bool ok = true;
       for (int i = 0; i < ke - kb; ++i) {
         const int st = i % kStages;
         const uint32_t ph = (i / kStages) & 1;
@@ -318,33 +331,41 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
         mma_commit(empty + st);
       }
       mma_commit(tfull);
-      if (FUSE) {
-        // fused unit: wait for the first epilogue's operand, then the 1x1 conv
-        // into the second accumulator (TMEM columns BN .. 2*BN-1)
-        ok = ok && mbar_wait(b2ready, 0, a.wait_ns);
-        tc_fence_after();
-        const int nks = ke - kb;
-        for (int j = 0; ok && j < a.k2; ++j) {
-          const int i = nks + j;
-          const int st = i % kStages;
-          const uint32_t ph = (i / kStages) & 1;
-          if (!mbar_wait(full + st, ph, a.wait_ns)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t sa = smem_u32(sA + st * L::kA), sb = smem_u32(sB2 + j * BN * 128);
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            mma_f16(tmem + BN, sw128_kmajor_desc(sa + k * 32), sw128_kmajor_desc(sb + k * 32), idesc,
-                    (j | k) != 0);
-          mma_commit(empty + st);
-        }
-        mma_commit(tfull2);
-      }
-      if (!ok) atomicOr(a.err, 4);
     }
     __syncwarp();
+    // the operand exchange of a cluster-fused unit: arrive before waiting for
+    // the operand (the epilogues' barrier needs every thread of the cluster)
+    if (FUSE && MT > 1) {
+      cluster_wait();
+      cluster_arrive();
+    }
+    if (FUSE && lane == 0) {
+      // fused unit: wait for the first epilogue's operand, then the 1x1 conv
+      // into the second accumulator (TMEM columns BN .. 2*BN-1)
+      ok = ok && mbar_wait(b2ready, 0, a.wait_ns);
+      tc_fence_after();
+      const int nks = ke - kb;
+      for (int j = 0; ok && j < a.k2; ++j) {
+        const int i = nks + j;
+        const int st = i % kStages;
+        const uint32_t ph = (i / kStages) & 1;
+        if (!mbar_wait(full + st, ph, a.wait_ns)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(sA + st * L::kA), sb = smem_u32(sB2 + j * BN * 128);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_f16(tmem + BN, sw128_kmajor_desc(sa + k * 32), sw128_kmajor_desc(sb + k * 32), idesc,
+                  (j | k) != 0);
+        mma_commit(empty + st);
+      }
+      mma_commit(tfull2);
+    }
+    if (lane == 0 && !ok) atomicOr(a.err, 4);
+    __syncwarp();
+    if (FUSE && MT > 1) cluster_wait();
     if (KS > 1) cluster_sync();  // the epilogue's partial exchange
   } else {
     // ---------------------------------------------------------------- epilogue
@@ -474,6 +495,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
       const int32_t cm = m;  // channel = accumulator row (phases == 1)
       uint8_t* const b2row = sB2 + (cm >> 6) * (BN * 128) + (cm & 7) * 2;
       const int chunk1 = (cm & 63) >> 3;
+      if (MT > 1) cluster_wait();  // every peer has started
       if (all_ok)
 #pragma unroll 1
         for (int g = half; g < BN / 8; g += kParts) {
@@ -488,11 +510,30 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
               const uint16_t h = lp_bf16 ? __bfloat16_as_ushort(__float2bfloat16_rn(y))
                                          : __half_as_ushort(__float2half_rn(y));
               const int c = 8 * g + k;
-              *reinterpret_cast<uint16_t*>(b2row + c * 128 + ((chunk1 ^ (c & 7)) << 4)) = h;
+              uint8_t* const dst = b2row + c * 128 + ((chunk1 ^ (c & 7)) << 4);
+              if (MT == 1) {
+                *reinterpret_cast<uint16_t*>(dst) = h;
+              } else {
+                // every CTA of the cluster multiplies the whole intermediate
+                const uint32_t sa = smem_u32(dst);
+#pragma unroll
+                for (int q = 0; q < MT; ++q) dsmem_st_u16(dsmem_map(sa, (uint32_t)q), h);
+              }
             }
         }
-      fence_proxy_async_smem();  // the operand is read by the tensor cores (async proxy)
-      asm volatile("bar.sync 1, %0;" ::"n"(kEpi) : "memory");
+      // the operand is read by the tensor cores (async proxy)
+      if (MT > 1)
+        fence_proxy_async_cluster();
+      else
+        fence_proxy_async_smem();
+      if (MT > 1) {
+        // every CTA's channels are in every CTA's operand after this
+        cluster_arrive();
+        cluster_wait();
+        fence_proxy_async_smem();
+      } else {
+        asm volatile("bar.sync 1, %0;" ::"n"(kEpi) : "memory");
+      }
       if (t == 0) mbar_arrive(b2ready);
       const bool waited2 = mbar_wait(tfull2, 0, a.wait_ns);
       uint32_t ok2;
@@ -644,13 +685,14 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT>::kThread
   if (warp == 1) tmem_dealloc(tmem, L::kTmemCols);
 }
 
-template <int BN, int STAGES, bool FUSE, int EW, bool SPLIT = false>
+template <int BN, int STAGES, bool FUSE, int EW, bool SPLIT = false, int MT = 1>
 cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs& a, int ks, cudaStream_t st) {
   static bool configured = false;
-  using L = TcLayout<BN, STAGES, FUSE, EW, SPLIT>;
+  using L = TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>;
   constexpr int bytes = L::kBytes;
+  static_assert(bytes <= 232448, "shared memory per CTA");
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<BN, STAGES, FUSE, EW, SPLIT>,
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<BN, STAGES, FUSE, EW, SPLIT, MT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
     configured = true;
@@ -668,11 +710,11 @@ cudaError_t launch_bn(const CUtensorMap& ta, const CUtensorMap& tb, const TcArgs
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   attr[1].id = cudaLaunchAttributeClusterDimension;
   attr[1].val.clusterDim.x = 1;
-  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.y = (unsigned)MT;
   attr[1].val.clusterDim.z = (unsigned)ks;
   cfg.attrs = attr;
-  cfg.numAttrs = ks > 1 ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, k_conv_tc<BN, STAGES, FUSE, EW, SPLIT>, ta, tb, a);
+  cfg.numAttrs = (ks > 1 || MT > 1) ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, k_conv_tc<BN, STAGES, FUSE, EW, SPLIT, MT>, ta, tb, a);
 }
 
 }  // namespace
@@ -689,8 +731,14 @@ cudaError_t launch_conv_tc(const void* tmap_t, const void* tmap_b, const TcArgs&
   const CUtensorMap& tb = *reinterpret_cast<const CUtensorMap*>(tmap_b);
   const int ks = a.ksplit > 1 ? a.ksplit : 1;
   if (a.k2 > 0) {
-    // fused residual unit: 128-column tiles, no split, one M tile (M <= 128)
-    if (ks != 1 || a.M > kBM || a.k2 > 2) return cudaErrorInvalidValue;
+    // fused residual unit: 128-column tiles, no split; one M tile (M <= 128),
+    // or two as a cluster exchanging the intermediate (M <= 256, one wave)
+    if (ks != 1) return cudaErrorInvalidValue;
+    if (a.M > kBM) {
+      if (a.M > 2 * kBM || a.k2 > 4 || !a.deep_ok) return cudaErrorInvalidValue;
+      return launch_bn<128, 4, true, 16, false, 2>(ta, tb, a, 1, st);
+    }
+    if (a.k2 > 2) return cudaErrorInvalidValue;
     if (a.deep_ok && (N + 127) / 128 <= 148) return launch_bn<128, 4, true, 16>(ta, tb, a, 1, st);
     return launch_bn<128, 2, true, 8>(ta, tb, a, 1, st);
   }

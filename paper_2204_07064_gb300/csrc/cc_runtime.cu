@@ -232,9 +232,13 @@ static void plan_siblings(Model& m) {
 
 // Residual units on tensor cores: a stride-1 conv whose only consumer is a
 // 1x1 conv with a fused residual (and no history) run as one launch; the
-// intermediate never leaves the chip.  Both must fit one 128-row tile.
+// intermediate never leaves the chip.  Units of up to 128 channels fit one
+// 128-row tile; units of up to 256 channels run as clusters of two M tiles
+// that exchange their halves of the intermediate in distributed shared
+// memory (one CTA per SM, so only in models of at most 256 streams, whose
+// launches fit one wave).  A model built without unit fusion runs the same
+// layers unsplit, so that both forms sum in the same order.
 static void plan_units(Model& m) {
-  if (!m.fuse_units) return;
   const int n = (int)m.nodes.size();
   for (int i = 0; i < n; ++i) {
     NodePlan& p = m.nodes[i];
@@ -246,7 +250,14 @@ static void plan_units(Model& m) {
     if (q.d.op != CC_OP_CONV || q.engine != 1 || q.d.kernel != 1 || q.d.stride != 1 || q.hist_need != 0 ||
         q.fused_add < 0 || q.unit_fused)
       continue;
-    if (p.M > 128 || q.M > 128 || q.d.c_in != p.d.c_out || q.d.c_out != p.d.c_out || q.Kt > 128) continue;
+    if (q.d.c_in != p.d.c_out || q.d.c_out != p.d.c_out) continue;
+    const bool wide = p.M > 128 || q.M > 128 || q.Kt > 128;
+    if (p.M > 256 || q.M > 256 || q.Kt > 256) continue;
+    if (wide && m.max_streams > 256) continue;
+    if (!m.fuse_units) {
+      if (wide) p.no_split = q.no_split = true;
+      continue;
+    }
     p.unit_next = qi;
     q.unit_fused = true;
   }
@@ -259,7 +270,7 @@ static void plan_units(Model& m) {
 static void plan_ksplit(Model& m) {
   for (auto& p : m.nodes) {
     p.ksplit = 1;
-    if (p.engine != 1 || p.unit_next >= 0 || p.unit_fused) continue;
+    if (p.engine != 1 || p.unit_next >= 0 || p.unit_fused || p.no_split) continue;
     if (p.group_leader >= 0 && p.group_leader != (int)(&p - m.nodes.data())) continue;
     const int nk = p.Kt / 64, mt = p.Mpad / 128;
     const int64_t cols =

@@ -59,6 +59,7 @@ struct NodePlan {
   std::vector<int> group;            // (leader) members, leader first
   int32_t group_taps = 0, group_hist = 0;  // (leader) merged window
   bool unit_fused = false;  // (1x1 conv) computed by its producer's fused launch
+  bool no_split = false;    // a unit the model could fuse but runs unfused: unsplit K, as if fused
   std::map<int64_t, int32_t> tile_n;  // autotuned N tile by launch width (columns), 0: heuristic
 };
 

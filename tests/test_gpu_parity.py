@@ -323,17 +323,21 @@ def test_lowp_window_boxes_match_gathers(cclib, cuda):
 
 @pytest.mark.parametrize("count,dtype", [(256, "bf16"), (250, "bf16"), (250, "f16")])
 def test_fused_residual_units_equal_unfused(cclib, cuda, count, dtype):
-    """A residual unit (k=3 conv -> 1x1 conv + skip) with at most 128 channels
-    runs as one tensor-core launch, its intermediate rounded to BF16 in
-    shared memory exactly as the unfused path rounds it into its ring: the two
-    give identical outputs.  One stream is also checked against the oracle."""
+    """A residual unit (k=3 conv -> 1x1 conv + skip) runs as one tensor-core
+    launch, its intermediate rounded to BF16 in shared memory exactly as the
+    unfused path rounds it into its ring: up to 128 channels in one CTA, the
+    decoder's 256-channel stage-1 units as clusters of two CTAs that exchange
+    their halves of the intermediate in distributed shared memory (the
+    unfused model then runs those layers unsplit, so both sum in one order).
+    The two give identical outputs with fewer launches fused.  One stream is
+    also checked against the oracle."""
     import torch
 
     dec, p = _decoder(12)
     steps = 4
     seeds = W.stream_seeds(21, count)
     z = np.random.default_rng(6).standard_normal((steps, count, 1, 128))
-    outs = []
+    outs, launches = [], []
     for fuse in (True, False):
         model = api.Model(dec, p, dtype=dtype, max_streams=count, max_steps_per_call=1, fuse_units=fuse)
         streams = [model.stream(seed=s) for s in seeds]
@@ -344,8 +348,12 @@ def test_fused_residual_units_equal_unfused(cclib, cuda, count, dtype):
             o[:, t * 2048:(t + 1) * 2048] = y[:, :, 0].cpu().numpy()
         assert model.device_status() == 0
         outs.append(o)
+        launches.append(model.chain_launches)
         model.close()
     np.testing.assert_array_equal(outs[0], outs[1])
+    # the three residual units of each of stages 1, 2 and 3 are one launch each
+    # fused (stage 0, 512 channels, stays unfused)
+    assert launches[0] == launches[1] - 9, launches
     k = count // 3
     ref = M.run_causal(dec, p, z[:, k, 0, :], seed=seeds[k])[:, 0]
     _assert_lowp(outs[0][k], ref, f"{dtype} fused units, stream {k} of {count}")

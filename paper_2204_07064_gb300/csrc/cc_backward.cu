@@ -399,10 +399,16 @@ __global__ void __launch_bounds__(256) k_bwd_data(BwdConv a) {
       __syncthreads();
     }
     const float* wt = a.Wt + (int64_t)tap * a.cout * a.cin;
+    // gy: a warp reads 32 consecutive channels of one row (coalesced) and
+    // stores them down a column of Gs; W: a warp reads along input channels
+    for (int e = threadIdx.x; e < kBC * kBT; e += 256) {
+      const int q = e / kBC, c = e - q * kBC;
+      const int32_t n = n0 + c;
+      Gs[c][q] = (gp[q] && n < a.cout) ? gp[q][n] : 0.f;
+    }
     for (int e = threadIdx.x; e < kBC * kBT; e += 256) {
       const int c = e / kBT, q = e - c * kBT;
       const int32_t n = n0 + c;
-      Gs[c][q] = (gp[q] && n < a.cout) ? gp[q][n] : 0.f;
       Ws[c][q] = (n < a.cout && m0 + q < a.cin) ? wt[(int64_t)n * a.cin + m0 + q] : 0.f;
     }
     __syncthreads();
@@ -506,7 +512,11 @@ __global__ void __launch_bounds__(256) k_bwd_data_narrow(BwdConv a) {
     const int32_t s = (int32_t)(row / span), i = (int32_t)(row - (int64_t)s * span) - a.hist;
     const int64_t t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
     float acc = 0.f;
-    for (int32_t tap = 0; tap < a.K; ++tap) {
+    // a stride-S convolution of dilation 1 meets this frame with taps
+    // k = (i + hist) mod S + S*j only
+    const bool res = !convt && a.S > 1 && a.dil == 1;
+    const int32_t tap0 = res ? (i + a.hist) % a.S : 0, tstep = res ? a.S : 1;
+    for (int32_t tap = tap0; tap < a.K; tap += tstep) {
       const float* g = nullptr;
       if (!convt) {
         const int32_t jj2 = i + a.hist - tap * a.dil;
@@ -522,6 +532,109 @@ __global__ void __launch_bounds__(256) k_bwd_data_narrow(BwdConv a) {
     const int64_t t = chunk_t0(a.b, s, a.u_in, a.steps) + i;
     adj_row(a.adj, a.adj_slot_bytes, a.b.slots[s], a.gx, t)[m] += acc * deriv_at(val_row(a.b, s, a.x, t), a.x, m);
   }
+}
+
+// dL/dW (and dL/db) of a narrow layer whose taps hold at most NW weights
+// (cout x cin; both PQMF filterbanks have 16): blocks over (tap, split of the
+// columns), each thread accumulating every weight of the tap over its
+// columns, so a column's rows are found once.  A block's sums are reduced in
+// a fixed order; with several splits the tap's last block to arrive adds the
+// splits' partials in split order.
+template <int NW>
+__global__ void __launch_bounds__(256) k_bwd_weight_tap(BwdConv a) {
+  __shared__ float red[2][8][NW + 1];
+  __shared__ float tot[2][NW];
+  __shared__ bool last;
+  const int32_t kk = blockIdx.x, split = blockIdx.y;
+  const bool convt = a.op == CC_OP_CONVT;
+  const int32_t ph = convt ? kk % a.S : 0, jj = convt ? kk / a.S : 0;
+  const int32_t ncol = convt ? a.n_in : a.n_out;
+  const int64_t total = (int64_t)a.b.count * ncol;
+  const int64_t c_begin = (int64_t)split * a.per_split;
+  const int64_t c_end = c_begin + a.per_split < total ? c_begin + a.per_split : total;
+  const int32_t nw = a.cout * a.cin;
+  const bool bias = a.db && kk == 0;
+  float acc[NW], bacc[NW];
+#pragma unroll
+  for (int j = 0; j < NW; ++j) acc[j] = bacc[j] = 0.f;
+  for (int64_t col = c_begin + threadIdx.x; col < c_end; col += blockDim.x) {
+    const int32_t s = (int32_t)(col / ncol), q = (int32_t)(col - (int64_t)s * ncol);
+    const int64_t t0_in = chunk_t0(a.b, s, a.u_in, a.steps), t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
+    const float* g = gy_row(a, s, convt ? (int64_t)q * a.S + ph : q, t0_out);
+    const int64_t t = convt ? t0_in + q - jj : t0_in + (int64_t)q * a.S + (int64_t)kk * a.dil - a.hist;
+    const char* xr = val_row(a.b, s, a.x, t);
+#pragma unroll
+    for (int j = 0; j < NW; ++j)
+      if (j < nw) acc[j] = fmaf(g[j / a.cin], val_at(xr, a.x, j % a.cin), acc[j]);
+    if (bias) {
+      if (!convt) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j)
+          if (j < a.cout) bacc[j] += g[j];
+      } else {
+        for (int32_t p = 0; p < a.S; ++p) {
+          const float* gp = gy_row(a, s, (int64_t)q * a.S + p, t0_out);
+#pragma unroll
+          for (int j = 0; j < NW; ++j)
+            if (j < a.cout) bacc[j] += gp[j];
+        }
+      }
+    }
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    float x = acc[j], y = bacc[j];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      x += __shfl_xor_sync(0xffffffffu, x, d);
+      y += __shfl_xor_sync(0xffffffffu, y, d);
+    }
+    if (lane == 0) {
+      red[0][w][j] = x;
+      red[1][w][j] = y;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < NW) {
+    float sw = 0.f, sb = 0.f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      sw += red[0][k][threadIdx.x];
+      sb += red[1][k][threadIdx.x];
+    }
+    tot[0][threadIdx.x] = sw;
+    tot[1][threadIdx.x] = sb;
+  }
+  __syncthreads();
+  const int j = threadIdx.x;
+  if (a.splits > 1) {
+    if (j < NW) {
+      a.part[((int64_t)kk * a.splits + split) * NW + j] = tot[0][j];
+      if (bias) a.bpart[(int64_t)split * NW + j] = tot[1][j];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const uint32_t prev = atomicAdd(a.counters + kk, 1u);
+      last = prev == (uint32_t)a.splits - 1;
+      if (last) a.counters[kk] = 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (j < NW) {
+      float sw = 0.f, sb = 0.f;
+      for (int32_t q = 0; q < a.splits; ++q) {
+        sw += __ldcg(a.part + ((int64_t)kk * a.splits + q) * NW + j);
+        if (bias) sb += __ldcg(a.bpart + (int64_t)q * NW + j);
+      }
+      tot[0][j] = sw;
+      tot[1][j] = sb;
+    }
+  }
+  // tap-major [K][cout][cin]: weight j = (n, m) of tap kk
+  if (j < nw && j < NW) a.dW[(int64_t)kk * nw + j] += tot[0][j];
+  if (bias && j < a.cout && j < NW) a.db[j] += tot[1][j];
 }
 
 struct BwdMerge {
@@ -1050,7 +1163,16 @@ cc_status cc_backward_chunk(cc_grads* g, cc_stream* const* streams, int32_t coun
       }
       // dL/dW (and dL/db)
       BW_CUDA(t_begin(CC_BWD_WEIGHT, i));
-      if (narrow) {
+      if (narrow && a.cout * a.cin <= 64) {
+        // blocks over (tap, split of the columns)
+        const int64_t cols = (int64_t)count * (d.op == CC_OP_CONVT ? a.n_in : a.n_out);
+        a.splits = pick_splits(a.K, cols, 256, 1, &a.per_split);
+        const dim3 grid((unsigned)a.K, (unsigned)a.splits);
+        if (a.cout * a.cin <= 16)
+          k_bwd_weight_tap<16><<<grid, 256, 0, st>>>(a);
+        else
+          k_bwd_weight_tap<64><<<grid, 256, 0, st>>>(a);
+      } else if (narrow) {
         k_bwd_weight_narrow<<<(unsigned)((int64_t)a.cout * a.cin * a.K), 256, 0, st>>>(a);
       } else {
         // output-channel x input-channel x tap tiles, the (stream, frame)

@@ -31,7 +31,10 @@
  *     thread-local message is available from cc_last_error().
  *   - A stream must not be processed concurrently with itself; different
  *     streams may be processed concurrently on different CUDA streams only if
- *     they are not in the same batch call.
+ *     they are not in the same batch call.  Calls on one model come from one
+ *     host thread at a time (its host-side plan, staging and graph caches are
+ *     not locked); the serving scheduler (cc_server_*) is the exception and
+ *     documents its own rules.
  */
 #ifndef CACHEDCONV_H
 #define CACHEDCONV_H
@@ -254,11 +257,17 @@ cc_status cc_process_batch(cc_model* model, cc_stream* const* streams, const flo
                            void* cuda_stream);
 
 /* The fast form of cc_process_batch for equal-length buffers laid out with a
- * fixed stride (no staging, so it can be captured in a CUDA graph):
+ * fixed stride (with device buffers there is no staging, so the call can be
+ * captured in a CUDA graph):
  * in:  count buffers of n_in frames, stream i at in + i*in_stride (floats);
  * out: count buffers of n_out frames, stream i at out + i*out_stride.
  * Whole-step lengths only (cc_stream_process outside FIFO mode); streams in
- * FIFO mode are refused (STATE). */
+ * FIFO mode are refused (STATE).  With host buffers in and out, the buffers go
+ * through device staging of the CUDA stream's own, and the launch chain
+ * between the copies is captured into a CUDA graph on its first use for that
+ * number of streams and steps and replayed after (the first such call takes
+ * the capture's time; a later autotuning, or staging that has to grow,
+ * captures again). */
 cc_status cc_process_batch_strided(cc_model* model, cc_stream* const* streams, int32_t count,
                                    const float* in, int64_t in_stride, int64_t n_in, float* out,
                                    int64_t out_stride, int64_t n_out, void* cuda_stream);

@@ -1055,10 +1055,11 @@ cc_status cc_backward_chunk(cc_grads* g, cc_stream* const* streams, int32_t coun
   // 1. recompute this chunk's forward from the restored state; its output is
   //    not needed (grad_x doubles as scratch only if the shapes agree, so use
   //    the model's staging buffers)
-  cc_status s = m->ensure_staging(count);
+  cc::Model::Staging* sg = nullptr;
+  cc_status s = m->ensure_staging(count, st, &sg);
   if (s) return s;
   BW_CUDA(t_begin(CC_BWD_RECOMPUTE, -1));
-  s = m->run_chain(b, x, x_stride, m->stage_out, (int64_t)steps * m->nodes.back().u * m->nodes.back().d.c_out,
+  s = m->run_chain(b, x, x_stride, sg->out, (int64_t)steps * m->nodes.back().u * m->nodes.back().d.c_out,
                    steps, st);
   if (s) return s;
   BW_CUDA(t_end());

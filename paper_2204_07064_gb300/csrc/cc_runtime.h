@@ -99,10 +99,26 @@ struct Model {
   };
   std::map<cudaStream_t, SlotList> slot_lists;
   int32_t* batch_slots = nullptr;  // the default CUDA stream's list (allocated at creation)
-  // host I/O staging
-  float* stage_in = nullptr;
-  float* stage_out = nullptr;
-  size_t stage_in_bytes = 0, stage_out_bytes = 0;
+  // host I/O staging, one pair of device buffers per CUDA stream (calls on
+  // different CUDA streams may overlap on the GPU)
+  struct Staging {
+    float* in = nullptr;
+    float* out = nullptr;
+    size_t in_bytes = 0, out_bytes = 0;
+  };
+  std::map<cudaStream_t, Staging> stagings;
+  // launch chains of host-buffer calls, captured once per (streams, steps,
+  // device slot list, staging) and replayed: they read and write only the
+  // staging buffers (dropped when a staging grows or the tile shapes change)
+  struct ChainGraph {
+    int32_t count, steps;
+    const int32_t* d_slots;
+    const float *in, *out;
+    cudaGraphExec_t exec;
+  };
+  std::vector<ChainGraph> chain_graphs;
+  cudaStream_t capture_stream = nullptr;
+  void drop_chain_graphs(const float* in = nullptr, const float* out = nullptr);
   // ragged-batch / FIFO staging: one row of whole steps per stream
   float* rag_in = nullptr;
   float* rag_out = nullptr;
@@ -136,7 +152,7 @@ struct Model {
                     int64_t n_in, float* out, int64_t out_stride, int64_t n_out, cudaStream_t st);
   cc_status run_chain(const Batch& b, const float* in, int64_t in_stride, float* out,
                       int64_t out_stride, int32_t steps, cudaStream_t st);
-  cc_status ensure_staging(int32_t count);
+  cc_status ensure_staging(int32_t count, cudaStream_t st, Staging** sg);
   cudaError_t take_event(cudaEvent_t* ev);
 };
 

@@ -204,6 +204,49 @@ def test_host_buffers_match_device_buffers(cclib, cuda):
     np.testing.assert_array_equal(yh, yd)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_host_buffer_batches_replay_one_graph(cclib, cuda, dtype):
+    """Batched calls with host buffers run their launch chain from a CUDA graph
+    captured on the first call (for that number of streams and steps) and
+    replayed after; two groups of streams on two CUDA streams use staging of
+    their own.  Every call equals, bit for bit, the same streams driven with
+    device buffers."""
+    import torch
+
+    dec = W.rave_decoder(latent=16, capacity=16 if dtype == "f32" else 64, ratios=(2, 2), dilations=(1, 3),
+                         bands=4, pqmf_taps=16)
+    p = W.init_params(dec, 3)
+    _, g, _, _ = pqmf.design(4, 16)
+    p[W.pqmf_node_index(dec)] = (pqmf.synthesis_weights(g), None)
+    steps, n = 6, 3
+    z = np.random.default_rng(2).standard_normal((steps, 2 * n, 1, 16)).astype(np.float32)
+    cs = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = {}
+    for host in (True, False):
+        model = api.Model(dec, p, dtype=dtype, max_streams=2 * n, max_steps_per_call=1)
+        groups = [[model.stream(seed=10 * k + i) for i in range(n)] for k in range(2)]
+        ops = model.io["out_per_step"]
+        o = np.zeros((2 * n, steps * ops), np.float32)
+        for t in range(steps):
+            for k in range(2):
+                zk = z[t, k * n:(k + 1) * n]
+                if host:
+                    y = np.zeros((n, ops, 1), np.float32)
+                    model.process_batch(groups[k], np.ascontiguousarray(zk), y, cuda_stream=cs[k])
+                    cs[k].synchronize()
+                    o[k * n:(k + 1) * n, t * ops:(t + 1) * ops] = y[:, :, 0]
+                else:
+                    with torch.cuda.stream(cs[k]):
+                        y = torch.empty((n, ops, 1), dtype=torch.float32, device=cuda)
+                        model.process_batch(groups[k], torch.tensor(zk, device=cuda), y, cuda_stream=cs[k])
+                    cs[k].synchronize()
+                    o[k * n:(k + 1) * n, t * ops:(t + 1) * ops] = y[:, :, 0].cpu().numpy()
+        assert model.device_status() == 0
+        outs[host] = o
+        model.close()
+    np.testing.assert_array_equal(outs[True], outs[False])
+
+
 def test_errors(cclib, cuda):
     import torch
 

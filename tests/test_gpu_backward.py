@@ -91,30 +91,31 @@ def wide_strided_stack(seed=0):
     """Layers wide enough for the tiled backward kernels, with the strides of
     the encoder and decoder: a stride-4 conv (K=8) and a stride-2 conv (K=5,
     so residues meet different tap counts), a stride-4 transposed conv, a
-    dilated conv and a residual add."""
+    dilated conv (dilation 5) and a residual add."""
     n = W._node
     nodes = [W.input_node(32),
              n("conv", [0], 32, 64, k=8, stride=4, pad_left=2, pad_right=2, act_in=None, name="down4"),
              n("conv", [1], 64, 96, k=5, stride=2, pad_left=2, pad_right=2, act_in="leaky", name="down2"),
              n("convt", [2], 96, 64, k=8, stride=4, crop=2, act_in="leaky", name="up4"),
-             n("conv", [3], 64, 64, k=3, dilation=3, pad_left=3, pad_right=3, act_in="leaky", name="dil"),
+             n("conv", [3], 64, 64, k=3, dilation=5, pad_left=5, pad_right=5, act_in="leaky", name="dil"),
              n("add", [3, 4], 64, 64, bias=False, name="add"),
              n("conv", [5], 64, 48, k=3, pad_left=1, pad_right=1, act_in="leaky", name="out")]
     return nodes, W.init_params(nodes, seed)
 
 
-def test_backward_wide_strided_layers(cclib, cuda):
+@pytest.mark.parametrize("chunk", [1, 3])
+def test_backward_wide_strided_layers(cclib, cuda, chunk):
     """FP32 parity of the tiled dW / dX kernels (split reductions, residue-
-    ordered rows of strided convolutions, phases of a transposed one) against
-    the oracle's gradient, over chunks of 3 steps with the cache adjoint
-    carried."""
+    ordered rows of strided convolutions, phases of a transposed one, a
+    dilation above a chunk's output frames at 1-step chunks) against the
+    oracle's gradient, the cache adjoint carried from chunk to chunk."""
     import torch
 
     nodes, p = wide_strided_stack(3)
     info = M.analyze(nodes)
     xs = [W.signal(50 + k, 12 * info["in_per_step"], 32) for k in range(3)]
     seeds = [1, 2, 3]
-    y, gx, grads, r, _, _ = _run(nodes, p, xs, seeds, 3, torch, cuda)
+    y, gx, grads, r, _, _ = _run(nodes, p, xs, seeds, chunk, torch, cuda)
     gw_ref = {}
     for k in range(3):
         _, gxr, gwr = AD.gradients(nodes, p, xs[k], r[k], seed=seeds[k])

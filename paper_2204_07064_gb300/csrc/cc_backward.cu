@@ -213,8 +213,8 @@ __device__ __forceinline__ bool finish_tile(const BwdConv& a, float (&acc)[4][4]
 __global__ void __launch_bounds__(256) k_bwd_weight(BwdConv a) {
   __shared__ __align__(16) float Gs[kBC][kBT + 4];
   __shared__ __align__(16) float Xs[kBC][kBT + 4];
-  __shared__ const float* gp[kBC];
-  __shared__ const char* xp[kBC];
+  __shared__ const float* gp[2][kBC];  // row pointers of a chunk's columns, two chunks in flight
+  __shared__ const char* xp[2][kBC];
   __shared__ bool blast;
   const int32_t n0 = blockIdx.x * kBT, m0 = blockIdx.y * kBT;
   const int32_t kk = blockIdx.z / a.splits, split = blockIdx.z - kk * a.splits;
@@ -229,7 +229,10 @@ __global__ void __launch_bounds__(256) k_bwd_weight(BwdConv a) {
   const int32_t nph = convt ? a.S : 1;
   float acc[4][4] = {};
   float bacc = 0.f;
-  for (int64_t c0 = c_begin; c0 < c_end; c0 += kBC) {
+  // Software pipeline over chunks of kBC columns: the row pointers of chunk
+  // i + 2 are computed, and chunk i + 1's values are loaded into registers,
+  // while chunk i is multiplied out of shared memory.
+  auto set_ptrs = [&](int64_t c0, int b) {
     if (threadIdx.x < kBC) {
       const int64_t col = c0 + threadIdx.x;
       const float* g = nullptr;
@@ -240,21 +243,41 @@ __global__ void __launch_bounds__(256) k_bwd_weight(BwdConv a) {
         g = gy_row(a, s, convt ? (int64_t)o * a.S + ph : o, t0_out);
         xr = val_row(a.b, s, a.x, convt ? t0_in + o - jj : t0_in + (int64_t)o * a.S + (int64_t)kk * a.dil - a.hist);
       }
-      gp[threadIdx.x] = g;
-      xp[threadIdx.x] = xr;
+      gp[b][threadIdx.x] = g;
+      xp[b][threadIdx.x] = xr;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kBC * kBT; e += 256) {
-      const int c = e / kBT, q = e - c * kBT;
+  };
+  constexpr int kPer = kBC * kBT / 256;  // elements per thread per chunk
+  float rg[kPer], rx[kPer];
+  auto load = [&](int b) {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int e = threadIdx.x + 256 * r, c = e / kBT, q = e - c * kBT;
       float g = 0.f, x = 0.f;
-      if (gp[c]) {
-        if (n0 + q < a.cout) g = gp[c][n0 + q];
-        if (m0 + q < a.cin) x = val_at(xp[c], a.x, m0 + q);
+      const float* gr = gp[b][c];
+      if (gr) {
+        if (n0 + q < a.cout) g = gr[n0 + q];
+        if (m0 + q < a.cin) x = val_at(xp[b][c], a.x, m0 + q);
       }
-      Gs[c][q] = g;
-      Xs[c][q] = x;
+      rg[r] = g;
+      rx[r] = x;
     }
-    __syncthreads();
+  };
+  set_ptrs(c_begin, 0);
+  set_ptrs(c_begin + kBC, 1);
+  __syncthreads();
+  load(0);
+  int cur = 0;
+  for (int64_t c0 = c_begin; c0 < c_end; c0 += kBC, cur ^= 1) {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int e = threadIdx.x + 256 * r, c = e / kBT, q = e - c * kBT;
+      Gs[c][q] = rg[r];
+      Xs[c][q] = rx[r];
+    }
+    __syncthreads();  // the chunk's tile is complete; chunk i + 1's pointers are visible
+    if (c0 + kBC < c_end) load(cur ^ 1);
+    set_ptrs(c0 + 2 * kBC, cur);  // (this buffer's loads were issued a chunk ago)
     if (bias && threadIdx.x < kBT)
       for (int c = 0; c < kBC; ++c) bacc += Gs[c][threadIdx.x];
 #pragma unroll 4
@@ -331,7 +354,7 @@ __global__ void __launch_bounds__(256) k_bwd_weight(BwdConv a) {
 __global__ void __launch_bounds__(256) k_bwd_data(BwdConv a) {
   __shared__ __align__(16) float Gs[kBC][kBT + 4];  // [n][row]
   __shared__ __align__(16) float Ws[kBC][kBT + 4];  // [n][m]
-  __shared__ const float* gp[kBT];
+  __shared__ const float* gp[2][kBT];  // gy row of each tile row for a step's tap, two steps in flight
   __shared__ int32_t rs[kBT];
   __shared__ int32_t ri[kBT];
   const int32_t span = a.hist + a.n_in;
@@ -374,44 +397,73 @@ __global__ void __launch_bounds__(256) k_bwd_data(BwdConv a) {
   const int64_t it_begin = (int64_t)split * a.per_split;
   const int64_t it_end = it_begin + a.per_split < steps_total ? it_begin + a.per_split : steps_total;
   float acc[4][4] = {};
-  int32_t cur_tap = -1;
-  for (int64_t it = it_begin; it < it_end; ++it) {
-    const int32_t jt = (int32_t)(it / nch), n0 = (int32_t)(it - (int64_t)jt * nch) * kBC;
-    const int32_t tap = a.res ? res + a.S * jt : jt;
-    if (tap != cur_tap) {
-      __syncthreads();
-      if (threadIdx.x < kBT) {
-        const int32_t s = rs[threadIdx.x], i = ri[threadIdx.x];
-        const float* p = nullptr;
-        if (s >= 0) {
-          const int64_t t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
-          if (!convt) {
-            const int32_t jj2 = i + a.hist - tap * a.dil;
-            if (jj2 >= 0 && jj2 % a.S == 0 && jj2 / a.S < a.n_out) p = gy_row(a, s, jj2 / a.S, t0_out);
-          } else {
-            const int32_t ph = tap % a.S, jj = tap / a.S, qq = i + jj;
-            if (qq >= 0 && qq < a.n_in) p = gy_row(a, s, (int64_t)qq * a.S + ph, t0_out);
-          }
+  // Software pipeline over the (tap, 32-channel chunk) steps: the gy rows of
+  // step i + 2's tap are found, and step i + 1's gy and W values are loaded
+  // into registers, while step i is multiplied out of shared memory.
+  auto tap_of = [&](int64_t it) -> int32_t {
+    const int32_t jt = (int32_t)(it / nch);
+    return a.res ? res + a.S * jt : jt;
+  };
+  auto set_gp = [&](int64_t it, int b) {
+    if (threadIdx.x < kBT) {
+      const int32_t s = rs[threadIdx.x], i = ri[threadIdx.x];
+      const float* p = nullptr;
+      if (s >= 0 && it < it_end) {
+        const int32_t tap = tap_of(it);
+        const int64_t t0_out = chunk_t0(a.b, s, a.u_out, a.steps);
+        if (!convt) {
+          const int32_t jj2 = i + a.hist - tap * a.dil;
+          if (jj2 >= 0 && jj2 % a.S == 0 && jj2 / a.S < a.n_out) p = gy_row(a, s, jj2 / a.S, t0_out);
+        } else {
+          const int32_t ph = tap % a.S, jj = tap / a.S, qq = i + jj;
+          if (qq >= 0 && qq < a.n_in) p = gy_row(a, s, (int64_t)qq * a.S + ph, t0_out);
         }
-        gp[threadIdx.x] = p;
       }
-      cur_tap = tap;
-      __syncthreads();
+      gp[b][threadIdx.x] = p;
     }
+  };
+  constexpr int kPer = kBC * kBT / 256;  // elements of each operand per thread per step
+  float rg[kPer], rw[kPer];
+  auto load = [&](int64_t it, int b) {
+    const int32_t tap = tap_of(it), n0 = (int32_t)(it - (int64_t)(it / nch) * nch) * kBC;
     const float* wt = a.Wt + (int64_t)tap * a.cout * a.cin;
-    // gy: a warp reads 32 consecutive channels of one row (coalesced) and
-    // stores them down a column of Gs; W: a warp reads along input channels
-    for (int e = threadIdx.x; e < kBC * kBT; e += 256) {
-      const int q = e / kBC, c = e - q * kBC;
-      const int32_t n = n0 + c;
-      Gs[c][q] = (gp[q] && n < a.cout) ? gp[q][n] : 0.f;
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      {  // gy: a warp reads 32 consecutive channels of one row (coalesced)
+        const int q = e / kBC, c = e - q * kBC;
+        const int32_t n = n0 + c;
+        const float* g = gp[b][q];
+        rg[r] = (g && n < a.cout) ? g[n] : 0.f;
+      }
+      {  // W: a warp reads along input channels
+        const int c = e / kBT, q = e - c * kBT;
+        const int32_t n = n0 + c;
+        rw[r] = (n < a.cout && m0 + q < a.cin) ? wt[(int64_t)n * a.cin + m0 + q] : 0.f;
+      }
     }
-    for (int e = threadIdx.x; e < kBC * kBT; e += 256) {
-      const int c = e / kBT, q = e - c * kBT;
-      const int32_t n = n0 + c;
-      Ws[c][q] = (n < a.cout && m0 + q < a.cin) ? wt[(int64_t)n * a.cin + m0 + q] : 0.f;
+  };
+  set_gp(it_begin, 0);
+  set_gp(it_begin + 1, 1);
+  __syncthreads();
+  if (it_begin < it_end) load(it_begin, 0);
+  int cur = 0;
+  for (int64_t it = it_begin; it < it_end; ++it, cur ^= 1) {
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const int e = threadIdx.x + 256 * r;
+      {
+        const int q = e / kBC, c = e - q * kBC;
+        Gs[c][q] = rg[r];
+      }
+      {
+        const int c = e / kBT, q = e - c * kBT;
+        Ws[c][q] = rw[r];
+      }
     }
-    __syncthreads();
+    __syncthreads();  // the step's tiles are complete; step i + 1's gy rows are visible
+    if (it + 1 < it_end) load(it + 1, cur ^ 1);
+    set_gp(it + 2, cur);  // (this buffer's loads were issued a step ago)
 #pragma unroll 4
     for (int c = 0; c < kBC; ++c) {
       const float4 g4 = *reinterpret_cast<const float4*>(&Gs[c][ty * 4]);

@@ -102,6 +102,9 @@ struct TcArgs {
   int32_t ksplit;      // split-K factor (1, 2 or 4): CTAs per cluster sharing a tile
   int32_t deep_ok;     // one-wave grids may take the deep one-CTA-per-SM pipelines (models
                        //   sized for at most 256 streams: no concurrent chains expected)
+  int32_t mdup;        // M <= 64 and the weight tiles (A and A2) repeat rows 0..63 in rows
+                       //   64..127: accumulator lanes 64..127 repeat lanes 0..63, so all
+                       //   four TMEM lane quarters have rows to store (split the columns)
   // Residual-unit fusion (k2 > 0): the tile's result, scaled, biased and
   // activated (act2) in BF16/FP16, is the B operand of a second, 1x1
   // contraction A2 [M][k2*64] (pre-tiled like A) whose result, with scale2,

@@ -25,7 +25,11 @@
 //              each lane holds 8 consecutive channels of one column, adds the
 //              aligned residual (16-byte loads) and stores every view with
 //              16-byte stores, at ring addresses from a per-column table built
-//              before the kernel waits on its predecessor
+//              before the kernel waits on its predecessor.  A layer of at most
+//              64 rows stores its weight tiles twice (rows 64..127 repeat
+//              0..63), so lane quarters 2 and 3 hold the same results and
+//              their warps store every other 32-column chunk: no epilogue
+//              warp idles on the padding rows
 // Residual-unit fusion (FUSE): a k-wide conv and the 1x1 conv that consumes
 // only it run as one launch.  The first epilogue writes the scaled, biased,
 // activated first result in BF16/FP16 straight into shared memory in the
@@ -33,7 +37,10 @@
 // (its weights streamed through the same pipeline) into a second TMEM
 // accumulator, and the second epilogue is the ordinary one.  The rounding of
 // the intermediate is the one the unfused path applies when it stores it, so
-// the results are identical.
+// the results are identical.  The unit's residual (its input, written by the
+// previous launch) is copied (cp.async) into the B stages as soon as the first
+// contraction has drained them, so the second epilogue reads it from shared
+// memory instead of waiting on L2 once per 8-column group.
 // Split-K (layers with few tiles and long K): the ksplit CTAs of a cluster
 // along z share one tile; CTA z accumulates an equal share of the K slices and
 // finishes columns [z, z+1) * BN/ksplit.  Each CTA pushes its partial sums of
@@ -372,7 +379,15 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
     const int t = threadIdx.x - 64;  // 0..255
     const int sub = warp & 3;        // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;  // which groups of 8 columns: half, half + kParts, ...
-    const int32_t m = m0 + sub * 32 + lane;  // accumulator row of this thread
+    // Repeated rows (TcArgs::mdup; not with split-K or cluster tiles): lane
+    // quarters 2 and 3 hold rows 0..63 again, and the two quarter pairs take
+    // alternate 32-column chunks (alternate kParts-group runs in the fused
+    // unit's first epilogue)
+    const bool dup = !SPLIT && MT == 1 && a.mdup != 0;
+    const int rsub = dup ? (sub & 1) : sub;  // rows 32*rsub .. +31 of the tile
+    const int rpart = dup ? (sub >> 1) : 0;
+    const int nrep = dup ? 2 : 1;
+    const int32_t m = m0 + rsub * 32 + lane;  // accumulator row of this thread
     const bool mok = m < a.M;
     const int32_t ph = (mok && a.phases > 1) ? m / a.cout : 0;  // transposed conv: phase
     const int32_t ch = mok ? m - ph * a.cout : 0;                // output channel
@@ -414,7 +429,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
     // consecutive rows 8*(l % 4) .. +7 of its warp's 32: channels ch_l .. +7
     // of phase ph_l (cout is a multiple of 8, so they share a phase).
     const int kk = lane >> 2;
-    const int32_t mrow = m0 + sub * 32 + 8 * (lane & 3);
+    const int32_t mrow = m0 + rsub * 32 + 8 * (lane & 3);
     const bool vok = mrow < a.M;
     const int32_t ph_l = (vok && phased) ? mrow / a.cout : 0;
     const int32_t ch_l = vok ? mrow - ph_l * a.cout : 0;
@@ -454,21 +469,28 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
       sk0 = ok ? ld_global_nc_v4(pa) : make_float4(0.f, 0.f, 0.f, 0.f);
       sk1 = ok ? ld_global_nc_v4(pa + 16) : make_float4(0.f, 0.f, 0.f, 0.f);
     };
+    // Fused unit: the residual tile (this tile's rows, FP32, a column per
+    // stg_rows * 4 bytes, 16-byte chunks XOR-swizzled by the column's parity)
+    // is copied into the B stages, free once the first contraction is done,
+    // while the first epilogue and the 1x1 MMAs run
+    const int stg_rows = a.M - m0 <= 64 ? 64 : 128;
+    const bool staged = FUSE && a.has_skip && BN * stg_rows * 4 <= kStages * L::kB;
+    const int cstep = 32 * nrep;  // chunk stride of this warp's column chunks
     uint32_t so_next = 0;
     int32_t sr_next = 0;
     if (a.has_skip) {
-      so_next = col_off[3 * BN + c_lo + lane];
-      sr_next = col_row[3 * BN + c_lo + lane];
+      so_next = col_off[3 * BN + c_lo + 32 * rpart + lane];
+      sr_next = col_row[3 * BN + c_lo + 32 * rpart + lane];
     }
     if (a.has_skip && a.skip_early) {
       prefetch_skip();
-      load_skip(c_lo, half, so_next, sr_next);
+      if (!staged) load_skip(c_lo + 32 * rpart, half, so_next, sr_next);
     }
     pdl_wait();
     pdl_release();
     if (a.has_skip && !a.skip_early) {
       prefetch_skip();
-      load_skip(c_lo, half, so_next, sr_next);
+      if (!staged) load_skip(c_lo + 32 * rpart, half, so_next, sr_next);
     }
     // one outcome for all epilogue threads (a reduction barrier), so the
     // named barriers stay matched
@@ -483,6 +505,19 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
         : "r"((uint32_t)waited), "n"(kEpi)
         : "memory");
     tc_fence_after();
+    if (staged && all_ok) {
+      // every MMA that read the B stages has completed (tfull)
+      const int nq = stg_rows / 4;
+      const uint32_t sdst = smem_u32(sB);
+      for (int i = t; i < BN * nq; i += kEpi) {
+        const int c = i / nq, q = i - c * nq;
+        if (n0 + c >= N) break;
+        if (m0 + 4 * q >= a.M) continue;
+        cp_async16(sdst + (uint32_t)(c * stg_rows * 4 + ((q ^ (c & 1)) << 4)),
+                   arena + (uint64_t)col_off[3 * BN + c] * 16 + (int64_t)(m0 + 4 * q) * 4);
+      }
+      cp_async_commit();
+    }
     uint32_t acc_col = 0;  // TMEM column of the stored result's accumulator
     if (FUSE) {
       // fused unit, first epilogue: the k-wide conv's result, scaled, biased,
@@ -498,7 +533,7 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
       if (MT > 1) cluster_wait();  // every peer has started
       if (all_ok)
 #pragma unroll 1
-        for (int g = half; g < BN / 8; g += kParts) {
+        for (int g = half + kParts * rpart; g < BN / 8; g += kParts * nrep) {
           uint32_t r[8];
           tmem_ld8(tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(8 * g), r);
           tmem_ld_wait();
@@ -535,6 +570,9 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
         asm volatile("bar.sync 1, %0;" ::"n"(kEpi) : "memory");
       }
       if (t == 0) mbar_arrive(b2ready);
+      // the staged residual: own copies complete here, everyone's after the
+      // barrier below
+      if (staged) cp_async_wait_all();
       const bool waited2 = mbar_wait(tfull2, 0, a.wait_ns);
       uint32_t ok2;
       asm volatile(
@@ -584,9 +622,11 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
       const bool has_skip = a.has_skip != 0;
       char* const f_base = arena + (int64_t)ch_l * 4;
       char* const l_base = arena + (int64_t)ch_l * 2;
+      const uint32_t stg_base = smem_u32(sB);
+      const int stg_q0 = (rsub * 32 + 8 * (lane & 3)) >> 2;  // this lane's first 16-byte chunk of a column
 #pragma unroll 1
-      for (int cb = c_lo; cb < c_lo + c_n; cb += 32) {
-        if (n0 + cb >= N) break;  // uniform over the CTA
+      for (int cb = c_lo + 32 * rpart; cb < c_lo + c_n; cb += cstep) {
+        if (n0 + cb >= N) break;  // uniform over the warp
         const int cl = cb + lane;
         const int64_t eb = col_ext[cl];
         const uint32_t fo = col_off[cl], lo0 = col_off[BN + cl], lo1 = col_off[2 * BN + cl];
@@ -594,9 +634,9 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
         const int32_t fr = col_row[cl], lr0 = col_row[BN + cl], lr1 = col_row[2 * BN + cl];
         const uint32_t so_cur = so_next;
         const int32_t sr_cur = sr_next;
-        if (has_skip && cb + 32 < c_lo + c_n) {
-          so_next = col_off[3 * BN + cl + 32];
-          sr_next = col_row[3 * BN + cl + 32];
+        if (has_skip && cb + cstep < c_lo + c_n) {
+          so_next = col_off[3 * BN + cl + cstep];
+          sr_next = col_row[3 * BN + cl + cstep];
         }
 #pragma unroll 1
         for (int g = half; g < 4; g += kParts) {
@@ -625,14 +665,21 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
           const float4 v0 = *reinterpret_cast<const float4*>(tw + kk * 32 + 8 * (lane & 3));
           const float4 v1 = *reinterpret_cast<const float4*>(tw + kk * 32 + 8 * (lane & 3) + 4);
           float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-          if (has_skip) {
+          if (staged) {
+            const int c = cb + 8 * g + kk;  // tile column (fused units: c_lo = 0)
+            const uint32_t rb = stg_base + (uint32_t)(c * stg_rows * 4);
+            const float4 s0 = ld_shared_v4(rb + (uint32_t)((stg_q0 ^ (c & 1)) << 4));
+            const float4 s1 = ld_shared_v4(rb + (uint32_t)(((stg_q0 + 1) ^ (c & 1)) << 4));
+            x[0] += s0.x; x[1] += s0.y; x[2] += s0.z; x[3] += s0.w;
+            x[4] += s1.x; x[5] += s1.y; x[6] += s1.z; x[7] += s1.w;
+          } else if (has_skip) {
             x[0] += sk0.x; x[1] += sk0.y; x[2] += sk0.z; x[3] += sk0.w;
             x[4] += sk1.x; x[5] += sk1.y; x[6] += sk1.z; x[7] += sk1.w;
             // the next group's residual loads overlap this group's stores
             if (g + kParts < 4)
               load_skip(cb, g + kParts, so_cur, sr_cur);
-            else if (cb + 32 < c_lo + c_n && n0 + cb + 32 < N)
-              load_skip(cb + 32, half, so_next, sr_next);
+            else if (cb + cstep < c_lo + c_n && n0 + cb + cstep < N)
+              load_skip(cb + cstep, half, so_next, sr_next);
           }
           const int src = 8 * g + kk;  // table lane of this lane's column
           const bool ok = vok && n0 + cb + src < N;

@@ -444,17 +444,21 @@ static cc_status upload_tc_operand(Model& m, NodePlan& p, const std::vector<floa
   // the same operand as contiguous 128 x 64 blocks (16 KB), block (mt, kc) at
   // (mt * Kt/64 + kc) * 16 KB; inside a block row r's 16-byte chunk c sits at
   // r*128 + ((c ^ (r & 7)) * 16): the shared-memory image of a 128-byte-swizzled
-  // K-major tile, so one bulk copy reproduces it
+  // K-major tile, so one bulk copy reproduces it.  With M <= 64, rows 64..127
+  // repeat rows 0..63 (TcArgs::mdup): the padding rows compute the same
+  // results, which the epilogue warps of the upper lane quarters store
   {
     const int nk = p.Kt / 64, mt_n = p.Mpad / 128;
     std::vector<uint16_t> tiled(lp.size());
     for (int mt = 0; mt < mt_n; ++mt)
       for (int kc = 0; kc < nk; ++kc) {
         uint16_t* blk = tiled.data() + ((size_t)mt * nk + kc) * 128 * 64;
-        for (int r = 0; r < 128; ++r)
+        for (int r = 0; r < 128; ++r) {
+          const int rs = p.M <= 64 ? (r & 63) : r;
           for (int c = 0; c < 8; ++c)
             std::memcpy(blk + r * 64 + ((c ^ (r & 7)) * 8),
-                        lp.data() + (size_t)(mt * 128 + r) * p.Kt + kc * 64 + c * 8, 16);
+                        lp.data() + (size_t)(mt * 128 + rs) * p.Kt + kc * 64 + c * 8, 16);
+        }
       }
     CC_CUDA(cudaMalloc(&p.dA_tiled, tiled.size() * 2));
     CC_CUDA(cudaMemcpy(p.dA_tiled, tiled.data(), tiled.size() * 2, cudaMemcpyHostToDevice));
@@ -742,6 +746,7 @@ cc_status Model::run_chain(const Batch& batch, const float* in, int64_t in_strid
         a.box_ok = li >= 0;
         a.ksplit = p.ksplit;
         a.deep_ok = max_streams <= 256;
+        a.mdup = p.M <= 64 && (!q || q->M <= 64);  // the tiles repeat their rows (upload_tc_operand)
         const int bn = tile_n_for(p, (int64_t)batch.count * ncols);
         CC_CUDA(launch_conv_tc(li >= 0 ? p.tmapT[li] : p.tmapB, p.tmapB, a, bn, st));
       } else {

@@ -111,6 +111,21 @@ __device__ __forceinline__ float4 ld_global_nc_v4(const void* p) {
   return v;
 }
 
+// 16-byte global -> shared copy that completes asynchronously (L2 only);
+// cp_async_wait_all waits for the calling thread's copies.
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* gptr) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gptr) : "memory");
+}
+__device__ __forceinline__ float4 ld_shared_v4(uint32_t saddr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(saddr));
+  return v;
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
   const int lo = __shfl_sync(0xffffffffu, (int)(uint32_t)v, src);
   const int hi = __shfl_sync(0xffffffffu, (int)(v >> 32), src);

@@ -164,6 +164,59 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
     fence_mbar_init();
     prefetch_tmap(a.box_ok ? &tmT : &tmB);
   }
+  // Producer set-up before the CTA barrier: the batch's slots and step
+  // counters are loaded while thread 0 initialises the barriers and warp 1
+  // allocates TMEM.  For most CTAs of a one-wave launch this runs when the
+  // previous launch's CTA on the SM exits, on the chain's critical path.
+  const int nks = ke - kb;
+  const int pre = nks < kStages ? nks : kStages;
+  const uint8_t* atile = static_cast<const uint8_t*>(a.A_tiled) + ((size_t)blockIdx.y * nk + kb) * L::kA;
+  constexpr int G = BN / 128;
+  bool boxes = false;
+  int32_t by[G], bz[G];
+  if (warp == 0) {
+    // Box form: the streams of the tile sit in consecutive slots at one step p,
+    // and the call's frames do not cross the ring's end; then tap k's rows of
+    // the 128 columns of half g start at view row pre + p - hist + j_g + k*dil
+    // of slot bz[g] (the mirrored tail holds the rows before ring row 0).
+    if (a.box_ok) {
+      const int64_t s_first = n0 / a.ncols;
+      const int64_t s_end = min((n0 + BN - 1) / a.ncols + 1, (int64_t)a.batch.count);
+      // A tile spans at most BN streams; lane l checks streams s_first + l +
+      // 32 i.  Every slot is loaded at once, then every step counter: two
+      // dependent round trips to L2.
+      constexpr int kIt = BN / 32;
+      int32_t sl[kIt];
+      int64_t sp[kIt];
+#pragma unroll
+      for (int i = 0; i < kIt; ++i) {
+        const int64_t s = s_first + lane + 32 * i;
+        sl[i] = s < s_end ? a.batch.slots[s] : 0;
+      }
+#pragma unroll
+      for (int i = 0; i < kIt; ++i) {
+        const int64_t s = s_first + lane + 32 * i;
+        sp[i] = s < s_end ? a.batch.counters[sl[i]] : 0;
+      }
+      const int32_t slot0 = __shfl_sync(0xffffffffu, sl[0], 0);  // stream s_first (lane 0, i = 0)
+      const int64_t step0 = shfl64(sp[0], 0);
+      bool reg = true;
+#pragma unroll
+      for (int i = 0; i < kIt; ++i) {
+        const int64_t s = s_first + lane + 32 * i;
+        if (s < s_end) reg = reg && sl[i] == slot0 + (int32_t)(s - s_first) && sp[i] == step0;
+      }
+      const int32_t p = (int32_t)ring_row(step0 * a.in.u, a.in.rows);
+      boxes = __all_sync(0xffffffffu, reg) && p + a.ncols <= a.in.rows;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int64_t ng = n0 + 128 * g;
+        const int64_t sg = ng / a.ncols;
+        by[g] = a.in.pre + p - a.hist + (int32_t)(ng - sg * a.ncols);
+        bz[g] = slot0 + (int32_t)(sg - s_first);
+      }
+    }
+  }
   if (warp == 1) {
     tmem_alloc(tbase, L::kTmemCols);
     tmem_relinquish();
@@ -179,41 +232,12 @@ __global__ void __launch_bounds__(TcLayout<BN, STAGES, FUSE, EW, SPLIT, MT>::kTh
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
-    // The weight tiles of the first stages are requested before anything else.
-    const int nks = ke - kb;
-    const int pre = nks < kStages ? nks : kStages;
-    const uint8_t* atile = static_cast<const uint8_t*>(a.A_tiled) + ((size_t)blockIdx.y * nk + kb) * L::kA;
+    // the weight tiles of the first stages
     if (lane == 0)
       for (int i = 0; i < pre; ++i) {
         mbar_arrive_expect_tx(full + i, L::kA + L::kB);
         bulk_load(sA + i * L::kA, atile + (size_t)i * L::kA, L::kA, full + i);
       }
-    constexpr int G = BN / 128;
-    // Box form: the streams of the tile sit in consecutive slots at one step p,
-    // and the call's frames do not cross the ring's end; then tap k's rows of
-    // the 128 columns of half g start at view row pre + p - hist + j_g + k*dil
-    // of slot bz[g] (the mirrored tail holds the rows before ring row 0).
-    bool boxes = false;
-    int32_t by[G], bz[G];
-    if (a.box_ok) {
-      const int64_t s_first = n0 / a.ncols;
-      const int64_t s_end = min((n0 + BN - 1) / a.ncols + 1, (int64_t)a.batch.count);
-      const int32_t slot0 = a.batch.slots[s_first];
-      const int64_t step0 = steps_of(a.batch, (int32_t)s_first);
-      bool reg = true;
-      for (int64_t s = s_first + lane; s < s_end; s += 32)
-        reg = reg && a.batch.slots[s] == slot0 + (int32_t)(s - s_first) &&
-              steps_of(a.batch, (int32_t)s) == step0;
-      const int32_t p = (int32_t)ring_row(step0 * a.in.u, a.in.rows);
-      boxes = __all_sync(0xffffffffu, reg) && p + a.ncols <= a.in.rows;
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int64_t ng = n0 + 128 * g;
-        const int64_t sg = ng / a.ncols;
-        by[g] = a.in.pre + p - a.hist + (int32_t)(ng - sg * a.ncols);
-        bz[g] = slot0 + (int32_t)(sg - s_first);
-      }
-    }
     // gather form: lane l gathers tile rows 4*(l + 32*g) .. +3 for g < G
     int32_t ybase[G][4], r0[G][4];
 #pragma unroll

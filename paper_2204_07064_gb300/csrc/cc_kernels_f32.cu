@@ -38,12 +38,9 @@ __device__ __forceinline__ void store_conv(const ConvArgs& a, int32_t m, int32_t
 // store, then the values go to every output view -- as float4 / 4-element
 // low-precision stores when the channel count allows it.
 template <int TM>
-__device__ __forceinline__ void store_column(const ConvArgs& a, int32_t n, const int32_t (&m)[TM],
-                                             float (&v)[TM], bool vec) {
-  const int32_t s = n / a.ncols;
-  const int32_t j = n - s * a.ncols;
-  char* base = slot_base(a.batch, s);
-  const int64_t tb = steps_of(a.batch, s) * a.out_u + (int64_t)j * a.phases;
+__device__ __forceinline__ void store_column_at(const ConvArgs& a, int32_t s, int32_t j, char* base, int64_t step,
+                                                const int32_t (&m)[TM], float (&v)[TM], bool vec) {
+  const int64_t tb = step * a.out_u + (int64_t)j * a.phases;
   const int32_t rf = a.out.f32.rows ? (int32_t)ring_row(tb, a.out.f32.rows) : 0;
   const int32_t r0 = a.out.lp[0].rows ? (int32_t)ring_row(tb, a.out.lp[0].rows) : 0;
   const int32_t r1 = a.out.lp[1].rows ? (int32_t)ring_row(tb, a.out.lp[1].rows) : 0;
@@ -117,6 +114,13 @@ __device__ __forceinline__ void store_column(const ConvArgs& a, int32_t n, const
     if (a.out.lp[0].rows) store_lp(base, a.out.lp[0], wrap_row(r0 + ph[i], a.out.lp[0].rows), ch[i], x);
     if (a.out.lp[1].rows) store_lp(base, a.out.lp[1], wrap_row(r1 + ph[i], a.out.lp[1].rows), ch[i], leaky(x));
   }
+}
+
+template <int TM>
+__device__ __forceinline__ void store_column(const ConvArgs& a, int32_t n, const int32_t (&m)[TM],
+                                             float (&v)[TM], bool vec) {
+  const int32_t s = n / a.ncols;
+  store_column_at<TM>(a, s, n - s * a.ncols, slot_base(a.batch, s), steps_of(a.batch, s), m, v, vec);
 }
 
 // ---------------------------------------------------------------------------
@@ -353,97 +357,117 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Narrow contraction (M <= 16 rows, Kt <= 64, cin % 4 == 0): one thread per
-// GEMM column with the weights in shared memory (every thread reads the same
-// weight: a broadcast) and its window read once, 16 bytes at a time.  Used by
-// the tail of the decoder (the noise branch's second conv, the inverse PQMF).
-// Only the 16-row form is instantiated: fully unrolled, a 32-row form is
-// 2048 FMAs on which the compiler's optimiser (not ptxas) spends minutes;
-// such layers take the general kernels.
+// Narrow contraction (M <= 16 rows, Kt <= 64, cin % 4 == 0): four threads per
+// GEMM column.  Thread q of a column's quad reduces indices 16q .. 16q+15 (its
+// quarter of the window, read with four 16-byte loads) into all 16 rows; the
+// quad then sums its partials with two XOR shuffles, in the fixed order
+// (q0 + q1) + (q2 + q3), and thread q stores rows 4q .. 4q+3.  Used by the
+// tail of the decoder (the noise branch's second conv, the inverse PQMF),
+// whose launches are short chains of dependent work: four threads per column
+// quarter each thread's chain.
 // ---------------------------------------------------------------------------
-template <int TM>
-__device__ __forceinline__ void small_column(const ConvArgs& a, int32_t n, const float* As) {
-  const int32_t s = n / a.ncols, j = n - s * a.ncols;
-  const float* col = ring_ptr<const float>(a.batch, s, a.in) + a.in.choff;
-  const int32_t r0 =
-      (int32_t)ring_row(steps_of(a.batch, s) * a.in.u + (int64_t)j * a.stride - a.hist, a.in.rows);
-  // the whole window (taps x cin <= 64 values) is requested before any use
-  float xw[64];
+constexpr int kSmallCols = 128;  // columns per block (threads = 4 x)
+constexpr int kSmallRowPad = 4;  // floats of padding after every 16 reduction indices
+
+__device__ __forceinline__ void small_column(const ConvArgs& a, bool valid, int32_t s, int32_t j, int32_t slot,
+                                             int64_t step, int q, const float* As) {
+  char* const base = a.batch.arena + (int64_t)slot * a.batch.slot_bytes;
+  const float* col = reinterpret_cast<const float*>(base + a.in.off) + a.in.choff;
+  const int32_t r0 = (int32_t)ring_row(step * a.in.u + (int64_t)j * a.stride - a.hist, a.in.rows);
+  // this thread's quarter of the window (cin % 4 == 0: four consecutive
+  // indices never straddle a tap), requested before any use
+  float xw[16];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int32_t k = 4 * q;
+  for (int i = 0; i < 4; ++i) {
+    const int32_t k = 16 * q + 4 * i;
     float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k < a.Kt) {
+    if (valid && k < a.Kt) {
       const int32_t tap = k / a.cin, c = k - tap * a.cin;
       v4 = *reinterpret_cast<const float4*>(col + (int64_t)wrap_row(r0 + tap * a.dil, a.in.rows) * a.in.chans + c);
     }
-    xw[k] = activate(v4.x, a.act);
-    xw[k + 1] = activate(v4.y, a.act);
-    xw[k + 2] = activate(v4.z, a.act);
-    xw[k + 3] = activate(v4.w, a.act);
+    xw[4 * i] = activate(v4.x, a.act);
+    xw[4 * i + 1] = activate(v4.y, a.act);
+    xw[4 * i + 2] = activate(v4.z, a.act);
+    xw[4 * i + 3] = activate(v4.w, a.act);
   }
-  float acc[TM];
+  float acc[16];
 #pragma unroll
-  for (int m = 0; m < TM; ++m) acc[m] = 0.f;
+  for (int m = 0; m < 16; ++m) acc[m] = 0.f;
+  // weights k-major, 16 rows per index, each quarter's block offset by
+  // kSmallRowPad floats so the quad's four reads fall in distinct banks
+  const float* Aq = As + q * (16 * 16 + kSmallRowPad);
 #pragma unroll
-  for (int k = 0; k < 64; ++k) {
-    if (k >= a.Kt) break;
-    const float4* w4 = reinterpret_cast<const float4*>(As + k * TM);
+  for (int i = 0; i < 16; ++i) {
+    const float4* w4 = reinterpret_cast<const float4*>(Aq + i * 16);
 #pragma unroll
-    for (int q = 0; q < TM / 4; ++q) {
-      const float4 w = w4[q];
-      acc[4 * q] = fmaf(w.x, xw[k], acc[4 * q]);
-      acc[4 * q + 1] = fmaf(w.y, xw[k], acc[4 * q + 1]);
-      acc[4 * q + 2] = fmaf(w.z, xw[k], acc[4 * q + 2]);
-      acc[4 * q + 3] = fmaf(w.w, xw[k], acc[4 * q + 3]);
+    for (int g = 0; g < 4; ++g) {
+      const float4 w = w4[g];
+      acc[4 * g] = fmaf(w.x, xw[i], acc[4 * g]);
+      acc[4 * g + 1] = fmaf(w.y, xw[i], acc[4 * g + 1]);
+      acc[4 * g + 2] = fmaf(w.z, xw[i], acc[4 * g + 2]);
+      acc[4 * g + 3] = fmaf(w.w, xw[i], acc[4 * g + 3]);
     }
   }
-  // an output that is only the caller's buffer with the TM rows contiguous
+#pragma unroll
+  for (int m = 0; m < 16; ++m) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], 1);
+#pragma unroll
+  for (int m = 0; m < 16; ++m) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], 2);
+  if (!valid) return;  // a column past the batch (its quad's shuffles are done)
+  float v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = q == 0 ? acc[i] : q == 1 ? acc[4 + i] : q == 2 ? acc[8 + i] : acc[12 + i];
+  // an output that is only the caller's buffer with the 16 rows contiguous
   // there (one phase per row of one channel, or channels of one phase):
-  // 16-byte stores
+  // one 16-byte store per thread
   const bool ext_only = a.out.ext && !a.out.f32.rows && !a.out.lp[0].rows && !a.out.lp[1].rows && !a.has_skip;
-  if (ext_only && a.M == TM && (a.cout == 1 || a.phases == 1)) {
-    float* e = a.out.ext + (int64_t)s * a.out.ext_stride + (int64_t)j * TM;
+  if (ext_only && a.M == 16 && (a.cout == 1 || a.phases == 1)) {
+    float* e = a.out.ext + (int64_t)s * a.out.ext_stride + (int64_t)j * 16 + 4 * q;
     if ((reinterpret_cast<uintptr_t>(e) & 15) == 0) {
+      float b4[4];
 #pragma unroll
-      for (int m = 0; m < TM; m += 4) {
-        float b4[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) b4[q] = acc[m + q] + (a.bias ? a.bias[a.cout == 1 ? 0 : m + q] : 0.f);
-        *reinterpret_cast<float4*>(e + m) = make_float4(b4[0], b4[1], b4[2], b4[3]);
-      }
+      for (int i = 0; i < 4; ++i) b4[i] = v[i] + (a.bias ? a.bias[a.cout == 1 ? 0 : 4 * q + i] : 0.f);
+      *reinterpret_cast<float4*>(e) = make_float4(b4[0], b4[1], b4[2], b4[3]);
       return;
     }
   }
-  int32_t ms[TM];
-#pragma unroll
-  for (int m = 0; m < TM; ++m) ms[m] = m;
-  store_column<TM>(a, n, ms, acc, (a.cout % 4 == 0) && (a.M % 4 == 0));
+  const int32_t ms[4] = {4 * q, 4 * q + 1, 4 * q + 2, 4 * q + 3};
+  store_column_at<4>(a, s, j, base, step, ms, v, (a.cout % 4 == 0) && (a.M % 4 == 0));
 }
 
-template <int TM>
-__global__ void __launch_bounds__(128) k_conv_small_f32(const ConvArgs a) {
-  // weights k-major ([Kt][TM], rows past M zero): the TM weights of one
-  // reduction index are four 16-byte broadcast reads
-  __shared__ __align__(16) float As[TM * 64];
-  // weights are written once at model creation: staged before the wait
-  for (int i = threadIdx.x; i < TM * a.Kt; i += 128) {
-    const int m = i / a.Kt, k = i - m * a.Kt;
-    As[k * TM + m] = m < a.M ? a.A[m * a.Kt + k] : 0.f;
+__global__ void __launch_bounds__(4 * kSmallCols, 2) k_conv_small_f32(const ConvArgs a) {
+  // weights k-major ([Kt][16], rows past M zero; see small_column)
+  __shared__ __align__(16) float As[4 * (16 * 16 + kSmallRowPad)];
+  // Before the wait: the weights (written once at model creation), and the
+  // column's slot and step counter, final when any launch after the chain's
+  // first starts (the slot list is uploaded before the chain; the counters
+  // were advanced by the previous chain's last launch or, in this launch,
+  // after every column has read them)
+  const int q = threadIdx.x & 3;
+  const int32_t n = blockIdx.x * kSmallCols + (threadIdx.x >> 2);
+  const int32_t N = a.batch.count * a.ncols;
+  int32_t s = 0, slot = 0;
+  int64_t step = 0;
+  if (n < N) {
+    s = n / a.ncols;
+    slot = a.batch.slots[s];
+    step = a.batch.counters[slot];
+  }
+  for (int i = threadIdx.x; i < 16 * 64; i += 4 * kSmallCols) {
+    const int m = i & 15, k = i >> 4;
+    As[(k >> 4) * (16 * 16 + kSmallRowPad) + (k & 15) * 16 + m] = (m < a.M && k < a.Kt) ? a.A[m * a.Kt + k] : 0.f;
   }
   __syncthreads();
   pdl_wait();
   pdl_release();
-  const int32_t n = blockIdx.x * 128 + threadIdx.x;
-  const int32_t N = a.batch.count * a.ncols;
-  if (n < N) small_column<TM>(a, n, As);
+  // a column past the batch still takes part in its quad's shuffles
+  small_column(a, n < N, s, n < N ? n - s * a.ncols : 0, slot, step, q, As);
   if (a.advance) {
     // the last launch of the chain: this block's columns are whole streams
     // (128 a multiple of the columns per stream, or equal to them); once every
     // thread has read its stream's counter, the block advances them
     __syncthreads();
-    const int32_t s0 = blockIdx.x * 128 / a.ncols;
-    const int32_t s1 = min((blockIdx.x * 128 + 127) / a.ncols + 1, a.batch.count);
+    const int32_t s0 = blockIdx.x * kSmallCols / a.ncols;
+    const int32_t s1 = min((blockIdx.x * kSmallCols + kSmallCols - 1) / a.ncols + 1, a.batch.count);
     if ((int32_t)threadIdx.x < s1 - s0)
       const_cast<int64_t*>(a.batch.counters)[a.batch.slots[s0 + threadIdx.x]] += a.advance;
   }
@@ -463,79 +487,88 @@ __device__ __forceinline__ float input_noise(uint64_t seed, int64_t frame, int32
 
 __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf(-x)); }
 
-// One thread per (stream, frame): the ring rows of the three branches and of
-// every output view are computed once; bands go 16 at a time, the 48 branch
-// values of a block of 16 requested before any use.
+// One thread per (stream, frame, group of four bands): short chains of
+// dependent work (three 16-byte branch loads, four tanh / sigmoid / noise
+// evaluations, the view stores), four threads per frame of 16 bands.
 __global__ void k_heads(const HeadsArgs a) {
+  const int32_t G = (a.bands + 3) / 4;  // band groups per frame
+  const int64_t total = (int64_t)a.batch.count * a.ncols * G;
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // the first item's slot, step counter and seed before the wait (final
+  // when any launch after the chain's first starts; the heads never start a
+  // chain)
+  int32_t slot = 0;
+  int64_t step = 0;
+  uint64_t seed = 0;
+  if (i0 < total) {
+    slot = a.batch.slots[i0 / G / a.ncols];
+    step = a.batch.counters[slot];
+    seed = a.batch.seeds[slot];
+  }
   pdl_wait();
   pdl_release();
-  const int64_t total = (int64_t)a.batch.count * a.ncols;
-  for (int64_t nj = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; nj < total;
-       nj += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t it = i0; it < total; it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nj = it / G;
+    const int32_t b0 = 4 * (int32_t)(it - nj * G);
     const int32_t s = (int32_t)(nj / a.ncols);
     const int32_t j = (int32_t)(nj - (int64_t)s * a.ncols);
-    const int64_t t = steps_of(a.batch, s) * a.out_u + j;
-    char* base = slot_base(a.batch, s);
+    if (it != i0) {
+      slot = a.batch.slots[s];
+      step = a.batch.counters[slot];
+      seed = a.batch.seeds[slot];
+    }
+    const int64_t t = step * a.out_u + j;
+    char* base = a.batch.arena + (int64_t)slot * a.batch.slot_bytes;
     const float* in[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q)
       in[q] = reinterpret_cast<const float*>(base + a.in[q].off) +
-              ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + a.in[q].choff;
-    const uint64_t seed = a.batch.seeds[a.batch.slots[s]];
-    const int32_t rf = a.out.f32.rows ? (int32_t)ring_row(t, a.out.f32.rows) : 0;
-    const int32_t r0 = a.out.lp[0].rows ? (int32_t)ring_row(t, a.out.lp[0].rows) : 0;
-    const int32_t r1 = a.out.lp[1].rows ? (int32_t)ring_row(t, a.out.lp[1].rows) : 0;
-    float* fo = a.out.f32.rows ? reinterpret_cast<float*>(base + a.out.f32.off) + (int64_t)rf * a.out.f32.chans
+              ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + a.in[q].choff + b0;
+    float* fo = a.out.f32.rows ? reinterpret_cast<float*>(base + a.out.f32.off) +
+                                     ring_row(t, a.out.f32.rows) * a.out.f32.chans + b0
                                : nullptr;
-    float* eo = a.out.ext ? a.out.ext + (int64_t)s * a.out.ext_stride + (int64_t)j * a.bands : nullptr;
-    // 16-byte loads of the branches and stores of the FP32 view when every
+    // 16-byte loads of the branches and store of the FP32 view when every
     // row is 16-byte aligned (channel counts and offsets multiples of 4)
     bool vec4 = (a.bands & 3) == 0 && (!fo || (reinterpret_cast<uintptr_t>(fo) & 15) == 0);
 #pragma unroll
     for (int q = 0; q < 3; ++q) vec4 = vec4 && (reinterpret_cast<uintptr_t>(in[q]) & 15) == 0;
-    for (int32_t b0 = 0; b0 < a.bands; b0 += 16) {
-      float v[3][16];
+    float v[3][4];
 #pragma unroll
-      for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < 3; ++q) {
+      if (vec4) {
+        const float4 t4 = *reinterpret_cast<const float4*>(in[q]);
+        v[q][0] = t4.x;
+        v[q][1] = t4.y;
+        v[q][2] = t4.z;
+        v[q][3] = t4.w;
+      } else {
 #pragma unroll
-        for (int k = 0; k < 16; k += 4) {
-          if (vec4 && b0 + k < a.bands) {
-            const float4 t4 = *reinterpret_cast<const float4*>(in[q] + b0 + k);
-            v[q][k] = t4.x;
-            v[q][k + 1] = t4.y;
-            v[q][k + 2] = t4.z;
-            v[q][k + 3] = t4.w;
-          } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) v[q][k + e] = b0 + k + e < a.bands ? in[q][b0 + k + e] : 0.f;
-          }
-        }
-      float y[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int32_t b = b0 + k;
-        y[k] = tanhf(v[0][k]) * sigmoidf_(v[1][k]);
-        if (a.noise && b < a.bands) y[k] += sigmoidf_(v[2][k]) * noise_uniform(seed, t - a.delay, b, a.bands);
+        for (int e = 0; e < 4; ++e) v[q][e] = b0 + e < a.bands ? in[q][e] : 0.f;
       }
+    }
+    float y[4];
 #pragma unroll
-      for (int k = 0; k < 16; k += 4) {
-        const int32_t b = b0 + k;
-        if (b >= a.bands) break;
-        if (fo && vec4) {
-          *reinterpret_cast<float4*>(fo + b) = make_float4(y[k], y[k + 1], y[k + 2], y[k + 3]);
-        } else if (fo) {
+    for (int e = 0; e < 4; ++e) {
+      const int32_t b = b0 + e;
+      y[e] = tanhf(v[0][e]) * sigmoidf_(v[1][e]);
+      if (a.noise && b < a.bands) y[e] += sigmoidf_(v[2][e]) * noise_uniform(seed, t - a.delay, b, a.bands);
+    }
+    if (fo && vec4) {
+      *reinterpret_cast<float4*>(fo) = make_float4(y[0], y[1], y[2], y[3]);
+    } else if (fo) {
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (b + e < a.bands) fo[b + e] = y[k + e];
-        }
+      for (int e = 0; e < 4; ++e)
+        if (b0 + e < a.bands) fo[e] = y[e];
+    }
+    float* eo = a.out.ext ? a.out.ext + (int64_t)s * a.out.ext_stride + (int64_t)j * a.bands + b0 : nullptr;
+    const int32_t r0 = a.out.lp[0].rows ? (int32_t)ring_row(t, a.out.lp[0].rows) : 0;
+    const int32_t r1 = a.out.lp[1].rows ? (int32_t)ring_row(t, a.out.lp[1].rows) : 0;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          if (b + e >= a.bands) break;
-          if (eo) eo[b + e] = y[k + e];
-          if (a.out.lp[0].rows) store_lp(base, a.out.lp[0], r0, b + e, y[k + e]);
-          if (a.out.lp[1].rows) store_lp(base, a.out.lp[1], r1, b + e, leaky(y[k + e]));
-        }
-      }
+    for (int e = 0; e < 4; ++e) {
+      if (b0 + e >= a.bands) break;
+      if (eo) eo[e] = y[e];
+      if (a.out.lp[0].rows) store_lp(base, a.out.lp[0], r0, b0 + e, y[e]);
+      if (a.out.lp[1].rows) store_lp(base, a.out.lp[1], r1, b0 + e, leaky(y[e]));
     }
   }
 }
@@ -604,7 +637,7 @@ int elementwise_grid(int64_t total) {
 static bool takes_small(const ConvArgs& a) { return a.M <= 16 && a.Kt <= 64 && a.cin % 4 == 0; }
 
 bool conv_f32_can_advance(const ConvArgs& a) {
-  return takes_small(a) && a.ncols > 0 && (a.ncols == 128 || 128 % a.ncols == 0);
+  return takes_small(a) && a.ncols > 0 && (a.ncols == kSmallCols || kSmallCols % a.ncols == 0);
 }
 
 cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
@@ -613,8 +646,8 @@ cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
   if (a.advance && !conv_f32_can_advance(a)) return cudaErrorInvalidValue;
   auto tiles = [&](int bm, int bn) { return ((a.M + bm - 1) / bm) * ((N + bn - 1) / bn); };
   if (takes_small(a)) {
-    dim3 grid((unsigned)((N + 127) / 128));
-    return launch_pdl(k_conv_small_f32<16>, grid, dim3(128), 0, st, a);
+    dim3 grid((unsigned)((N + kSmallCols - 1) / kSmallCols));
+    return launch_pdl(k_conv_small_f32, grid, dim3(4 * kSmallCols), 0, st, a);
   }
   if (a.cin % 8 == 0 && a.M >= 128 && tiles(128, 128) >= 2 * 152) {
     dim3 grid((unsigned)((N + 127) / 128), (unsigned)((a.M + 127) / 128));
@@ -634,7 +667,8 @@ cudaError_t launch_conv_f32(const ConvArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_heads(const HeadsArgs& a, cudaStream_t st) {
-  const int64_t total = (int64_t)a.batch.count * a.ncols;
+  // one thread per (stream, frame, group of four bands)
+  const int64_t total = (int64_t)a.batch.count * a.ncols * ((a.bands + 3) / 4);
   if (total <= 0) return cudaSuccess;
   return launch_pdl(k_heads, dim3(elementwise_grid(total)), dim3(256), 0, st, a);
 }

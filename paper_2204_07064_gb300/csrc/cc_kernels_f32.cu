@@ -37,14 +37,28 @@ __device__ __forceinline__ void store_conv(const ConvArgs& a, int32_t m, int32_t
 // modulo per view), every bias / residual load is issued before the first
 // store, then the values go to every output view -- as float4 / 4-element
 // low-precision stores when the channel count allows it.
-template <int TM>
-__device__ __forceinline__ void store_column_at(const ConvArgs& a, int32_t s, int32_t j, char* base, int64_t step,
-                                                const int32_t (&m)[TM], float (&v)[TM], bool vec) {
+// Ring rows of a column's first output time in each view (and of its
+// residual): known from the stream's step counter alone, so the narrow kernel
+// computes them before its dependency wait.
+struct ColRows {
+  int32_t rf, r0, r1, rs;
+};
+
+__device__ __forceinline__ ColRows col_rows(const ConvArgs& a, int64_t step, int32_t j) {
   const int64_t tb = step * a.out_u + (int64_t)j * a.phases;
-  const int32_t rf = a.out.f32.rows ? (int32_t)ring_row(tb, a.out.f32.rows) : 0;
-  const int32_t r0 = a.out.lp[0].rows ? (int32_t)ring_row(tb, a.out.lp[0].rows) : 0;
-  const int32_t r1 = a.out.lp[1].rows ? (int32_t)ring_row(tb, a.out.lp[1].rows) : 0;
-  const int32_t rs = a.has_skip ? (int32_t)ring_row(tb - a.skip_A, a.skip.rows) : 0;
+  ColRows r;
+  r.rf = a.out.f32.rows ? (int32_t)ring_row(tb, a.out.f32.rows) : 0;
+  r.r0 = a.out.lp[0].rows ? (int32_t)ring_row(tb, a.out.lp[0].rows) : 0;
+  r.r1 = a.out.lp[1].rows ? (int32_t)ring_row(tb, a.out.lp[1].rows) : 0;
+  r.rs = a.has_skip ? (int32_t)ring_row(tb - a.skip_A, a.skip.rows) : 0;
+  return r;
+}
+
+template <int TM>
+__device__ __forceinline__ void store_column_rows(const ConvArgs& a, int32_t s, int32_t j, char* base,
+                                                  const ColRows& cr, const int32_t (&m)[TM], float (&v)[TM],
+                                                  bool vec) {
+  const int32_t rf = cr.rf, r0 = cr.r0, r1 = cr.r1, rs = cr.rs;
   int32_t ph[TM], ch[TM];
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
@@ -120,7 +134,8 @@ template <int TM>
 __device__ __forceinline__ void store_column(const ConvArgs& a, int32_t n, const int32_t (&m)[TM],
                                              float (&v)[TM], bool vec) {
   const int32_t s = n / a.ncols;
-  store_column_at<TM>(a, s, n - s * a.ncols, slot_base(a.batch, s), steps_of(a.batch, s), m, v, vec);
+  const int32_t j = n - s * a.ncols;
+  store_column_rows<TM>(a, s, j, slot_base(a.batch, s), col_rows(a, steps_of(a.batch, s), j), m, v, vec);
 }
 
 // ---------------------------------------------------------------------------
@@ -369,11 +384,9 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
 constexpr int kSmallCols = 128;  // columns per block (threads = 4 x)
 constexpr int kSmallRowPad = 4;  // floats of padding after every 16 reduction indices
 
-__device__ __forceinline__ void small_column(const ConvArgs& a, bool valid, int32_t s, int32_t j, int32_t slot,
-                                             int64_t step, int q, const float* As) {
-  char* const base = a.batch.arena + (int64_t)slot * a.batch.slot_bytes;
+__device__ __forceinline__ void small_column(const ConvArgs& a, bool valid, int32_t s, int32_t j, char* base,
+                                             int32_t r0, const ColRows& cr, int q, const float* As) {
   const float* col = reinterpret_cast<const float*>(base + a.in.off) + a.in.choff;
-  const int32_t r0 = (int32_t)ring_row(step * a.in.u + (int64_t)j * a.stride - a.hist, a.in.rows);
   // this thread's quarter of the window (cin % 4 == 0: four consecutive
   // indices never straddle a tap), requested before any use
   float xw[16];
@@ -431,26 +444,30 @@ __device__ __forceinline__ void small_column(const ConvArgs& a, bool valid, int3
     }
   }
   const int32_t ms[4] = {4 * q, 4 * q + 1, 4 * q + 2, 4 * q + 3};
-  store_column_at<4>(a, s, j, base, step, ms, v, (a.cout % 4 == 0) && (a.M % 4 == 0));
+  store_column_rows<4>(a, s, j, base, cr, ms, v, (a.cout % 4 == 0) && (a.M % 4 == 0));
 }
 
 __global__ void __launch_bounds__(4 * kSmallCols, 2) k_conv_small_f32(const ConvArgs a) {
   // weights k-major ([Kt][16], rows past M zero; see small_column)
   __shared__ __align__(16) float As[4 * (16 * 16 + kSmallRowPad)];
-  // Before the wait: the weights (written once at model creation), and the
-  // column's slot and step counter, final when any launch after the chain's
-  // first starts (the slot list is uploaded before the chain; the counters
+  // Before the wait: the weights (written once at model creation), the
+  // column's slot and step counter (final when any launch after the chain's
+  // first starts: the slot list is uploaded before the chain; the counters
   // were advanced by the previous chain's last launch or, in this launch,
-  // after every column has read them)
+  // after every column has read them), and the ring rows that follow from
+  // them (64-bit remainders, kept off the path after the wait)
   const int q = threadIdx.x & 3;
   const int32_t n = blockIdx.x * kSmallCols + (threadIdx.x >> 2);
   const int32_t N = a.batch.count * a.ncols;
-  int32_t s = 0, slot = 0;
-  int64_t step = 0;
+  int32_t s = 0, j = 0, slot = 0, r0 = 0;
+  ColRows cr{0, 0, 0, 0};
   if (n < N) {
     s = n / a.ncols;
+    j = n - s * a.ncols;
     slot = a.batch.slots[s];
-    step = a.batch.counters[slot];
+    const int64_t step = a.batch.counters[slot];
+    r0 = (int32_t)ring_row(step * a.in.u + (int64_t)j * a.stride - a.hist, a.in.rows);
+    cr = col_rows(a, step, j);
   }
   for (int i = threadIdx.x; i < 16 * 64; i += 4 * kSmallCols) {
     const int m = i & 15, k = i >> 4;
@@ -460,7 +477,7 @@ __global__ void __launch_bounds__(4 * kSmallCols, 2) k_conv_small_f32(const Conv
   pdl_wait();
   pdl_release();
   // a column past the batch still takes part in its quad's shuffles
-  small_column(a, n < N, s, n < N ? n - s * a.ncols : 0, slot, step, q, As);
+  small_column(a, n < N, s, j, a.batch.arena + (int64_t)slot * a.batch.slot_bytes, r0, cr, q, As);
   if (a.advance) {
     // the last launch of the chain: this block's columns are whole streams
     // (128 a multiple of the columns per stream, or equal to them); once every
@@ -489,87 +506,108 @@ __device__ __forceinline__ float sigmoidf_(float x) { return 1.0f / (1.0f + expf
 
 // One thread per (stream, frame, group of four bands): short chains of
 // dependent work (three 16-byte branch loads, four tanh / sigmoid / noise
-// evaluations, the view stores), four threads per frame of 16 bands.
+// evaluations, the view stores), four threads per frame of 16 bands.  What
+// depends only on the stream's slot, step and seed (ring rows, addresses, the
+// noise draws) is prepared before the dependency wait.
+struct HeadsItem {
+  const float* in[3];  // the three branches' values of bands b0 .. b0+3
+  float* fo;           // FP32 view row (+ b0) or null
+  float* eo;           // caller's buffer (+ b0) or null
+  char* base;          // the stream's slot
+  int32_t r0, r1;      // low-precision view rows
+  int32_t b0;
+  bool vec4;
+  float nz[4];         // noise draws u(t, b) of the four bands (0 without noise)
+};
+
+__device__ __forceinline__ HeadsItem heads_prep(const HeadsArgs& a, int64_t it, int32_t G, int32_t slot,
+                                                int64_t step, uint64_t seed) {
+  HeadsItem h;
+  const int64_t nj = it / G;
+  h.b0 = 4 * (int32_t)(it - nj * G);
+  const int32_t s = (int32_t)(nj / a.ncols);
+  const int32_t j = (int32_t)(nj - (int64_t)s * a.ncols);
+  const int64_t t = step * a.out_u + j;
+  h.base = a.batch.arena + (int64_t)slot * a.batch.slot_bytes;
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+    h.in[q] = reinterpret_cast<const float*>(h.base + a.in[q].off) +
+              ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + a.in[q].choff + h.b0;
+  h.fo = a.out.f32.rows ? reinterpret_cast<float*>(h.base + a.out.f32.off) +
+                              ring_row(t, a.out.f32.rows) * a.out.f32.chans + h.b0
+                        : nullptr;
+  h.eo = a.out.ext ? a.out.ext + (int64_t)s * a.out.ext_stride + (int64_t)j * a.bands + h.b0 : nullptr;
+  h.r0 = a.out.lp[0].rows ? (int32_t)ring_row(t, a.out.lp[0].rows) : 0;
+  h.r1 = a.out.lp[1].rows ? (int32_t)ring_row(t, a.out.lp[1].rows) : 0;
+  // 16-byte loads of the branches and store of the FP32 view when every
+  // row is 16-byte aligned (channel counts and offsets multiples of 4)
+  bool vec4 = (a.bands & 3) == 0 && (!h.fo || (reinterpret_cast<uintptr_t>(h.fo) & 15) == 0);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) vec4 = vec4 && (reinterpret_cast<uintptr_t>(h.in[q]) & 15) == 0;
+  h.vec4 = vec4;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int32_t b = h.b0 + e;
+    h.nz[e] = (a.noise && b < a.bands) ? noise_uniform(seed, t - a.delay, b, a.bands) : 0.f;
+  }
+  return h;
+}
+
+__device__ __forceinline__ void heads_item(const HeadsArgs& a, const HeadsItem& h) {
+  float v[3][4];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    if (h.vec4) {
+      const float4 t4 = *reinterpret_cast<const float4*>(h.in[q]);
+      v[q][0] = t4.x;
+      v[q][1] = t4.y;
+      v[q][2] = t4.z;
+      v[q][3] = t4.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[q][e] = h.b0 + e < a.bands ? h.in[q][e] : 0.f;
+    }
+  }
+  float y[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    y[e] = tanhf(v[0][e]) * sigmoidf_(v[1][e]);
+    if (a.noise && h.b0 + e < a.bands) y[e] += sigmoidf_(v[2][e]) * h.nz[e];
+  }
+  if (h.fo && h.vec4) {
+    *reinterpret_cast<float4*>(h.fo) = make_float4(y[0], y[1], y[2], y[3]);
+  } else if (h.fo) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (h.b0 + e < a.bands) h.fo[e] = y[e];
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    if (h.b0 + e >= a.bands) break;
+    if (h.eo) h.eo[e] = y[e];
+    if (a.out.lp[0].rows) store_lp(h.base, a.out.lp[0], h.r0, h.b0 + e, y[e]);
+    if (a.out.lp[1].rows) store_lp(h.base, a.out.lp[1], h.r1, h.b0 + e, leaky(y[e]));
+  }
+}
+
 __global__ void k_heads(const HeadsArgs a) {
   const int32_t G = (a.bands + 3) / 4;  // band groups per frame
   const int64_t total = (int64_t)a.batch.count * a.ncols * G;
   const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  // the first item's slot, step counter and seed before the wait (final
-  // when any launch after the chain's first starts; the heads never start a
-  // chain)
-  int32_t slot = 0;
-  int64_t step = 0;
-  uint64_t seed = 0;
+  // the first item prepared before the wait: its stream's slot, step counter
+  // and seed are final when any launch after the chain's first starts (the
+  // heads never start a chain)
+  HeadsItem h0;
   if (i0 < total) {
-    slot = a.batch.slots[i0 / G / a.ncols];
-    step = a.batch.counters[slot];
-    seed = a.batch.seeds[slot];
+    const int32_t slot = a.batch.slots[i0 / G / a.ncols];
+    h0 = heads_prep(a, i0, G, slot, a.batch.counters[slot], a.batch.seeds[slot]);
   }
   pdl_wait();
   pdl_release();
-  for (int64_t it = i0; it < total; it += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t nj = it / G;
-    const int32_t b0 = 4 * (int32_t)(it - nj * G);
-    const int32_t s = (int32_t)(nj / a.ncols);
-    const int32_t j = (int32_t)(nj - (int64_t)s * a.ncols);
-    if (it != i0) {
-      slot = a.batch.slots[s];
-      step = a.batch.counters[slot];
-      seed = a.batch.seeds[slot];
-    }
-    const int64_t t = step * a.out_u + j;
-    char* base = a.batch.arena + (int64_t)slot * a.batch.slot_bytes;
-    const float* in[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      in[q] = reinterpret_cast<const float*>(base + a.in[q].off) +
-              ring_row(t - a.A[q], a.in[q].rows) * a.in[q].chans + a.in[q].choff + b0;
-    float* fo = a.out.f32.rows ? reinterpret_cast<float*>(base + a.out.f32.off) +
-                                     ring_row(t, a.out.f32.rows) * a.out.f32.chans + b0
-                               : nullptr;
-    // 16-byte loads of the branches and store of the FP32 view when every
-    // row is 16-byte aligned (channel counts and offsets multiples of 4)
-    bool vec4 = (a.bands & 3) == 0 && (!fo || (reinterpret_cast<uintptr_t>(fo) & 15) == 0);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) vec4 = vec4 && (reinterpret_cast<uintptr_t>(in[q]) & 15) == 0;
-    float v[3][4];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (vec4) {
-        const float4 t4 = *reinterpret_cast<const float4*>(in[q]);
-        v[q][0] = t4.x;
-        v[q][1] = t4.y;
-        v[q][2] = t4.z;
-        v[q][3] = t4.w;
-      } else {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) v[q][e] = b0 + e < a.bands ? in[q][e] : 0.f;
-      }
-    }
-    float y[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int32_t b = b0 + e;
-      y[e] = tanhf(v[0][e]) * sigmoidf_(v[1][e]);
-      if (a.noise && b < a.bands) y[e] += sigmoidf_(v[2][e]) * noise_uniform(seed, t - a.delay, b, a.bands);
-    }
-    if (fo && vec4) {
-      *reinterpret_cast<float4*>(fo) = make_float4(y[0], y[1], y[2], y[3]);
-    } else if (fo) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (b0 + e < a.bands) fo[e] = y[e];
-    }
-    float* eo = a.out.ext ? a.out.ext + (int64_t)s * a.out.ext_stride + (int64_t)j * a.bands + b0 : nullptr;
-    const int32_t r0 = a.out.lp[0].rows ? (int32_t)ring_row(t, a.out.lp[0].rows) : 0;
-    const int32_t r1 = a.out.lp[1].rows ? (int32_t)ring_row(t, a.out.lp[1].rows) : 0;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      if (b0 + e >= a.bands) break;
-      if (eo) eo[e] = y[e];
-      if (a.out.lp[0].rows) store_lp(base, a.out.lp[0], r0, b0 + e, y[e]);
-      if (a.out.lp[1].rows) store_lp(base, a.out.lp[1], r1, b0 + e, leaky(y[e]));
-    }
+  if (i0 < total) heads_item(a, h0);
+  for (int64_t it = i0 + (int64_t)gridDim.x * blockDim.x; it < total; it += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t slot = a.batch.slots[it / G / a.ncols];
+    heads_item(a, heads_prep(a, it, G, slot, a.batch.counters[slot], a.batch.seeds[slot]));
   }
 }
 

@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Narrow contraction (M <= 16 rows, Kt <= 64, cin % 4 == 0): four threads per
+// Narrow contraction (M <= 16 rows, Kt <= 64): four threads per
 // GEMM column.  Thread q of a column's quad reduces indices 16q .. 16q+15 (its
 // quarter of the window, read with four 16-byte loads) into all 16 rows; the
 // quad then sums its partials with two XOR shuffles, in the fixed order
@@ -387,16 +387,29 @@ constexpr int kSmallRowPad = 4;  // floats of padding after every 16 reduction i
 __device__ __forceinline__ void small_column(const ConvArgs& a, bool valid, int32_t s, int32_t j, char* base,
                                              int32_t r0, const ColRows& cr, int q, const float* As) {
   const float* col = reinterpret_cast<const float*>(base + a.in.off) + a.in.choff;
-  // this thread's quarter of the window (cin % 4 == 0: four consecutive
-  // indices never straddle a tap), requested before any use
+  // this thread's quarter of the window, requested before any use: 16-byte
+  // loads when cin % 4 == 0 (four consecutive indices never straddle a tap),
+  // else one value per index (the PQMF analysis filterbank: cin = 1)
+  const bool vec_in = a.cin % 4 == 0;
   float xw[16];
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int32_t k = 16 * q + 4 * i;
     float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid && k < a.Kt) {
-      const int32_t tap = k / a.cin, c = k - tap * a.cin;
-      v4 = *reinterpret_cast<const float4*>(col + (int64_t)wrap_row(r0 + tap * a.dil, a.in.rows) * a.in.chans + c);
+      if (vec_in) {
+        const int32_t tap = k / a.cin, c = k - tap * a.cin;
+        v4 = *reinterpret_cast<const float4*>(col + (int64_t)wrap_row(r0 + tap * a.dil, a.in.rows) * a.in.chans + c);
+      } else {
+        float e4[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int32_t ke = k + e;
+          const int32_t tap = ke / a.cin, c = ke - tap * a.cin;
+          e4[e] = ke < a.Kt ? col[(int64_t)wrap_row(r0 + tap * a.dil, a.in.rows) * a.in.chans + c] : 0.f;
+        }
+        v4 = make_float4(e4[0], e4[1], e4[2], e4[3]);
+      }
     }
     xw[4 * i] = activate(v4.x, a.act);
     xw[4 * i + 1] = activate(v4.y, a.act);
@@ -672,7 +685,7 @@ int elementwise_grid(int64_t total) {
 
 }  // namespace
 
-static bool takes_small(const ConvArgs& a) { return a.M <= 16 && a.Kt <= 64 && a.cin % 4 == 0; }
+static bool takes_small(const ConvArgs& a) { return a.M <= 16 && a.Kt <= 64; }
 
 bool conv_f32_can_advance(const ConvArgs& a) {
   return takes_small(a) && a.ncols > 0 && (a.ncols == kSmallCols || kSmallCols % a.ncols == 0);

@@ -27,12 +27,14 @@ pytestmark = pytest.mark.gpu
 FP32_TOL = 1e-5
 
 # (c_in, c_out, kernel, dilation, pad_left, act, frames per call, calls); the
-# FP32 kernel each reaches: narrow (M <= 16, K*c_in <= 64), 64 x 64 tile,
-# skinny GEMV without / with 16-byte window loads, 128 x 128 tile
+# FP32 kernel each reaches: narrow (M <= 16, K*c_in <= 64) with 16-byte or
+# single-value window loads, 64 x 64 tile, skinny GEMV without / with 16-byte
+# window loads, 128 x 128 tile
 CASES = [
     (16, 16, 3, 2, 2, "leaky", 512, 2),     # narrow kernel, symmetric pads
     (64, 32, 3, 9, 9, None, 300, 2),        # 64 x 64 tile
-    (6, 5, 3, 9, 9, "leaky", 3, 5),         # GEMV (c_in % 4 != 0); 3 frames < 18 cached: the cache wraps
+    (6, 5, 3, 9, 9, "leaky", 3, 5),         # narrow, c_in % 4 != 0; 3 frames < 18 cached: the cache wraps
+    (6, 20, 3, 9, 9, "leaky", 3, 5),        # GEMV (c_in % 4 != 0, M > 16); the cache wraps
     (64, 40, 3, 1, 1, None, 16, 3),         # GEMV with vector loads (N < 32)
     (32, 48, 5, 2, 2, None, 100, 2),        # uneven pads: 2 left, 6 right
     (128, 256, 3, 1, 1, "leaky", 19456, 2), # 128 x 128 tile (>= 2 x 152 tiles)

@@ -963,7 +963,7 @@ def main():
 
     # roofline of the dominant kernel class: the contractions on the tensor
     # cores (FFMA in FP32 mode).  Their algorithmic FLOPs per step divided by
-    # their share of the graph-timed step; the share comes from the per-launch
+    # their share of the timed step; the share comes from the per-launch
     # event pass, whose absolute times break the launch overlap and so are
     # not used as durations
     info_u = [model.node_info(i)["frames_per_step"] for i in range(len(nodes))]
@@ -982,7 +982,7 @@ def main():
     pk, pk_kind = peaks()
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = flops / (step_ms_mean * share / 1000.0) / 1e12
-    timing_note = ("algorithmic FLOPs per step / (graph-timed ms per step x the class's share of the per-launch "
+    timing_note = ("algorithmic FLOPs per step / (timed ms per step x the class's share of the per-launch "
                    "event pass)")
     if dtype == "f32":
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",

@@ -374,12 +374,13 @@ __global__ void __launch_bounds__(256) k_conv_tile_f32(const ConvArgs a) {
 // ---------------------------------------------------------------------------
 // Narrow contraction (M <= 16 rows, Kt <= 64): four threads per
 // GEMM column.  Thread q of a column's quad reduces indices 16q .. 16q+15 (its
-// quarter of the window, read with four 16-byte loads) into all 16 rows; the
-// quad then sums its partials with two XOR shuffles, in the fixed order
-// (q0 + q1) + (q2 + q3), and thread q stores rows 4q .. 4q+3.  Used by the
-// tail of the decoder (the noise branch's second conv, the inverse PQMF),
-// whose launches are short chains of dependent work: four threads per column
-// quarter each thread's chain.
+// quarter of the window: four 16-byte loads when cin % 4 == 0, else one load
+// per index) into all 16 rows; the quad then sums its partials with two XOR
+// shuffles, in the fixed order (q0 + q1) + (q2 + q3), and thread q stores rows
+// 4q .. 4q+3.  Used by the tail of the decoder (the noise branch's second
+// conv, the inverse PQMF) and the encoder's PQMF analysis, whose launches are
+// short chains of dependent work: four threads per column quarter each
+// thread's chain.
 // ---------------------------------------------------------------------------
 constexpr int kSmallCols = 128;  // columns per block (threads = 4 x)
 constexpr int kSmallRowPad = 4;  // floats of padding after every 16 reduction indices
